@@ -1,0 +1,124 @@
+/*
+ * lbo.h -- C ABI of the GB300 (sm_103a) fast Fourier spectral linearized
+ * Boltzmann collision operator library (liblbo.so).
+ *
+ * Method: T. Yin, Z. Cai, Y. Wang, "A fast Fourier spectral method for the
+ * linearized Boltzmann collision operator", arXiv 2503.09580.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  N points per velocity direction (N even; the paper's N is N/2),
+ *   periodic box [-L, L]^3, spacing h = 2L/N, collocation points
+ *   v_i = (i - N/2) h for i = 0..N-1 (Sec. 2.3: v_l = l L / N_p,
+ *   l = -N_p..N_p-1).  A velocity field is N^3 doubles, row-major
+ *   [i1][i2][i3]; a batch is [batch][i1][i2][i3].
+ * Maxwellian parameters.  params[b*5 + 0..4] = (rho, u1, u2, u3, theta):
+ *   M(v) = rho (2 pi theta)^{-3/2} exp(-|v-u|^2 / (2 theta))  (Sec. 2.1).
+ * Collision kernel.  Variable hard spheres, B(g) = C g^{2(1-omega)} for
+ *   g <= R and 0 beyond (Eq. (2.4), Sec. 2.3); C = 1/(4 pi) by default
+ *   (Eq. (4.1)), R = 4L/(3+sqrt 2) by default (the dealiasing bound).
+ * Memory.  Array arguments are caller-owned.  Each may be a device pointer
+ *   (CUDA global memory of the plan's device) or a host pointer; host
+ *   arrays are staged through plan-owned device buffers with copies on the
+ *   plan's stream, and such a call returns only after the result is back
+ *   in host memory.  Device-pointer calls are asynchronous on the plan's
+ *   stream; the plan owns its tables and workspace.
+ * Precision.  Inputs and outputs are FP64 in every mode; LBO_OPT_PRECISION
+ *   selects the arithmetic of the transforms and pointwise products.
+ * Errors.  Every call returns an lbo_status.  Argument errors are detected
+ *   before any launch; CUDA errors map to LBO_ECUDA and the CUDA error text
+ *   is available from lbo_last_error().  A plan is not thread-safe.
+ */
+#ifndef LBO_H
+#define LBO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbo_plan lbo_plan;
+
+typedef enum {
+  LBO_OK = 0,
+  LBO_EINVAL = 1,        /* bad argument (size, pointer, option value)      */
+  LBO_ENOMEM = 2,        /* device or host allocation failed                */
+  LBO_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed     */
+  LBO_ENOTCONV = 4,      /* iterative solve stopped at its iteration cap    */
+  LBO_EBREAKDOWN = 5,    /* Krylov breakdown                                */
+  LBO_ENAN = 6,          /* non-finite value detected                       */
+  LBO_EUNSUPPORTED = 7   /* combination of N / precision not built          */
+} lbo_status;
+
+typedef enum {
+  LBO_PREC_FP64 = 0,     /* FP64 transforms and products (the plain path)   */
+  LBO_PREC_FP32 = 1      /* FP32 transforms and products, FP64 in/out,
+                            FP64 Maxwellians, cut-off and final combination */
+} lbo_precision;
+
+typedef enum {
+  LBO_OPT_R = 0,           /* kernel cut-off R (double)                       */
+  LBO_OPT_C = 1,           /* kernel constant C                               */
+  LBO_OPT_EPS = 2,         /* cut-off level epsilon of Eq. (3.9), 1e-9        */
+  LBO_OPT_CUTOFF = 3,      /* 1: apply Eq. (3.9) to r = g/M (default), 0: no  */
+  LBO_OPT_MASS_FIX = 4,    /* 1: set the zero mode of the output to 0 (Sec 4.2)*/
+  LBO_OPT_MOMENT_FIX = 5,  /* 1: FP64 projection of the output onto zero mass,
+                              momentum and energy (least squares on the grid) */
+  LBO_OPT_HEMISPHERE_P = 6,/* hemisphere rule order p: M = 2 p^2 points (4)   */
+  LBO_OPT_PRECISION = 7    /* lbo_precision                                   */
+} lbo_option;
+
+/* Create a plan for N^3 grids on [-box, box]^3, VHS exponent vhs_omega in
+ * [0.5, 1], radial_nodes Gauss-Legendre nodes on [0, R] (Eq. (2.13)).
+ * Builds the tables of Algorithm 1 (its precomputation step) on the current
+ * CUDA device.  N must be 16, 32 or 64.  On success *out owns device memory
+ * until lbo_plan_destroy.  Errors: LBO_EINVAL, LBO_EUNSUPPORTED, LBO_ENOMEM,
+ * LBO_ECUDA (then *out is NULL). */
+lbo_status lbo_plan_create(int N, double box, double vhs_omega, int radial_nodes,
+                           lbo_plan **out);
+
+/* Set an option.  Options that change the tables (R, C, hemisphere order)
+ * rebuild them at the next apply.  LBO_EINVAL for an unknown key or an
+ * out-of-range value. */
+lbo_status lbo_plan_set(lbo_plan *plan, lbo_option key, double value);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*; NULL = the legacy
+ * default stream) for every launch and copy of the plan. */
+lbo_status lbo_plan_set_stream(lbo_plan *plan, void *stream);
+
+/* Linearized collision operator, Algorithm 1 ("CollisionOperator"):
+ *   out[b] = L_b[g[b]] = Q(M_b, g[b]) + Q(g[b], M_b),
+ * M_b the Maxwellian of params[b].  params: batch*5 doubles; g, out:
+ * batch*N^3 doubles (out must not alias g or params).  batch >= 0
+ * (0 is a no-op).  Point values in, point values out (Sec. 3.5). */
+lbo_status lbo_apply_linearized(lbo_plan *plan, const double *maxwellian_params,
+                                const double *g, double *out, int batch);
+
+/* Quadratic collision operator Q(f,f) in the M-point hemisphere-quadrature
+ * form of Eq. (2.14) with the plan's radial rule and a product hemisphere
+ * rule of M = 2p^2 points.  f, out: batch*N^3 doubles, no aliasing. */
+lbo_status lbo_apply_quadratic(lbo_plan *plan, const double *f, double *out, int batch);
+
+/* Wait for all work queued on the plan's stream; report the first
+ * asynchronous CUDA error, if any. */
+lbo_status lbo_plan_sync(lbo_plan *plan);
+
+/* Number of kernels the last apply call launched (for accounting). */
+int lbo_plan_last_launches(const lbo_plan *plan);
+
+/* Free a plan (NULL is allowed). */
+void lbo_plan_destroy(lbo_plan *plan);
+
+/* Static description of a status code. */
+const char *lbo_status_string(lbo_status s);
+
+/* Text of the last CUDA error seen by this thread in any lbo call ("" if
+ * none). */
+const char *lbo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBO_H */

@@ -1,0 +1,42 @@
+// Internal plan structure of liblbo (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbo.h"
+
+struct lbo_plan {
+  int N = 0, J = 0, device = 0;
+  double L = 0, omega = 0, R = 0, C = 0, eps = 1e-9;
+  int cutoff = 1, mass_fix = 0, moment_fix = 0, hemi_p = 4, precision = 0;
+  cudaStream_t stream = nullptr;
+  bool tables_dirty = false;
+  // radial rule (host copy)
+  std::vector<double> gj, wj, Bj;
+  // device tables of Algorithm 1
+  double* d_phi64 = nullptr;    // [J][QMAX] phi_j(|k|^2) / N^3
+  double* d_omega64 = nullptr;  // [QMAX] omega(|k|^2) / N^3
+  double* d_phit64 = nullptr;   // [J][N^3] phit_j, cyclic order
+  float* d_phi32 = nullptr;
+  float* d_omega32 = nullptr;
+  float* d_phit32 = nullptr;
+  double* d_dummy_params = nullptr;
+  // workspace of the generic path
+  void* ws = nullptr;
+  int ws_batch = 0;
+  // staging for host-pointer calls
+  double *stage_in = nullptr, *stage_out = nullptr, *stage_par = nullptr;
+  size_t stage_in_cap = 0, stage_out_cap = 0, stage_par_cap = 0;
+  // quadratic operator state (hemisphere rule, workspace)
+  void* quad = nullptr;
+  int last_launches = 0;
+};
+
+namespace lbo {
+lbo_status cuda_fail(cudaError_t e, const char* where);
+// zero-mode removal and/or FP64 conservation projection of out[B][N^3]
+lbo_status launch_fixes(lbo_plan* p, double* out, int B, int N, double h, cudaStream_t s, int* launches);
+void free_quadratic(lbo_plan* p);
+}  // namespace lbo

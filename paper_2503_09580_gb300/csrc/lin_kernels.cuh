@@ -1,0 +1,345 @@
+// Kernels of the generic (FP64 / FP32) path of Algorithm 1.
+//
+// A batched 3-D real transform is split into
+//   * plane kernels: for each i1-plane, the axis-3 real<->half-complex
+//     transform (two real rows packed into one complex row) and the axis-2
+//     complex transform, done in shared memory;
+//   * axis-1 kernels: for a tile of (p2, k3) columns of one instance, the
+//     axis-1 complex transform, fused with the pointwise stage that follows
+//     it (a product with r^, a multiplier table indexed by |k|^2, or the
+//     accumulation of phi_j psi^_j into L^+).
+// Half-spectrum layout per instance: [p1][p2][k3], k3 = 0..N/2 natural,
+// p1, p2 digit-reversed positions (see fft.cuh); H = N*N*(N/2+1).
+// Real fields: [i1][i2][i3] centred order (v_i = (i - N/2) h), except the
+// kernel u_j = M^g phit_j, which is indexed by cyclic displacement.
+#pragma once
+#include "fft.cuh"
+
+namespace lbo {
+
+struct InstanceParams {
+  double rho, u1, u2, u3, theta;
+};
+
+__device__ __forceinline__ InstanceParams load_params(const double* p, int b) {
+  InstanceParams q;
+  q.rho = p[5 * b + 0];
+  q.u1 = p[5 * b + 1];
+  q.u2 = p[5 * b + 2];
+  q.u3 = p[5 * b + 3];
+  q.theta = p[5 * b + 4];
+  return q;
+}
+
+// Sources of the real plane fed to a forward plane transform.
+enum PlaneSrc {
+  SRC_RATIO = 0,   // r = g / M, 0 where the cut-off of Eq. (3.9) applies
+  SRC_REAL64 = 1,  // a double field (the ABI input g)
+  SRC_MAXW = 2,    // the Maxwellian M
+  SRC_U = 3        // u_j = M^g phit_j, cyclic displacement order
+};
+
+struct PlaneArgs {
+  const double* params;  // [B][5]
+  const double* g;       // [B][N^3] (SRC_RATIO / SRC_REAL64)
+  const void* phit;      // [N^3] of T (SRC_U): phit_j, cyclic order
+  double h;              // grid spacing
+  double log_inv_eps;    // ln(1/eps)
+  int cutoff;            // apply Eq. (3.9)
+};
+
+// Cut-off test of Eq. (3.9), M/rho < eps  <=>
+//   |v-u|^2/(2 theta) > ln(1/eps) - 1.5 ln(2 pi theta).
+// Every operation is rounded separately (no FMA contraction) so that the
+// decision is reproducible.
+__device__ __forceinline__ bool cut_point(double d2, double theta, double log_inv_eps) {
+  double lhs = __ddiv_rn(d2, __dmul_rn(2.0, theta));
+  double thr = __dsub_rn(log_inv_eps, __dmul_rn(1.5, log(__dmul_rn(__dmul_rn(2.0, 3.141592653589793), theta))));
+  return lhs > thr;
+}
+
+__device__ __forceinline__ double sq_rn(double a) { return __dmul_rn(a, a); }
+
+// |v - u|^2 at centred index (i1, i2, i3), as ((d1^2 + d2^2) + d3^2).
+__device__ __forceinline__ double dist2(int i1, int i2, int i3, int N, double h, const InstanceParams& q) {
+  double v1 = __dmul_rn((double)(i1 - N / 2), h), v2 = __dmul_rn((double)(i2 - N / 2), h),
+         v3 = __dmul_rn((double)(i3 - N / 2), h);
+  return __dadd_rn(__dadd_rn(sq_rn(__dsub_rn(v1, q.u1)), sq_rn(__dsub_rn(v2, q.u2))), sq_rn(__dsub_rn(v3, q.u3)));
+}
+
+__device__ __forceinline__ double maxwellian(double d2, const InstanceParams& q) {
+  return q.rho * pow(2.0 * 3.141592653589793 * q.theta, -1.5) * exp(-d2 / (2.0 * q.theta));
+}
+
+template <typename T, int N, int SRC>
+__device__ __forceinline__ T plane_source(const PlaneArgs& a, const InstanceParams& q, int b, int i1, int i2, int i3,
+                                          const double* ex1) {
+  if constexpr (SRC == SRC_U) {
+    // M^g(d) phit_j(d), d = cyclic displacement; ex1[i] = exp(-d_i^2/theta)
+    const T* ph = (const T*)a.phit;
+    double mg = ex1[N + i1] * ex1[i2] * ex1[i3];  // ex1[N] holds the prefactor-folded axis-1 table
+    return (T)(mg * (double)ph[(i1 * N + i2) * N + i3]);
+  } else {
+    size_t idx = (((size_t)b * N + i1) * N + i2) * N + i3;
+    if constexpr (SRC == SRC_REAL64) {
+      return (T)a.g[idx];
+    } else {
+      double d2 = dist2(i1, i2, i3, N, a.h, q);
+      if constexpr (SRC == SRC_MAXW) {
+        return (T)maxwellian(d2, q);
+      } else {  // SRC_RATIO
+        if (a.cutoff && cut_point(d2, q.theta, a.log_inv_eps)) return (T)0;
+        return (T)(a.g[idx] / maxwellian(d2, q));
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ plane parts
+// Shared memory of a plane kernel handling PPC planes:
+//   A: [PPC][N/2][N]  packed complex rows along i3  (pencil ps=N, es=1)
+//   B: [N][PPC][N/2+1] half rows; axis-2 pencils p = pp*(N/2+1)+k3,
+//      ps = 1, es = PPC*(N/2+1)
+template <typename T, int N, int PPC>
+struct PlaneSmem {
+  static constexpr int HC = N / 2 + 1;
+  static constexpr int A_ELEMS = PPC * (N / 2) * N;
+  static constexpr int B_ELEMS = N * PPC * HC;
+  static constexpr size_t BYTES = sizeof(cpx<T>) * (A_ELEMS + B_ELEMS);
+};
+
+// A (packed rows, after the forward i3 transform) -> B half rows, then the
+// forward axis-2 transform of B.
+template <typename T, int N, int PPC>
+__device__ __forceinline__ void plane_forward_from_A(cpx<T>* A, cpx<T>* B) {
+  constexpr int HC = N / 2 + 1;
+  smem_fft<T, N, false, false>(A, PPC * (N / 2), N, 1);
+  for (int t = threadIdx.x; t < PPC * (N / 2) * HC; t += blockDim.x) {
+    int k3 = t % HC, rest = t / HC, qq = rest % (N / 2), pp = rest / (N / 2);
+    const cpx<T>* z = A + (pp * (N / 2) + qq) * N;
+    cpx<T> z1 = z[pos_of_freq<N>(k3)], z2 = conjc(z[pos_of_freq<N>((N - k3) & (N - 1))]);
+    cpx<T> xa = cscale(z1 + z2, (T)0.5);
+    cpx<T> d = z1 - z2;
+    cpx<T> xb = make_c((T)0.5 * d.y, (T)-0.5 * d.x);  // (z1 - conj z2) / (2i)
+    B[((2 * qq) * PPC + pp) * HC + k3] = xa;
+    B[((2 * qq + 1) * PPC + pp) * HC + k3] = xb;
+  }
+  __syncthreads();
+  smem_fft<T, N, false, true>(B, PPC * HC, 1, PPC * HC);
+}
+
+// B (half spectrum, axis 2 in digit-reversed positions) -> inverse axis 2 ->
+// packed rows in A -> inverse i3 transform: A[pp][q][i3] = x[2q][i3] + i x[2q+1][i3].
+template <typename T, int N, int PPC>
+__device__ __forceinline__ void plane_inverse_to_A(cpx<T>* A, cpx<T>* B) {
+  constexpr int HC = N / 2 + 1;
+  smem_fft<T, N, true, true>(B, PPC * HC, 1, PPC * HC);
+  for (int t = threadIdx.x; t < PPC * (N / 2) * N; t += blockDim.x) {
+    int k3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
+    const cpx<T>* ra = B + ((2 * qq) * PPC + pp) * HC;
+    const cpx<T>* rb = B + ((2 * qq + 1) * PPC + pp) * HC;
+    cpx<T> xa, xb;
+    if (k3 == 0 || k3 == N / 2) {
+      xa = make_c(ra[k3].x, (T)0);
+      xb = make_c(rb[k3].x, (T)0);
+    } else if (k3 < N / 2) {
+      xa = ra[k3];
+      xb = rb[k3];
+    } else {
+      xa = conjc(ra[N - k3]);
+      xb = conjc(rb[N - k3]);
+    }
+    A[(pp * (N / 2) + qq) * N + pos_of_freq<N>(k3)] = make_c(xa.x - xb.y, xa.y + xb.x);  // xa + i xb
+  }
+  __syncthreads();
+  smem_fft<T, N, true, false>(A, PPC * (N / 2), N, 1);
+}
+
+template <typename T, int N, int PPC>
+__device__ __forceinline__ void plane_store_B(const cpx<T>* B, cpx<T>* dst, int b, int i1_0) {
+  constexpr int HC = N / 2 + 1;
+  for (int t = threadIdx.x; t < PPC * N * HC; t += blockDim.x) {
+    int k3 = t % HC, rest = t / HC, k2 = rest % N, pp = rest / N;
+    dst[(((size_t)b * N + i1_0 + pp) * N + k2) * HC + k3] = B[(k2 * PPC + pp) * HC + k3];
+  }
+}
+
+template <typename T, int N, int PPC>
+__device__ __forceinline__ void plane_load_B(cpx<T>* B, const cpx<T>* src, int b, int i1_0) {
+  constexpr int HC = N / 2 + 1;
+  for (int t = threadIdx.x; t < PPC * N * HC; t += blockDim.x) {
+    int k3 = t % HC, rest = t / HC, k2 = rest % N, pp = rest / N;
+    B[(k2 * PPC + pp) * HC + k3] = src[(((size_t)b * N + i1_0 + pp) * N + k2) * HC + k3];
+  }
+  __syncthreads();
+}
+
+// Per-instance separable Gaussian tables for M^g (SRC_U): ex[i] for axes 2,3
+// = exp(-d_i^2/theta); ex[N + i] = rho (pi theta)^{-3/2} exp(-d_i^2/theta).
+template <int N>
+__device__ __forceinline__ void fill_mg_tables(double* ex, const InstanceParams& q, double h) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double d = (double)centred<N>(i) * h;
+    double e = exp(-(d * d) / q.theta);
+    ex[i] = e;
+    ex[N + i] = q.rho * pow(3.141592653589793 * q.theta, -1.5) * e;
+  }
+  __syncthreads();
+}
+
+// Per-instance separable tables for M^h = rho (pi theta)^{-3/2} prod_d exp(-(v_d-u_d)^2/theta):
+// eh[d*N + i] = exp(-(v_i-u_d)^2/theta), axis 1 carries the prefactor.
+template <int N>
+__device__ __forceinline__ void fill_mh_tables(double* eh, const InstanceParams& q, double h) {
+  for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) {
+    int d = t / N, i = t % N;
+    double ud = d == 0 ? q.u1 : (d == 1 ? q.u2 : q.u3);
+    double v = (double)(i - N / 2) * h - ud;
+    double e = exp(-(v * v) / q.theta);
+    if (d == 0) e *= q.rho * pow(3.141592653589793 * q.theta, -1.5);
+    eh[t] = e;
+  }
+  __syncthreads();
+}
+
+// Forward plane transform of a real source field -> half spectrum (axis 1
+// untransformed).  grid = (N/PPC, B).
+template <typename T, int N, int PPC, int SRC>
+__global__ void __launch_bounds__(256) k_plane_fwd(PlaneArgs a, cpx<T>* __restrict__ dst) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* A = (cpx<T>*)smem_raw;
+  cpx<T>* B = A + PlaneSmem<T, N, PPC>::A_ELEMS;
+  __shared__ double ex[2 * N];
+  const int b = blockIdx.y, i1_0 = blockIdx.x * PPC;
+  const InstanceParams q = load_params(a.params, b);
+  if constexpr (SRC == SRC_U) fill_mg_tables<N>(ex, q, a.h);
+  for (int t = threadIdx.x; t < PPC * (N / 2) * N; t += blockDim.x) {
+    int i3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
+    int i1 = i1_0 + pp;
+    T x0 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq, i3, ex);
+    T x1 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq + 1, i3, ex);
+    A[(pp * (N / 2) + qq) * N + i3] = make_c(x0, x1);
+  }
+  __syncthreads();
+  plane_forward_from_A<T, N, PPC>(A, B);
+  plane_store_B<T, N, PPC>(B, dst, b, i1_0);
+}
+
+enum PlaneInvMode {
+  INV_TO_REAL = 0,    // write the real field (T) to dst_real
+  INV_MH_FWD = 1      // multiply by M^h and transform forward again, in place
+};
+
+template <typename T, int N, int PPC, int MODE>
+__global__ void __launch_bounds__(256) k_plane_inv(PlaneArgs a, cpx<T>* __restrict__ src, T* __restrict__ dst_real) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* A = (cpx<T>*)smem_raw;
+  cpx<T>* B = A + PlaneSmem<T, N, PPC>::A_ELEMS;
+  __shared__ double eh[3 * N];
+  const int b = blockIdx.y, i1_0 = blockIdx.x * PPC;
+  const InstanceParams q = load_params(a.params, b);
+  if constexpr (MODE == INV_MH_FWD) fill_mh_tables<N>(eh, q, a.h);
+  plane_load_B<T, N, PPC>(B, src, b, i1_0);
+  plane_inverse_to_A<T, N, PPC>(A, B);
+  if constexpr (MODE == INV_TO_REAL) {
+    for (int t = threadIdx.x; t < PPC * (N / 2) * N; t += blockDim.x) {
+      int i3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
+      cpx<T> z = A[(pp * (N / 2) + qq) * N + i3];
+      size_t o = (((size_t)b * N + i1_0 + pp) * N + 2 * qq) * N + i3;
+      dst_real[o] = z.x;
+      dst_real[o + N] = z.y;
+    }
+  } else {
+    for (int t = threadIdx.x; t < PPC * (N / 2) * N; t += blockDim.x) {
+      int i3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
+      int i1 = i1_0 + pp;
+      double m13 = eh[i1] * eh[2 * N + i3];
+      cpx<T>& z = A[(pp * (N / 2) + qq) * N + i3];
+      z.x = (T)((double)z.x * (m13 * eh[N + 2 * qq]));
+      z.y = (T)((double)z.y * (m13 * eh[N + 2 * qq + 1]));
+    }
+    __syncthreads();
+    plane_forward_from_A<T, N, PPC>(A, B);
+    plane_store_B<T, N, PPC>(B, src, b, i1_0);
+  }
+}
+
+// ------------------------------------------------------------ axis 1
+enum Axis1Mode {
+  AX_FWD_STORE = 0,   // dst = F1(src)
+  AX_FWD_MULC_INV = 1,// dst = F1^-1( F1(src) * mulc * scale ), mulc per instance
+  AX_FWD_MULT_INV = 2,// dst = F1^-1( F1(src) * table[|k|^2] )
+  AX_FWD_ACC = 3,     // dst (+)= table[|k|^2] * F1(src)
+  AX_INV_STORE = 4    // dst = F1^-1(src)
+};
+
+struct Axis1Args {
+  const void* mulc;     // [B][H] complex T (AX_FWD_MULC_INV)
+  const void* table;    // [QMAX] T (AX_FWD_MULT_INV, AX_FWD_ACC)
+  double scale;         // AX_FWD_MULC_INV
+  int first;            // AX_FWD_ACC: store instead of accumulate
+};
+
+template <typename T, int N, int CW, int MODE>
+__global__ void __launch_bounds__(256) k_axis1(Axis1Args a, const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst) {
+  constexpr int HC = N / 2 + 1, NC = N * HC;
+  __shared__ __align__(16) cpx<T> S[N * CW];
+  const int b = blockIdx.y, c0 = blockIdx.x * CW;
+  const size_t inst = (size_t)b * N * NC;
+  for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
+    int c = t % CW, r = t / CW;
+    S[t] = (c0 + c < NC) ? src[inst + (size_t)r * NC + c0 + c] : make_c((T)0, (T)0);
+  }
+  __syncthreads();
+  if constexpr (MODE != AX_INV_STORE) smem_fft<T, N, false, true>(S, CW, 1, CW);
+  else smem_fft<T, N, true, true>(S, CW, 1, CW);
+  if constexpr (MODE == AX_FWD_MULC_INV || MODE == AX_FWD_MULT_INV) {
+    for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
+      int c = t % CW, r = t / CW;
+      if (c0 + c < NC) {
+        if constexpr (MODE == AX_FWD_MULC_INV) {
+          cpx<T> m = ((const cpx<T>*)a.mulc)[inst + (size_t)r * NC + c0 + c];
+          S[t] = cscale(cmul(S[t], m), (T)a.scale);
+        } else {
+          int col = c0 + c, p2 = col / HC, k3 = col % HC;
+          int k1 = centred<N>(freq_of_pos<N>(r)), k2 = centred<N>(freq_of_pos<N>(p2));
+          S[t] = cscale(S[t], ((const T*)a.table)[k1 * k1 + k2 * k2 + k3 * k3]);
+        }
+      }
+    }
+    __syncthreads();
+    smem_fft<T, N, true, true>(S, CW, 1, CW);
+  }
+  for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
+    int c = t % CW, r = t / CW;
+    if (c0 + c >= NC) continue;
+    size_t o = inst + (size_t)r * NC + c0 + c;
+    if constexpr (MODE == AX_FWD_ACC) {
+      int col = c0 + c, p2 = col / HC, k3 = col % HC;
+      int k1 = centred<N>(freq_of_pos<N>(r)), k2 = centred<N>(freq_of_pos<N>(p2));
+      cpx<T> v = cscale(S[t], ((const T*)a.table)[k1 * k1 + k2 * k2 + k3 * k3]);
+      dst[o] = a.first ? v : dst[o] + v;
+    } else {
+      dst[o] = S[t];
+    }
+  }
+}
+
+// out = L+ - uu M - ww g  (FP64), optional zero-mode removal done separately.
+template <typename T, int N>
+__global__ void k_combine(const double* __restrict__ params, const double* __restrict__ g, const T* __restrict__ Lp,
+                          const T* __restrict__ uu, const T* __restrict__ ww, double* __restrict__ out, double h,
+                          int B) {
+  const size_t n3 = (size_t)N * N * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)B * n3;
+       t += (size_t)gridDim.x * blockDim.x) {
+    int b = (int)(t / n3);
+    int r = (int)(t % n3);
+    int i3 = r % N, i2 = (r / N) % N, i1 = r / (N * N);
+    InstanceParams q = load_params(params, b);
+    double M = maxwellian(dist2(i1, i2, i3, N, h, q), q);
+    out[t] = (double)Lp[t] - (double)uu[t] * M - (double)ww[t] * g[t];
+  }
+}
+
+}  // namespace lbo

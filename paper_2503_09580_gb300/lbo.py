@@ -1,0 +1,153 @@
+"""Thin Python binding of liblbo.so (include/lbo.h): argument marshalling
+only.  Every step of the operators runs in the library's CUDA kernels; if
+the library is missing this module raises instead of computing anything.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays, float64,
+C-contiguous.  CUDA tensors are passed as device pointers and the call is
+asynchronous on torch's current stream; host arrays go through the
+library's staged-copy path (the call returns with the result in host
+memory).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbo.so")
+
+LBO_OPT = {"R": 0, "C": 1, "eps": 2, "cutoff": 3, "mass_fix": 4, "moment_fix": 5,
+           "hemisphere_p": 6, "precision": 7}
+PRECISION = {"fp64": 0, "fp32": 1}
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "not converged",
+          5: "Krylov breakdown", 6: "non-finite value", 7: "unsupported configuration"}
+
+# Every symbol include/lbo.h declares (checked by the tests).
+EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_linearized",
+           "lbo_apply_quadratic", "lbo_plan_sync", "lbo_plan_last_launches", "lbo_plan_destroy",
+           "lbo_status_string", "lbo_last_error")
+
+_lib = None
+
+
+class LboError(RuntimeError):
+    def __init__(self, status, where):
+        msg = "%s: %s" % (where, STATUS.get(status, "status %d" % status))
+        detail = _lib.lbo_last_error().decode() if _lib is not None else ""
+        if detail:
+            msg += " (" + detail + ")"
+        super().__init__(msg)
+        self.status = status
+
+
+def load():
+    """Load liblbo.so (built by paper_2503_09580_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblbo.so not built (%s); run paper_2503_09580_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
+    lib.lbo_plan_create.argtypes = [ip, ctypes.c_double, ctypes.c_double, ip, ctypes.POINTER(vp)]
+    lib.lbo_plan_create.restype = ip
+    lib.lbo_plan_set.argtypes = [vp, ip, ctypes.c_double]
+    lib.lbo_plan_set.restype = ip
+    lib.lbo_plan_set_stream.argtypes = [vp, vp]
+    lib.lbo_plan_set_stream.restype = ip
+    lib.lbo_apply_linearized.argtypes = [vp, dp, dp, dp, ip]
+    lib.lbo_apply_linearized.restype = ip
+    lib.lbo_apply_quadratic.argtypes = [vp, dp, dp, ip]
+    lib.lbo_apply_quadratic.restype = ip
+    lib.lbo_plan_sync.argtypes = [vp]
+    lib.lbo_plan_sync.restype = ip
+    lib.lbo_plan_last_launches.argtypes = [vp]
+    lib.lbo_plan_last_launches.restype = ip
+    lib.lbo_plan_destroy.argtypes = [vp]
+    lib.lbo_plan_destroy.restype = None
+    lib.lbo_status_string.argtypes = [ip]
+    lib.lbo_status_string.restype = ctypes.c_char_p
+    lib.lbo_last_error.argtypes = []
+    lib.lbo_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Data pointer of a float64 C-contiguous torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float64 array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(st, where):
+    if st != 0:
+        raise LboError(st, where)
+
+
+def _current_stream(*arrays):
+    for a in arrays:
+        if hasattr(a, "is_cuda") and a.is_cuda:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return None
+
+
+class Plan:
+    """lbo_plan: N^3 grid on [-box, box]^3, VHS exponent, radial nodes."""
+
+    def __init__(self, N, box, vhs_omega, radial_nodes, **options):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.lbo_plan_create(int(N), float(box), float(vhs_omega), int(radial_nodes), ctypes.byref(h)),
+               "lbo_plan_create")
+        self._h = h
+        self.N, self.box, self.vhs_omega, self.J = int(N), float(box), float(vhs_omega), int(radial_nodes)
+        for k, v in options.items():
+            self.set(k, v)
+
+    def set(self, key, value):
+        if key == "precision" and isinstance(value, str):
+            value = PRECISION[value]
+        _check(load().lbo_plan_set(self._h, LBO_OPT[key], float(value)), "lbo_plan_set(%s)" % key)
+
+    def _stream(self, *arrays):
+        s = _current_stream(*arrays)
+        _check(load().lbo_plan_set_stream(self._h, s), "lbo_plan_set_stream")
+
+    def apply_linearized(self, params, g, out):
+        """out[b] = L_b[g[b]] (Algorithm 1); params (B,5), g/out (B,N,N,N)."""
+        batch = int(params.shape[0]) if len(params.shape) == 2 else 1
+        self._stream(params, g, out)
+        _check(load().lbo_apply_linearized(self._h, _ptr(params), _ptr(g), _ptr(out), batch),
+               "lbo_apply_linearized")
+        return out
+
+    def apply_quadratic(self, f, out):
+        batch = int(f.shape[0]) if len(f.shape) == 4 else 1
+        self._stream(f, out)
+        _check(load().lbo_apply_quadratic(self._h, _ptr(f), _ptr(out), batch), "lbo_apply_quadratic")
+        return out
+
+    def sync(self):
+        _check(load().lbo_plan_sync(self._h), "lbo_plan_sync")
+
+    @property
+    def last_launches(self):
+        return load().lbo_plan_last_launches(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lbo_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,51 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports
+every entry point include/lbo.h declares, and rejects bad arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2503_09580_gb300 import lbo
+from paper_2503_09580_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return lbo.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lbo.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbo_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 10
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(lbo.EXPORTS)
+
+
+def test_status_strings(lib):
+    assert lib.lbo_status_string(0) == b"ok"
+    assert lib.lbo_status_string(7) == b"unsupported configuration"
+
+
+def test_argument_errors_before_any_launch(lib):
+    h = ctypes.c_void_p()
+    assert lib.lbo_plan_create(17, 8.0, 0.5, 16, ctypes.byref(h)) == 7   # odd / unbuilt N
+    assert h.value is None
+    assert lib.lbo_plan_create(32, -1.0, 0.5, 32, ctypes.byref(h)) == 1
+    assert lib.lbo_plan_create(32, 8.0, 0.3, 32, ctypes.byref(h)) == 1  # omega outside [0.5, 1]
+    assert lib.lbo_plan_create(32, 8.0, 0.5, 0, ctypes.byref(h)) == 1
+    assert lib.lbo_plan_set(None, 0, 1.0) == 1
+    assert lib.lbo_apply_linearized(None, None, None, None, 1) == 1
+    assert lib.lbo_plan_sync(None) == 1
+    lib.lbo_plan_destroy(None)

@@ -1,0 +1,170 @@
+"""Parity of the CUDA path of Algorithm 1 (L[g]) with the CPU oracle,
+through the C ABI.  Error metric: normwise max relative error
+max|x - y| / max|y| per batch.  Bar: 1e-12 in FP64 for inputs g = M p
+(r = g/M bounded); for inputs with grid noise r reaches noise/(eps rho)
+and every FFT evaluation (the oracle's included) loses digits in
+proportion (Sec. 3.3), so the bar scales with max|r|."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import grid
+from oracle.linearized import Tables, apply_linearized, collision_operator
+from oracle.moments import conservation_projection
+from paper_2503_09580_gb300 import lbo, workloads
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+_TABLES = {}
+
+
+def tables(n, L, om, J, **kw):
+    key = (n, L, om, J, tuple(sorted(kw.items())))
+    if key not in _TABLES:
+        _TABLES[key] = Tables(n, L, om, J, **kw)
+    return _TABLES[key]
+
+
+def run(plan, params, g):
+    tp = torch.from_numpy(params).to(DEV)
+    tg = torch.from_numpy(g).to(DEV)
+    out = torch.empty_like(tg)
+    plan.apply_linearized(tp, tg, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def ratio_max(params, g, n, L):
+    """max |g/M| over points the cut-off keeps (the conditioning of r)."""
+    out = 0.0
+    for b in range(params.shape[0]):
+        rho, u1, u2, u3, th = params[b]
+        a = workloads.velocity_axis(n, L)
+        d2 = (a[:, None, None] - u1) ** 2 + (a[None, :, None] - u2) ** 2 + (a[None, None, :] - u3) ** 2
+        M = rho * (2 * np.pi * th) ** -1.5 * np.exp(-d2 / (2 * th))
+        keep = d2 / (2 * th) <= np.log(1e9) - 1.5 * np.log(2 * np.pi * th)
+        out = max(out, np.abs(g[b][keep] / M[keep]).max())
+    return out
+
+
+@pytest.mark.parametrize("omega", [0.5, 1.0])
+def test_single_instance_n16_fp64(omega):
+    n, L = 16, 8.0
+    params, g = workloads.single_instance(n, L, seed=0)
+    plan = lbo.Plan(n, L, omega, n)
+    got = run(plan, params, g)
+    ref = apply_linearized(tables(n, L, omega, n), params, g)
+    assert relerr(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("omega", [0.5, 0.74, 1.0])
+def test_batched_n32_fp64_noise_free(omega):
+    n, L = 32, 8.0
+    params, g = workloads.batched_instances(n, L, batch=5, seed=1, noise=0.0)
+    plan = lbo.Plan(n, L, omega, n)
+    got = run(plan, params, g)
+    ref = apply_linearized(tables(n, L, omega, n), params, g)
+    assert relerr(got, ref) <= 1e-12
+
+
+def test_n64_fp64():
+    n, L = 64, 8.0
+    params, g = workloads.batched_instances(n, L, batch=2, seed=2, noise=0.0)
+    plan = lbo.Plan(n, L, 1.0, n)
+    got = run(plan, params, g)
+    ref = apply_linearized(tables(n, L, 1.0, n), params, g)
+    assert relerr(got, ref) <= 1e-12
+
+
+def test_noisy_n32_fp64_within_conditioning_bound():
+    n, L = 32, 8.0
+    params, g = workloads.batched_instances(n, L, batch=3, seed=4, noise=1e-3)
+    plan = lbo.Plan(n, L, 0.5, n)
+    got = run(plan, params, g)
+    ref = apply_linearized(tables(n, L, 0.5, n), params, g)
+    bound = 1e-15 * ratio_max(params, g, n, L)
+    assert relerr(got, ref) <= max(1e-12, bound)
+
+
+def test_full_size_batch_sampled_instances():
+    """The benchmark's launch configuration (N = 32, batch 256, per-instance
+    Maxwellians), noise-free twin, checked on sampled instances."""
+    n, L, om = 32, 8.0, 0.5
+    params, g = workloads.batched_instances(n, L, batch=256, seed=0, noise=0.0)
+    plan = lbo.Plan(n, L, om, n)
+    got = run(plan, params, g)
+    tab = tables(n, L, om, n)
+    for b in (0, 97, 255):
+        ref = apply_linearized(tab, params[b:b + 1], g[b:b + 1])
+        assert relerr(got[b:b + 1], ref) <= 1e-12
+
+
+def test_host_pointer_path_matches_device_path():
+    n, L = 16, 8.0
+    params, g = workloads.batched_instances(n, L, batch=3, seed=5, noise=0.0)
+    plan = lbo.Plan(n, L, 0.5, n)
+    dev = run(plan, params, g)
+    out = np.empty_like(g)
+    plan.apply_linearized(params, g, out)
+    assert np.array_equal(out, dev)
+
+
+def test_deterministic_and_batch_growth():
+    n, L = 16, 8.0
+    plan = lbo.Plan(n, L, 0.74, n)
+    p1, g1 = workloads.batched_instances(n, L, batch=2, seed=6, noise=0.0)
+    a = run(plan, p1, g1)
+    p2, g2 = workloads.batched_instances(n, L, batch=7, seed=6, noise=0.0)
+    b = run(plan, p2, g2)          # grows the workspace
+    c = run(plan, p2, g2)
+    assert np.array_equal(b, c)
+    assert np.array_equal(a[0], b[0])  # same seed -> same first instance
+    empty = torch.empty((0, n, n, n), dtype=torch.float64, device=DEV)
+    plan.apply_linearized(torch.empty((0, 5), dtype=torch.float64, device=DEV), empty, empty.clone())
+
+
+def test_mass_fix_and_moment_fix():
+    n, L = 16, 8.0
+    params, g = workloads.batched_instances(n, L, batch=2, seed=8, noise=0.0)
+    tab = tables(n, L, 0.5, n)
+    plan = lbo.Plan(n, L, 0.5, n, mass_fix=1)
+    got = run(plan, params, g)
+    ref = apply_linearized(tab, params, g, mass_fix=True)
+    assert relerr(got, ref) <= 1e-12
+    plan = lbo.Plan(n, L, 0.5, n, moment_fix=1)
+    got = run(plan, params, g)
+    ref = apply_linearized(tab, params, g)
+    for b in range(2):
+        proj = grid.to_centred(conservation_projection(grid.to_cyclic(ref[b]), n, L))
+        assert relerr(got[b], proj) <= 1e-12
+
+
+def test_cutoff_off_and_eps_option():
+    n, L = 16, 8.0
+    params, g = workloads.batched_instances(n, L, batch=2, seed=9, noise=0.0)
+    for kw, okw in (({"cutoff": 0}, {"cutoff": False}), ({"eps": 1e-5}, {"eps": 1e-5})):
+        plan = lbo.Plan(n, L, 0.5, n, **kw)
+        got = run(plan, params, g)
+        ref = apply_linearized(tables(n, L, 0.5, n), params, g, **okw)
+        assert relerr(got, ref) <= 1e-12
+
+
+def test_fp32_rounding_bound_noise_free():
+    """FP32 transforms against the FP64 oracle with the same cut-off.  The
+    FFT convolution of r loses accuracy in proportion to max|r| (Sec. 3.3):
+    the stated bound is u32 * max|r| with u32 = 2^-24 (measured ~0.13 of it)."""
+    n, L = 32, 8.0
+    params, g = workloads.batched_instances(n, L, batch=4, seed=10, noise=0.0)
+    plan = lbo.Plan(n, L, 0.5, n, precision="fp32")
+    got = run(plan, params, g)
+    ref = apply_linearized(tables(n, L, 0.5, n), params, g)
+    err = relerr(got, ref)
+    bound = 2.0 ** -24 * ratio_max(params, g, n, L)
+    print("fp32 noise-free rel err %.3e (bound %.3e)" % (err, bound))
+    assert err <= bound
