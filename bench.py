@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Benchmark: batched applications of the linearized collision operator
+L[g] (Algorithm 1) per second on one GB300, N = 32, batch 256, per-instance
+background Maxwellians rho ~ U[0.5,2], u_i ~ U[-0.5,0.5], theta ~ U[0.5,2],
+g = M * (quartic polynomial, N(0,1) coefficients) + 1e-3 N(0,1) grid noise.
+
+One step = one lbo_apply_linearized call over the whole batch (every kernel
+of the path).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+  python bench.py --impl reference   # the CPU oracle on the host cores
+
+Multi-GPU (torchrun): each rank applies L to its own batch (instances are
+independent; no data-path collective), value = all ranks' applications /
+max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "L[g] applications/sec at N=32 (batch 256, per-instance Maxwellians)"
+UNIT = "applications/s"
+N_GRID, BOX, BATCH = 32, 8.0, 256
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+# ALU peaks derived from unit counts and the maximum SM clock:
+#   FP64: 4 flop/clk/SM (2 DFMA/clk/SM, measured by an FMA probe) x 152 SMs x 2070 MHz
+#   FP32: 256 flop/clk/SM (128 FFMA lanes) x 152 SMs x 2070 MHz
+PEAK_TFLOPS = {"fp64": 4 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12,
+               "fp32": 256 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12}
+# DRAM bytes (read + write) per launch of the dominant kernel at the benchmark
+# workload, from ncu (profiles/*.md); None when not captured for this build.
+NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456}
+
+
+def transform_axis_flops(n):
+    """Conventional flops of one axis pass of a real 3-D transform of n^3
+    points: (2.5 n^3 log2(n^3)) / 3."""
+    return 2.5 * n ** 3 * np.log2(n)
+
+
+# Algorithmic flops per instance of each kernel of the generic path, in axis
+# passes of a real 3-D transform (pointwise products counted separately).
+KERNEL_AXIS_PASSES = {
+    "plane_fwd_ratio": 2, "plane_fwd_u": 2, "plane_fwd_g": 2, "plane_fwd_maxw": 2,
+    "plane_inv_mh_fwd": 4, "plane_inv": 2,
+    "axis1_fwd": 1, "axis1_inv": 1, "axis1_fwd_mul_inv": 2, "axis1_fwd_acc": 1,
+}
+KERNEL_POINTWISE = {  # flops per grid point per instance
+    "plane_inv_mh_fwd": 2, "axis1_fwd_mul_inv": 3, "axis1_fwd_acc": 4,
+}
+
+
+def kernel_flops_per_instance(name, n):
+    return (KERNEL_AXIS_PASSES.get(name, 0) * transform_axis_flops(n)
+            + KERNEL_POINTWISE.get(name, 0) * n ** 3)
+
+
+def apply_flops_per_instance(n, J):
+    """(3J + 6) real 3-D transforms of n^3 points at 2.5 n^3 log2(n^3) flops."""
+    return (3 * J + 6) * 3 * transform_axis_flops(n)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            self.path = "/tmp/lbo_clocks_%d.csv" % os.getpid()
+            f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sms.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(params, g, n, L, omega, seconds):
+    """Time the CPU oracle (single process, as it stands) on the leading
+    instances of the batch for about `seconds`; returns (outputs, apps/s)."""
+    from oracle.linearized import Tables, apply_linearized
+    t0 = time.perf_counter()
+    tab = Tables(n, L, omega, n)
+    outs = []
+    b = 0
+    while b < params.shape[0] and (b < 2 or time.perf_counter() - t0 < seconds):
+        outs.append(apply_linearized(tab, params[b:b + 1], g[b:b + 1])[0])
+        b += 1
+    dt = time.perf_counter() - t0
+    return np.stack(outs), len(outs) / dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2503_09580_gb300 import workloads
+    params, g = workloads.batched_instances(N_GRID, BOX, batch=BATCH, seed=args.seed, noise=1e-3)
+    from oracle.linearized import Tables, apply_linearized
+    tab = Tables(N_GRID, BOX, args.omega, N_GRID)
+    per_step = args.ref_instances
+    for w in range(args.warmup):
+        apply_linearized(tab, params[:1], g[:1])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s = (k * per_step) % BATCH
+        apply_linearized(tab, params[s:s + per_step], g[s:s + per_step])
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "batched L[g], N=32, batch 256 (sampled %d instances per step), "
+                               "per-instance Maxwellians, quartic polynomial + 1e-3 noise" % per_step,
+                   "N": N_GRID, "box": BOX, "vhs_omega": args.omega, "radial_nodes": N_GRID},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d instances per step, numpy FFT form of Algorithm 1" % per_step},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2503_09580_gb300 import lbo, workloads
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    params, g = workloads.batched_instances(N_GRID, BOX, batch=BATCH, seed=args.seed + rank, noise=1e-3)
+    plan = lbo.Plan(N_GRID, BOX, args.omega, N_GRID, precision=args.precision)
+    if args.eps is not None:
+        plan.set("eps", args.eps)
+    if args.moment_fix:
+        plan.set("moment_fix", 1)
+    tp = torch.from_numpy(params).to(dev)
+    tg = torch.from_numpy(g).to(dev)
+    out = torch.empty_like(tg)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan.apply_linearized(tp, tg, out)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    plan.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        plan.apply_linearized(tp, tg, out)
+        launches += plan.last_launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = plan.profile_read()
+    plan.profile(False)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, world)
+    value = world * BATCH / (ms_max * 1e-3)
+
+    # dominant kernel and its roofline
+    name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_ms = tot / max(cnt, 1)
+    flops = kernel_flops_per_instance(name, N_GRID) * BATCH
+    achieved = flops / (per_launch_ms * 1e-3) / 1e12
+    peak = PEAK_TFLOPS[args.precision]
+    share = tot / sum(v[1] for v in prof.values())
+    traffic = NCU_TRAFFIC.get((name, N_GRID, args.precision))
+
+    # end to end through the same C-ABI call with pinned host buffers
+    hp = torch.from_numpy(params).pin_memory()
+    hg = torch.from_numpy(g).pin_memory()
+    ho = torch.empty_like(hg).pin_memory()
+    plan.apply_linearized(hp, hg, ho)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan.apply_linearized(hp, hg, ho)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = max_over_ranks(e2e_s, world)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": "batched L[g], N=32, batch 256 per GPU, per-instance Maxwellians, "
+                               "quartic polynomial + 1e-3 noise",
+                   "N": N_GRID, "box": BOX, "vhs_omega": args.omega, "radial_nodes": N_GRID,
+                   "batch_per_gpu": BATCH, "precision": args.precision,
+                   "eps": args.eps if args.eps is not None else 1e-9,
+                   "parallelism": "replicas (instances sharded, no collective)" if world > 1 else "single GPU",
+                   "l2": "inputs 67 MB + outputs 67 MB + workspace 0.41 GB per step > 129 MB L2"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "derived: flop/clk/SM x 152 SMs x 2070 MHz",
+                     "kernel_share": share, "kernel_ms_per_launch": per_launch_ms,
+                     "apply_flops_per_instance": apply_flops_per_instance(N_GRID, N_GRID)},
+        "e2e": {"value": world * BATCH / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(params.nbytes + g.nbytes), "d2h_bytes_per_step": int(g.nbytes)},
+    }
+    if clk is not None:
+        line["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        got = out.cpu().numpy()
+        ref, cpu_rate = oracle_sample(params, g, N_GRID, BOX, args.omega, args.cpu_seconds)
+        k = ref.shape[0]
+        err = float(np.abs(got[:k] - ref).max() / np.abs(ref).max())
+        line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "first %d instances of the batch, numpy FFT form of "
+                                          "Algorithm 1, single process" % k}
+        line["rel_err_vs_oracle"] = {"value": err, "instances": k,
+                                     "metric": "max|gpu - oracle| / max|oracle| over the sampled instances"}
+    line["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--omega", type=float, default=0.5)
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--moment-fix", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-instances", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -107,6 +107,18 @@ lbo_status lbo_plan_sync(lbo_plan *plan);
 /* Number of kernels the last apply call launched (for accounting). */
 int lbo_plan_last_launches(const lbo_plan *plan);
 
+/* Per-kernel timing.  lbo_plan_profile(plan, 1) clears the counters and
+ * from then on brackets every kernel launch of the plan with CUDA events on
+ * the plan's stream; lbo_plan_profile(plan, 0) stops recording.
+ * lbo_plan_profile_count synchronizes the stream, folds the recorded events
+ * into per-kernel totals and returns the number of kernel names;
+ * lbo_plan_profile_get reads entry i (name is a static string owned by the
+ * library).  LBO_EINVAL for a bad plan or index. */
+lbo_status lbo_plan_profile(lbo_plan *plan, int enable);
+int lbo_plan_profile_count(lbo_plan *plan);
+lbo_status lbo_plan_profile_get(lbo_plan *plan, int i, const char **name, int *launches,
+                                double *total_ms);
+
 /* Free a plan (NULL is allowed). */
 void lbo_plan_destroy(lbo_plan *plan);
 

@@ -100,7 +100,7 @@ static void gram_inverse(int N, double h, double* ginv) {
 lbo_status launch_fixes(lbo_plan* p, double* out, int B, int N, double h, cudaStream_t s, int* launches) {
   Gram5 G;
   gram_inverse(N, h, G.ginv);
-  k_fixes<<<B, 512, 0, s>>>(out, N, h, p->mass_fix, p->moment_fix, G);
+  LBO_LAUNCH(p, "conservation_fix", s, k_fixes, B, 512, 0, out, N, h, p->mass_fix, p->moment_fix, G);
   ++*launches;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LBO_OK : cuda_fail(e, "conservation fix");

@@ -291,44 +291,56 @@ static lbo_status run_linearized(lbo_plan* p, const double* params, const double
   pa.h = 2.0 * p->L / N;
   pa.log_inv_eps = std::log(1.0 / p->eps);
   pa.cutoff = p->cutoff;
+  auto kf_ratio = k_plane_fwd<T, N, PPC, SRC_RATIO>;
+  auto kf_u = k_plane_fwd<T, N, PPC, SRC_U>;
+  auto kf_real = k_plane_fwd<T, N, PPC, SRC_REAL64>;
+  auto kf_maxw = k_plane_fwd<T, N, PPC, SRC_MAXW>;
+  auto ki_mh = k_plane_inv<T, N, PPC, INV_MH_FWD>;
+  auto ki_real = k_plane_inv<T, N, PPC, INV_TO_REAL>;
+  auto ka_fwd = k_axis1<T, N, CW, AX_FWD_STORE>;
+  auto ka_mulc = k_axis1<T, N, CW, AX_FWD_MULC_INV>;
+  auto ka_mult = k_axis1<T, N, CW, AX_FWD_MULT_INV>;
+  auto ka_acc = k_axis1<T, N, CW, AX_FWD_ACC>;
+  auto ka_inv = k_axis1<T, N, CW, AX_INV_STORE>;
+  auto k_comb = k_combine<T, N>;
   int launches = 0;
   // r^ = FFT(r), r = g/M with the cut-off (Algorithm 1, gain term)
-  k_plane_fwd<T, N, PPC, SRC_RATIO><<<gp, blk, sm, s>>>(pa, W1);
+  LBO_LAUNCH(p, "plane_fwd_ratio", s, kf_ratio, gp, blk, sm, pa, W1);
   Axis1Args ax{};
-  k_axis1<T, N, CW, AX_FWD_STORE><<<ga, blk, 0, s>>>(ax, W1, RH);
+  LBO_LAUNCH(p, "axis1_fwd", s, ka_fwd, ga, blk, 0, ax, W1, RH);
   launches += 2;
   for (int j = 0; j < p->J; ++j) {
     // u_j = M^g phit_j ; u^_j = FFT(u_j)
     pa.phit = phit + (size_t)j * n3;
-    k_plane_fwd<T, N, PPC, SRC_U><<<gp, blk, sm, s>>>(pa, W1);
+    LBO_LAUNCH(p, "plane_fwd_u", s, kf_u, gp, blk, sm, pa, W1);
     // psi_j = InvFFT(u^_j r^)
     Axis1Args a1{};
     a1.mulc = RH;
     a1.scale = 1.0 / (double)n3;
-    k_axis1<T, N, CW, AX_FWD_MULC_INV><<<ga, blk, 0, s>>>(a1, W1, W1);
+    LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mulc, ga, blk, 0, a1, W1, W1);
     // psi_j <- M^h psi_j ; psi^_j = FFT(psi_j)
-    k_plane_inv<T, N, PPC, INV_MH_FWD><<<gp, blk, sm, s>>>(pa, W1, nullptr);
+    LBO_LAUNCH(p, "plane_inv_mh_fwd", s, ki_mh, gp, blk, sm, pa, W1, (T*)nullptr);
     // L^+ += phi_j psi^_j
     Axis1Args a2{};
     a2.table = phi + (size_t)j * Q;
     a2.first = j == 0;
-    k_axis1<T, N, CW, AX_FWD_ACC><<<ga, blk, 0, s>>>(a2, W1, LH);
+    LBO_LAUNCH(p, "axis1_fwd_acc", s, ka_acc, ga, blk, 0, a2, W1, LH);
     launches += 4;
   }
   // L+ = InvFFT(L^+)
-  k_axis1<T, N, CW, AX_INV_STORE><<<ga, blk, 0, s>>>(ax, LH, LH);
-  k_plane_inv<T, N, PPC, INV_TO_REAL><<<gp, blk, sm, s>>>(pa, LH, R1);
+  LBO_LAUNCH(p, "axis1_inv", s, ka_inv, ga, blk, 0, ax, LH, LH);
+  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, LH, R1);
   // loss term: u = InvFFT(f^ omega), w = InvFFT(M^ omega)
   Axis1Args a3{};
   a3.table = omg;
-  k_plane_fwd<T, N, PPC, SRC_REAL64><<<gp, blk, sm, s>>>(pa, W1);
-  k_axis1<T, N, CW, AX_FWD_MULT_INV><<<ga, blk, 0, s>>>(a3, W1, W1);
-  k_plane_inv<T, N, PPC, INV_TO_REAL><<<gp, blk, sm, s>>>(pa, W1, R2);
-  k_plane_fwd<T, N, PPC, SRC_MAXW><<<gp, blk, sm, s>>>(pa, W1);
-  k_axis1<T, N, CW, AX_FWD_MULT_INV><<<ga, blk, 0, s>>>(a3, W1, W1);
-  k_plane_inv<T, N, PPC, INV_TO_REAL><<<gp, blk, sm, s>>>(pa, W1, R3);
+  LBO_LAUNCH(p, "plane_fwd_g", s, kf_real, gp, blk, sm, pa, W1);
+  LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
+  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R2);
+  LBO_LAUNCH(p, "plane_fwd_maxw", s, kf_maxw, gp, blk, sm, pa, W1);
+  LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
+  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R3);
   int cb = (int)std::min<size_t>(((size_t)B * n3 + 255) / 256, 152 * 32);
-  k_combine<T, N><<<cb, 256, 0, s>>>(params, g, R1, R2, R3, out, pa.h, B);
+  LBO_LAUNCH(p, "combine", s, k_comb, cb, 256, 0, params, g, R1, R2, R3, out, pa.h, B);
   launches += 9;
   if (p->mass_fix || p->moment_fix) {
     lbo_status st = launch_fixes(p, out, B, N, pa.h, s, &launches);
@@ -501,6 +513,7 @@ void lbo_plan_destroy(lbo_plan* p) {
   if (p->stage_out) cudaFree(p->stage_out);
   if (p->stage_par) cudaFree(p->stage_par);
   free_quadratic(p);
+  free_profile(p);
   delete p;
 }
 

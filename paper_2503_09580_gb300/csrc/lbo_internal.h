@@ -32,6 +32,20 @@ struct lbo_plan {
   // quadratic operator state (hemisphere rule, workspace)
   void* quad = nullptr;
   int last_launches = 0;
+  // per-kernel event timing
+  bool profiling = false;
+  struct ProfEvent {
+    const char* name;
+    cudaEvent_t start, stop;
+  };
+  std::vector<ProfEvent> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  struct ProfTotal {
+    const char* name;
+    int launches;
+    double ms;
+  };
+  std::vector<ProfTotal> prof_totals;
 };
 
 namespace lbo {
@@ -39,4 +53,22 @@ lbo_status cuda_fail(cudaError_t e, const char* where);
 // zero-mode removal and/or FP64 conservation projection of out[B][N^3]
 lbo_status launch_fixes(lbo_plan* p, double* out, int B, int N, double h, cudaStream_t s, int* launches);
 void free_quadratic(lbo_plan* p);
+void free_profile(lbo_plan* p);
+
+// Event bracket around one launch when profiling is on.
+struct ProfScope {
+  lbo_plan* p;
+  const char* name;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(lbo_plan* plan, const char* n, cudaStream_t s);
+  ~ProfScope();
+  cudaStream_t s;
+};
 }  // namespace lbo
+
+// Launch a kernel on stream s of plan p under a profiling scope.
+#define LBO_LAUNCH(p, name, s, kernel, grid, block, smem, ...)      \
+  do {                                                              \
+    lbo::ProfScope _ps((p), (name), (s));                           \
+    kernel<<<(grid), (block), (smem), (s)>>>(__VA_ARGS__);          \
+  } while (0)

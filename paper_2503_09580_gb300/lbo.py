@@ -25,7 +25,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4
 # Every symbol include/lbo.h declares (checked by the tests).
 EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_linearized",
            "lbo_apply_quadratic", "lbo_plan_sync", "lbo_plan_last_launches", "lbo_plan_destroy",
-           "lbo_status_string", "lbo_last_error")
+           "lbo_status_string", "lbo_last_error", "lbo_plan_profile", "lbo_plan_profile_count",
+           "lbo_plan_profile_get")
 
 _lib = None
 
@@ -67,6 +68,13 @@ def load():
     lib.lbo_plan_destroy.restype = None
     lib.lbo_status_string.argtypes = [ip]
     lib.lbo_status_string.restype = ctypes.c_char_p
+    lib.lbo_plan_profile.argtypes = [vp, ip]
+    lib.lbo_plan_profile.restype = ip
+    lib.lbo_plan_profile_count.argtypes = [vp]
+    lib.lbo_plan_profile_count.restype = ip
+    lib.lbo_plan_profile_get.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ip),
+                                         ctypes.POINTER(ctypes.c_double)]
+    lib.lbo_plan_profile_get.restype = ip
     lib.lbo_last_error.argtypes = []
     lib.lbo_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -136,6 +144,22 @@ class Plan:
 
     def sync(self):
         _check(load().lbo_plan_sync(self._h), "lbo_plan_sync")
+
+    def profile(self, enable=True):
+        """Start (clearing counters) or stop per-kernel event timing."""
+        _check(load().lbo_plan_profile(self._h, 1 if enable else 0), "lbo_plan_profile")
+
+    def profile_read(self):
+        """{kernel name: (launches, total ms)} since profiling started."""
+        lib = load()
+        n = lib.lbo_plan_profile_count(self._h)
+        out = {}
+        for i in range(n):
+            name, cnt, ms = ctypes.c_char_p(), ctypes.c_int(), ctypes.c_double()
+            _check(lib.lbo_plan_profile_get(self._h, i, ctypes.byref(name), ctypes.byref(cnt), ctypes.byref(ms)),
+                   "lbo_plan_profile_get")
+            out[name.value.decode()] = (cnt.value, ms.value)
+        return out
 
     @property
     def last_launches(self):
