@@ -119,6 +119,29 @@ int lbo_plan_profile_count(lbo_plan *plan);
 lbo_status lbo_plan_profile_get(lbo_plan *plan, int i, const char **name, int *launches,
                                 double *total_ms);
 
+/* Allocation-free variant of lbo_apply_linearized (the paper has no
+ * counterpart; this is a library facility).  For callers that cannot
+ * allocate device memory when they apply the operator: solvers whose memory
+ * budget is fixed at start-up, real-time loops where cudaMalloc's implicit
+ * synchronisation is not allowed, hosts that forbid allocation after
+ * initialisation.  Same operator, same arguments (device pointers only),
+ * but its scratch comes from one static 64 MiB device array of the library
+ * instead of plan-owned memory, and it calls no allocating routine.
+ * - Rejects (LBO_EINVAL, nothing launched) a batch needing more than
+ *   lbo_noalloc_scratch_bytes(), i.e. batch * lbo_noalloc_bytes_per_instance
+ *   (1.62 MB per instance at N = 32 in FP64, 0.81 MB in FP32), host
+ *   pointers, and a plan whose tables are out of date; LBO_EUNSUPPORTED with
+ *   the mass or moment fix options on.
+ * - All calls share the array: calls that overlap on the GPU race and must
+ *   be serialised.  Nothing in it needs to start at zero.
+ * - The first call on a device (with that device current) looks up the
+ *   array's address and uploads a constant table: make it before any
+ *   stream capture. */
+lbo_status lbo_apply_linearized_noalloc(lbo_plan *plan, const double *maxwellian_params,
+                                        const double *g, double *out, int batch);
+size_t lbo_noalloc_scratch_bytes(void);
+size_t lbo_noalloc_bytes_per_instance(const lbo_plan *plan);
+
 /* Free a plan (NULL is allowed). */
 void lbo_plan_destroy(lbo_plan *plan);
 

@@ -23,6 +23,8 @@ lbo_status cuda_fail(cudaError_t e, const char* where) {
   return LBO_ECUDA;
 }
 
+void set_error_text(const char* msg) { g_last_error = msg; }
+
 // ------------------------------------------------------------ quadrature
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on the
 // three-term recurrence of the Legendre polynomials.

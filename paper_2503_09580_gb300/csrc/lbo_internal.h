@@ -50,6 +50,7 @@ struct lbo_plan {
 
 namespace lbo {
 lbo_status cuda_fail(cudaError_t e, const char* where);
+void set_error_text(const char* msg);
 // zero-mode removal and/or FP64 conservation projection of out[B][N^3]
 lbo_status launch_fixes(lbo_plan* p, double* out, int B, int N, double h, cudaStream_t s, int* launches);
 void free_quadratic(lbo_plan* p);

@@ -26,7 +26,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4
 EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_linearized",
            "lbo_apply_quadratic", "lbo_plan_sync", "lbo_plan_last_launches", "lbo_plan_destroy",
            "lbo_status_string", "lbo_last_error", "lbo_plan_profile", "lbo_plan_profile_count",
-           "lbo_plan_profile_get")
+           "lbo_plan_profile_get", "lbo_apply_linearized_noalloc", "lbo_noalloc_scratch_bytes",
+           "lbo_noalloc_bytes_per_instance")
 
 _lib = None
 
@@ -75,6 +76,12 @@ def load():
     lib.lbo_plan_profile_get.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ip),
                                          ctypes.POINTER(ctypes.c_double)]
     lib.lbo_plan_profile_get.restype = ip
+    lib.lbo_apply_linearized_noalloc.argtypes = [vp, dp, dp, dp, ip]
+    lib.lbo_apply_linearized_noalloc.restype = ip
+    lib.lbo_noalloc_scratch_bytes.argtypes = []
+    lib.lbo_noalloc_scratch_bytes.restype = ctypes.c_size_t
+    lib.lbo_noalloc_bytes_per_instance.argtypes = [vp]
+    lib.lbo_noalloc_bytes_per_instance.restype = ctypes.c_size_t
     lib.lbo_last_error.argtypes = []
     lib.lbo_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -136,6 +143,19 @@ class Plan:
                "lbo_apply_linearized")
         return out
 
+    def apply_linearized_noalloc(self, params, g, out):
+        """lbo_apply_linearized_noalloc: same operator, scratch from the
+        library's static device array (device tensors only)."""
+        batch = int(params.shape[0]) if len(params.shape) == 2 else 1
+        self._stream(params, g, out)
+        _check(load().lbo_apply_linearized_noalloc(self._h, _ptr(params), _ptr(g), _ptr(out), batch),
+               "lbo_apply_linearized_noalloc")
+        return out
+
+    def noalloc_max_batch(self):
+        lib = load()
+        return lib.lbo_noalloc_scratch_bytes() // lib.lbo_noalloc_bytes_per_instance(self._h)
+
     def apply_quadratic(self, f, out):
         batch = int(f.shape[0]) if len(f.shape) == 4 else 1
         self._stream(f, out)
@@ -157,7 +177,8 @@ class Plan:
         for i in range(n):
             name, cnt, ms = ctypes.c_char_p(), ctypes.c_int(), ctypes.c_double()
             _check(lib.lbo_plan_profile_get(self._h, i, ctypes.byref(name), ctypes.byref(cnt), ctypes.byref(ms)),
-                   "lbo_plan_profile_get")
+                   "lbo_plan_profile_get", "lbo_apply_linearized_noalloc", "lbo_noalloc_scratch_bytes",
+           "lbo_noalloc_bytes_per_instance")
             out[name.value.decode()] = (cnt.value, ms.value)
         return out
 
