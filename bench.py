@@ -38,7 +38,7 @@ PEAK_TFLOPS = {"fp64": 4 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12,
                "fp32": 256 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12}
 # DRAM bytes (read + write) per launch of the dominant kernel at the benchmark
 # workload, from ncu (profiles/*.md); None when not captured for this build.
-NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456}
+NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456, ("f32_gain", 32, "fp32"): 254556000}
 
 
 def transform_axis_flops(n):
@@ -57,9 +57,18 @@ KERNEL_AXIS_PASSES = {
 KERNEL_POINTWISE = {  # flops per grid point per instance
     "plane_inv_mh_fwd": 2, "axis1_fwd_mul_inv": 3, "axis1_fwd_acc": 4,
 }
+# Fused FP32 kernels (N = 32): whole real 3-D transforms per instance.
+#   head: r^ (1);  gain: 3 per radial node (u^_j, psi_j, psi^_j) plus the
+#   loss term's 4 (g, M forward and back);  tail: the inverse of L^+ (1).
+FUSED_TRANSFORMS = {"f32_head": lambda J: 1, "f32_gain": lambda J: 3 * J + 4, "f32_tail": lambda J: 1}
+FUSED_POINTWISE = {"f32_gain": lambda J: 12 * J}
 
 
-def kernel_flops_per_instance(name, n):
+def kernel_flops_per_instance(name, n, J=None):
+    J = n if J is None else J
+    if name in FUSED_TRANSFORMS:
+        return (FUSED_TRANSFORMS[name](J) * 3 * transform_axis_flops(n)
+                + FUSED_POINTWISE.get(name, lambda J: 0)(J) * n ** 3)
     return (KERNEL_AXIS_PASSES.get(name, 0) * transform_axis_flops(n)
             + KERNEL_POINTWISE.get(name, 0) * n ** 3)
 
@@ -275,6 +284,7 @@ def run_ours(args, world, rank, local):
     }
     if clk is not None:
         line["clocks"] = clk
+    ref = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         got = out.cpu().numpy()
         ref, cpu_rate = oracle_sample(params, g, N_GRID, BOX, args.omega, args.cpu_seconds)
@@ -285,6 +295,27 @@ def run_ours(args, world, rank, local):
                                           "Algorithm 1, single process" % k}
         line["rel_err_vs_oracle"] = {"value": err, "instances": k,
                                      "metric": "max|gpu - oracle| / max|oracle| over the sampled instances"}
+    if args.precision != "fp64" and not args.no_fp64_leg:
+        # the plain FP64 GPU path on the same inputs, same timing method
+        p64 = lbo.Plan(N_GRID, BOX, args.omega, N_GRID, precision="fp64")
+        out64 = torch.empty_like(tg)
+        for _ in range(2):
+            p64.apply_linearized(tp, tg, out64)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            p64.apply_linearized(tp, tg, out64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(f0.elapsed_time(f1) / args.fp64_steps, world)
+        line["fp64_plain"] = {"value": world * BATCH / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                              "speedup_of_value": value / (world * BATCH / (ms64 * 1e-3))}
+        if ref is not None:
+            k = ref.shape[0]
+            got64 = out64.cpu().numpy()[:k]
+            line["fp64_plain"]["rel_err_vs_oracle"] = float(np.abs(got64 - ref).max() / np.abs(ref).max())
+        p64.close()
     line["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -297,7 +328,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--omega", type=float, default=0.5)
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--moment-fix", action="store_true")

@@ -66,7 +66,11 @@ typedef enum {
   LBO_OPT_MOMENT_FIX = 5,  /* 1: FP64 projection of the output onto zero mass,
                               momentum and energy (least squares on the grid) */
   LBO_OPT_HEMISPHERE_P = 6,/* hemisphere rule order p: M = 2 p^2 points (4)   */
-  LBO_OPT_PRECISION = 7    /* lbo_precision                                   */
+  LBO_OPT_PRECISION = 7,   /* lbo_precision                                   */
+  LBO_OPT_KERNEL = 8,      /* 0: fastest built kernel set for (N, precision)
+                              (default), 1: the generic plane/axis kernels    */
+  LBO_OPT_JGROUPS = 9      /* radial nodes per CTA of the fused FP32 kernel are
+                              J / jgroups; 0 (default): chosen from the batch */
 } lbo_option;
 
 /* Create a plan for N^3 grids on [-box, box]^3, VHS exponent vhs_omega in

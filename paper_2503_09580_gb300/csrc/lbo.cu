@@ -169,16 +169,13 @@ static lbo_status build_tables(lbo_plan* p) {
 }
 
 // ------------------------------------------------------------ workspace
-static lbo_status ensure_workspace(lbo_plan* p, int batch) {
-  if (batch <= p->ws_batch && p->ws) return LBO_OK;
+static lbo_status ensure_ws_bytes(lbo_plan* p, size_t bytes) {
+  if (p->ws && bytes <= p->ws_bytes) return LBO_OK;
   if (p->ws) {
     cudaFree(p->ws);
     p->ws = nullptr;
-    p->ws_batch = 0;
+    p->ws_bytes = 0;
   }
-  const size_t N = p->N, H = N * N * (N / 2 + 1), n3 = N * N * N;
-  // sized for FP64 (FP32 uses the same buffers)
-  size_t bytes = (size_t)batch * (3 * H * 16 + 3 * n3 * 8);
   cudaError_t e = cudaMalloc(&p->ws, bytes);
   if (e != cudaSuccess) {
     p->ws = nullptr;
@@ -186,8 +183,14 @@ static lbo_status ensure_workspace(lbo_plan* p, int batch) {
     g_last_error = "workspace allocation";
     return LBO_ENOMEM;
   }
-  p->ws_batch = batch;
+  p->ws_bytes = bytes;
   return LBO_OK;
+}
+
+static lbo_status ensure_workspace(lbo_plan* p, int batch) {
+  const size_t N = p->N, H = N * N * (N / 2 + 1), n3 = N * N * N;
+  // generic path: 3 half spectra + 3 real fields per instance, sized for FP64
+  return ensure_ws_bytes(p, (size_t)batch * (3 * H * 16 + 3 * n3 * 8));
 }
 
 static lbo_status ensure_stage(lbo_plan* p, size_t in_doubles, size_t out_doubles, size_t par_doubles) {
@@ -341,8 +344,7 @@ static lbo_status run_linearized(lbo_plan* p, const double* params, const double
   LBO_LAUNCH(p, "plane_fwd_maxw", s, kf_maxw, gp, blk, sm, pa, W1);
   LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
   LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R3);
-  int cb = (int)std::min<size_t>(((size_t)B * n3 + 255) / 256, 152 * 32);
-  LBO_LAUNCH(p, "combine", s, k_comb, cb, 256, 0, params, g, R1, R2, R3, out, pa.h, B);
+  LBO_LAUNCH(p, "combine", s, k_comb, dim3(N, B), 256, 0, params, g, R1, R2, R3, out, pa.h, pa.log_inv_eps);
   launches += 9;
   if (p->mass_fix || p->moment_fix) {
     lbo_status st = launch_fixes(p, out, B, N, pa.h, s, &launches);
@@ -448,6 +450,14 @@ lbo_status lbo_plan_set(lbo_plan* p, lbo_option key, double v) {
       if (v != 0.0 && v != 1.0) return LBO_EINVAL;
       p->precision = (int)v;
       break;
+    case LBO_OPT_KERNEL:
+      if (v != 0.0 && v != 1.0) return LBO_EINVAL;
+      p->kernel_choice = (int)v;
+      break;
+    case LBO_OPT_JGROUPS:
+      if (!(v >= 0.0 && v <= 64.0)) return LBO_EINVAL;
+      p->jgroups = (int)v;
+      break;
     default: return LBO_EINVAL;
   }
   return LBO_OK;
@@ -487,8 +497,19 @@ lbo_status lbo_apply_linearized(lbo_plan* p, const double* params, const double*
     dg = p->stage_in;
     dout = p->stage_out;
   }
-  st = p->precision == LBO_PREC_FP64 ? dispatch_lin<double>(p, dp, dg, dout, batch)
-                                     : dispatch_lin<float>(p, dp, dg, dout, batch);
+  if (p->precision == LBO_PREC_FP32 && p->N == 32 && p->kernel_choice == 0) {
+    int G = p->jgroups > 0 ? std::min(p->jgroups, p->J) : std::min(fused32_default_groups(batch), p->J);
+    st = ensure_ws_bytes(p, fused32_workspace_bytes(batch, G));
+    if (st != LBO_OK) return st;
+    int launches = 0;
+    st = run_linearized_fused32(p, dp, dg, dout, batch, p->ws, G, &launches);
+    if (st == LBO_OK && (p->mass_fix || p->moment_fix))
+      st = launch_fixes(p, dout, batch, p->N, 2.0 * p->L / p->N, p->stream, &launches);
+    p->last_launches = launches;
+  } else {
+    st = p->precision == LBO_PREC_FP64 ? dispatch_lin<double>(p, dp, dg, dout, batch)
+                                       : dispatch_lin<float>(p, dp, dg, dout, batch);
+  }
   if (st != LBO_OK) return st;
   if (!dev) {
     cudaError_t e = cudaMemcpyAsync(out, p->stage_out, sizeof(double) * n3 * batch, cudaMemcpyDefault, p->stream);

@@ -11,6 +11,7 @@ struct lbo_plan {
   int N = 0, J = 0, device = 0;
   double L = 0, omega = 0, R = 0, C = 0, eps = 1e-9;
   int cutoff = 1, mass_fix = 0, moment_fix = 0, hemi_p = 4, precision = 0;
+  int kernel_choice = 0, jgroups = 0;
   cudaStream_t stream = nullptr;
   bool tables_dirty = false;
   // radial rule (host copy)
@@ -25,7 +26,7 @@ struct lbo_plan {
   double* d_dummy_params = nullptr;
   // workspace of the generic path
   void* ws = nullptr;
-  int ws_batch = 0;
+  size_t ws_bytes = 0;
   // staging for host-pointer calls
   double *stage_in = nullptr, *stage_out = nullptr, *stage_par = nullptr;
   size_t stage_in_cap = 0, stage_out_cap = 0, stage_par_cap = 0;
@@ -54,6 +55,11 @@ void set_error_text(const char* msg);
 // zero-mode removal and/or FP64 conservation projection of out[B][N^3]
 lbo_status launch_fixes(lbo_plan* p, double* out, int B, int N, double h, cudaStream_t s, int* launches);
 void free_quadratic(lbo_plan* p);
+// fused FP32 path for N = 32 (lin_fused32.cu)
+size_t fused32_workspace_bytes(int B, int G);
+int fused32_default_groups(int B);
+lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const double* g, double* out, int B,
+                                  void* ws, int G, int* launches);
 void free_profile(lbo_plan* p);
 
 // Event bracket around one launch when profiling is on.

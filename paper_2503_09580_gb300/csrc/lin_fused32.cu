@@ -1,0 +1,448 @@
+// Fused FP32 path of Algorithm 1 for N = 32.
+//
+// One CTA holds the half spectrum of one instance (32 x 32 x 17 complex
+// FP32 = 139 KB of shared memory) and runs the gain-term loop for a group
+// of radial nodes j entirely on chip.  Every axis pass is one in-register
+// 32-point FFT per thread (544 threads = one pencil each):
+//   rows   (i1, q):  two real rows 2q, 2q+1 packed as one complex row,
+//                    transformed along i3 and split into two half rows;
+//   axis 2 (i1, k3): pencil along i2;   axis 1 (i2, k3): pencil along i1.
+// Shared-memory index of (i1, i2, k3) = i1*544 + i2*17 + k3; the packed
+// row pair (i1, q) occupies the 34 slots of half rows 2q and 2q+1.
+// Spectra are in natural frequency order (the register FFT has no
+// permutation cost), so r^ and the partial sums use the same index.
+//
+// Kernels per application of a batch: k_f32_head (r^ = FFT(r) / N^3),
+// k_f32_gain (grid = (j-groups + 1) x batch: partial L^+ per group, and the
+// loss term written into out by the extra block), k_f32_tail (sum of the
+// partials, inverse transform, added to out in FP64).
+#include <cmath>
+
+#include "lbo_internal.h"
+#include "lin_kernels.cuh"
+
+namespace lbo {
+namespace {
+
+constexpr int F_N = 32, F_HC = 17, F_ROW = 544, F_H = 32 * 544, F_THREADS = 544;
+
+// x <- DFT_32(x) (forward: exp(-2 pi i nk/32); inverse: conjugate, unnormalised)
+template <bool INV>
+__device__ __forceinline__ void fft32(cpx<float> (&x)[32]) {
+  cpx<float> y[32];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    cpx<float> v[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) v[n2] = x[n1 + 4 * n2];
+    dft8<float, INV>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      if (n1 == 0 || k2 == 0) y[n1 * 8 + k2] = v[k2];
+      else y[n1 * 8 + k2] = INV ? cmulc(v[k2], tw64<float>(2 * n1 * k2)) : cmul(v[k2], tw64<float>(2 * n1 * k2));
+    }
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) {
+    cpx<float> w[4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) w[n1] = y[n1 * 8 + k2];
+    dft4<float, INV>(w);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) x[k2 + 8 * k1] = w[k1];
+  }
+}
+
+// Forward row pass tail: z = FFT(x_a + i x_b) along i3 -> two half rows at dst[0..16], dst[17..33].
+__device__ __forceinline__ void split_store(const cpx<float> (&z)[32], cpx<float>* dst) {
+#pragma unroll
+  for (int k = 0; k <= 16; ++k) {
+    cpx<float> z1 = z[k], z2 = conjc(z[(32 - k) & 31]);
+    cpx<float> d = z1 - z2;
+    dst[k] = cscale(z1 + z2, 0.5f);
+    dst[17 + k] = make_c(0.5f * d.y, -0.5f * d.x);
+  }
+}
+
+// Inverse row pass head: two half rows -> packed z = X_a + i X_b on k = 0..31.
+__device__ __forceinline__ void load_merge(const cpx<float>* src, cpx<float> (&z)[32]) {
+#pragma unroll
+  for (int k = 0; k <= 16; ++k) {
+    cpx<float> a = src[k], b = src[17 + k];
+    if (k == 0 || k == 16) {
+      z[k] = make_c(a.x, b.x);
+    } else {
+      z[k] = make_c(a.x - b.y, a.y + b.x);
+      z[32 - k] = make_c(a.x + b.y, b.x - a.y);  // conj(a) + i conj(b)
+    }
+  }
+}
+
+__device__ __forceinline__ int ksq(int k1, int k2, int k3) {
+  int a = k1 < 16 ? k1 : k1 - 32, b = k2 < 16 ? k2 : k2 - 32;
+  return a * a + b * b + k3 * k3;
+}
+
+// In-place axis pass over pencils of V: AXIS 2 -> pencil (i1, k3), stride 17;
+// AXIS 1 -> pencil (i2, k3), stride 544.
+template <int AXIS, bool INV>
+__device__ __forceinline__ void axis_pass(cpx<float>* V) {
+  const int t = threadIdx.x;
+  const int a = t / F_HC, k3 = t % F_HC;
+  cpx<float>* base = AXIS == 2 ? V + a * F_ROW + k3 : V + a * F_HC + k3;
+  constexpr int st = AXIS == 2 ? F_HC : F_ROW;
+  cpx<float> x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) x[i] = base[i * st];
+  fft32<INV>(x);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) base[i * st] = x[i];
+}
+
+struct FusedArgs {
+  const double* params;
+  const double* g;
+  const float* phit;   // [J][N^3] cyclic displacement order
+  const float* phi;    // [J][QMAX], pre-scaled by N^-3
+  const float* omega;  // [QMAX], pre-scaled by N^-3
+  cpx<float>* rhat;    // [B][F_H], pre-scaled by N^-3
+  cpx<float>* part;    // [G][B][F_H] partial L^+ per j-group
+  double* out;         // [B][N^3]
+  double h, log_inv_eps;
+  int cutoff, J, G, B, Q;
+};
+
+// Per-instance FP64 tables of a CTA.  With a_d(i) = (v_i - u_d)^2 rounded as
+// in the definition, |v-u|^2 = (a_1 + a_2) + a_3 exactly as the oracle forms
+// it; M = em_1 em_2 em_3 and 1/M = ei_1 ei_2 ei_3 (axis 1 carries the
+// prefactors).  The cut-off of Eq. (3.9), fl(|v-u|^2 / (2 theta)) > thr, is
+// monotone in |v-u|^2, so it is replaced by the exact equivalent
+// |v-u|^2 >= dstar, dstar the smallest double that passes the test.
+struct PrepTables {
+  double a[3 * 32], em[3 * 32], ei[3 * 32];
+  double dstar;
+};
+
+__device__ __forceinline__ void fill_prep(PrepTables& T, const InstanceParams& q, double h, double log_inv_eps) {
+  const int t = threadIdx.x;
+  if (t < 96) {
+    const int d = t / 32, i = t % 32;
+    const double ud = d == 0 ? q.u1 : (d == 1 ? q.u2 : q.u3);
+    const double dv = __dsub_rn(__dmul_rn((double)(i - 16), h), ud);
+    const double a2 = __dmul_rn(dv, dv);
+    T.a[t] = a2;
+    double em = exp(-a2 / (2.0 * q.theta)), ei = exp(a2 / (2.0 * q.theta));
+    if (d == 0) {
+      const double pref = q.rho * pow(2.0 * 3.141592653589793 * q.theta, -1.5);
+      em *= pref;
+      ei /= pref;
+    }
+    T.em[t] = em;
+    T.ei[t] = ei;
+  } else if (t == 96) {
+    const double twoth = __dmul_rn(2.0, q.theta);
+    const double thr = __dsub_rn(log_inv_eps, __dmul_rn(1.5, log(__dmul_rn(__dmul_rn(2.0, 3.141592653589793), q.theta))));
+    double x = __dmul_rn(thr, twoth);
+    for (int it = 0; it < 64 && __ddiv_rn(x, twoth) > thr; ++it) x = nextafter(x, -1e308);
+    for (int it = 0; it < 64 && !(__ddiv_rn(x, twoth) > thr); ++it) x = nextafter(x, 1e308);
+    T.dstar = x;
+  }
+  __syncthreads();
+}
+
+// rows (i1, q) of a real source -> forward half spectrum in V (all three axes
+// except axis 1, which the caller fuses with its pointwise stage).
+template <typename Src>
+__device__ __forceinline__ void rows_forward(cpx<float>* V, Src src) {
+  const int t = threadIdx.x;
+  if (t < 512) {
+    const int i1 = t >> 4, qq = t & 15;
+    cpx<float> z[32];
+#pragma unroll
+    for (int i3 = 0; i3 < 32; ++i3) z[i3] = src(i1, qq, i3);
+    fft32<false>(z);
+    split_store(z, V + i1 * F_ROW + qq * 34);
+  }
+  __syncthreads();
+  axis_pass<2, false>(V);
+  __syncthreads();
+}
+
+// r^ = FFT(r) / N^3, r = g/M with the cut-off of Eq. (3.9).
+__global__ void __launch_bounds__(F_THREADS, 1) k_f32_head(FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cpx<float>* V = (cpx<float>*)smem;
+  __shared__ PrepTables T;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const InstanceParams q = load_params(a.params, b);
+  fill_prep(T, q, a.h, a.log_inv_eps);
+  const double* gb = a.g + (size_t)b * 32768;
+  const bool cut = a.cutoff != 0;
+  rows_forward(V, [&](int i1, int qq, int i3) {
+    float v[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int i2 = 2 * qq + r;
+      const double d2 = __dadd_rn(__dadd_rn(T.a[i1], T.a[32 + i2]), T.a[64 + i3]);
+      const double val = gb[(i1 * 32 + i2) * 32 + i3] * ((T.ei[i1] * T.ei[32 + i2]) * T.ei[64 + i3]);
+      v[r] = (cut && d2 >= T.dstar) ? 0.f : (float)val;
+    }
+    return make_c(v[0], v[1]);
+  });
+  const int i2 = t / F_HC, k3 = t % F_HC;
+  cpx<float>* base = V + i2 * F_HC + k3;
+  cpx<float> x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+  fft32<false>(x);
+  cpx<float>* dst = a.rhat + (size_t)b * F_H + i2 * F_HC + k3;
+  const float s = 1.0f / 32768.0f;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) dst[i * F_ROW] = cscale(x[i], s);
+}
+
+// Loss term of one instance: out = -InvFFT(FFT(g) omega) M - InvFFT(FFT(M) omega) g.
+__device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T, int b) {
+  const int t = threadIdx.x;
+  const double* gb = a.g + (size_t)b * 32768;
+  double* ob = a.out + (size_t)b * 32768;
+  for (int pass = 0; pass < 2; ++pass) {
+    rows_forward(V, [&](int i1, int qq, int i3) {
+      if (pass == 0)
+        return make_c((float)gb[(i1 * 32 + 2 * qq) * 32 + i3], (float)gb[(i1 * 32 + 2 * qq + 1) * 32 + i3]);
+      const double m13 = T.em[i1] * T.em[64 + i3];
+      return make_c((float)(m13 * T.em[32 + 2 * qq]), (float)(m13 * T.em[32 + 2 * qq + 1]));
+    });
+    {
+      const int i2 = t / F_HC, k3 = t % F_HC;
+      cpx<float>* base = V + i2 * F_HC + k3;
+      cpx<float> x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+      fft32<false>(x);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = cscale(x[i], __ldg(a.omega + ksq(i, i2, k3)));
+      fft32<true>(x);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) base[i * F_ROW] = x[i];
+    }
+    __syncthreads();
+    axis_pass<2, true>(V);
+    __syncthreads();
+    if (t < 512) {
+      const int i1 = t >> 4, qq = t & 15;
+      cpx<float> z[32];
+      load_merge(V + i1 * F_ROW + qq * 34, z);
+      fft32<true>(z);
+      double* o0 = ob + (i1 * 32 + 2 * qq) * 32;
+      const double* g0 = gb + (i1 * 32 + 2 * qq) * 32;
+#pragma unroll 4
+      for (int i3 = 0; i3 < 32; ++i3) {
+        if (pass == 0) {  // -u M
+          const double m13 = T.em[i1] * T.em[64 + i3];
+          o0[i3] = -(double)z[i3].x * (m13 * T.em[32 + 2 * qq]);
+          o0[32 + i3] = -(double)z[i3].y * (m13 * T.em[32 + 2 * qq + 1]);
+        } else {  // -w g
+          o0[i3] -= (double)z[i3].x * g0[i3];
+          o0[32 + i3] -= (double)z[i3].y * g0[32 + i3];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// grid (G + 1, B): blocks x < G run the gain term for their group of radial
+// nodes (partial L^+ = sum_j phi_j FFT(M^h InvFFT(u^_j r^))); block x = G
+// writes the loss term of the instance into out.
+__global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cpx<float>* V = (cpx<float>*)smem;
+  __shared__ float mg[F_N], mh[3 * F_N];
+  __shared__ PrepTables T;
+  const int grp = blockIdx.x, b = blockIdx.y, t = threadIdx.x;
+  const InstanceParams q = load_params(a.params, b);
+  if (grp == a.G) {
+    fill_prep(T, q, a.h, a.log_inv_eps);
+    loss_term(a, V, T, b);
+    return;
+  }
+  const int j0 = (a.J * grp) / a.G, j1 = (a.J * (grp + 1)) / a.G;
+  if (t < F_N) {
+    // exp(-|d|^2/theta) for the cyclic displacement d of M^g
+    double d = (double)(t < 16 ? t : t - 32) * a.h;
+    mg[t] = (float)exp(-(d * d) / q.theta);
+  } else if (t < 4 * F_N) {
+    int u = t - F_N, dd = u / F_N, i = u % F_N;
+    double ud = dd == 0 ? q.u1 : (dd == 1 ? q.u2 : q.u3);
+    double v = (double)(i - 16) * a.h - ud;
+    double e = exp(-(v * v) / q.theta);
+    if (dd == 0) e *= q.rho * pow(3.141592653589793 * q.theta, -1.5);
+    mh[u] = (float)e;
+  }
+  const float pref_g = (float)(q.rho * pow(3.141592653589793 * q.theta, -1.5));
+  __syncthreads();
+  const cpx<float>* rh = a.rhat + (size_t)b * F_H;
+  cpx<float>* acc = a.part + ((size_t)grp * a.B + b) * F_H;
+  for (int j = j0; j < j1; ++j) {
+    // u_j = M^g phit_j (cyclic displacement order) -> forward rows, axis 2
+    if (t < 512) {
+      const int i1 = t >> 4, qq = t & 15;
+      const float* ph = a.phit + (size_t)j * 32768 + (i1 * F_N + 2 * qq) * F_N;
+      const float m1 = pref_g * mg[i1];
+      const float ma = m1 * mg[2 * qq], mb = m1 * mg[2 * qq + 1];
+      cpx<float> z[32];
+#pragma unroll
+      for (int i3 = 0; i3 < 32; i3 += 4) {
+        float4 p0 = *(const float4*)(ph + i3);
+        float4 p1 = *(const float4*)(ph + F_N + i3);
+        z[i3 + 0] = make_c(ma * mg[i3 + 0] * p0.x, mb * mg[i3 + 0] * p1.x);
+        z[i3 + 1] = make_c(ma * mg[i3 + 1] * p0.y, mb * mg[i3 + 1] * p1.y);
+        z[i3 + 2] = make_c(ma * mg[i3 + 2] * p0.z, mb * mg[i3 + 2] * p1.z);
+        z[i3 + 3] = make_c(ma * mg[i3 + 3] * p0.w, mb * mg[i3 + 3] * p1.w);
+      }
+      fft32<false>(z);
+      split_store(z, V + i1 * F_ROW + qq * 34);
+    }
+    __syncthreads();
+    axis_pass<2, false>(V);
+    __syncthreads();
+    {  // axis 1: forward, x r^ (scaled), inverse
+      const int i2 = t / F_HC, k3 = t % F_HC;
+      cpx<float>* base = V + i2 * F_HC + k3;
+      const cpx<float>* rr = rh + i2 * F_HC + k3;
+      cpx<float> x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+      fft32<false>(x);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = cmul(x[i], rr[i * F_ROW]);
+      fft32<true>(x);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) base[i * F_ROW] = x[i];
+    }
+    __syncthreads();
+    axis_pass<2, true>(V);
+    __syncthreads();
+    if (t < 512) {  // rows: inverse, x M^h, forward
+      const int i1 = t >> 4, qq = t & 15;
+      cpx<float>* row = V + i1 * F_ROW + qq * 34;
+      cpx<float> z[32];
+      load_merge(row, z);
+      fft32<true>(z);
+      const float m1 = mh[i1], ma = m1 * mh[F_N + 2 * qq], mb = m1 * mh[F_N + 2 * qq + 1];
+#pragma unroll
+      for (int i3 = 0; i3 < 32; ++i3) {
+        const float m3 = mh[2 * F_N + i3];
+        z[i3] = make_c(z[i3].x * (ma * m3), z[i3].y * (mb * m3));
+      }
+      fft32<false>(z);
+      split_store(z, row);
+    }
+    __syncthreads();
+    axis_pass<2, false>(V);
+    __syncthreads();
+    {  // axis 1 forward, accumulate phi_j(|k|^2) psi^_j
+      const int i2 = t / F_HC, k3 = t % F_HC;
+      cpx<float>* base = V + i2 * F_HC + k3;
+      cpx<float>* ac = acc + i2 * F_HC + k3;
+      const float* ph = a.phi + (size_t)j * a.Q;
+      cpx<float> x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+      fft32<false>(x);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        cpx<float> v = cscale(x[i], __ldg(ph + ksq(i, i2, k3)));
+        ac[i * F_ROW] = j == j0 ? v : ac[i * F_ROW] + v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// out += InvFFT(sum over groups of the partial L^+).
+__global__ void __launch_bounds__(F_THREADS, 1) k_f32_tail(FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cpx<float>* V = (cpx<float>*)smem;
+  const int b = blockIdx.x, t = threadIdx.x;
+  {
+    const int i2 = t / F_HC, k3 = t % F_HC;
+    cpx<float> x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] = make_c(0.f, 0.f);
+    for (int gi = 0; gi < a.G; ++gi) {
+      const cpx<float>* src = a.part + ((size_t)gi * a.B + b) * F_H + i2 * F_HC + k3;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = x[i] + src[i * F_ROW];
+    }
+    fft32<true>(x);
+    cpx<float>* base = V + i2 * F_HC + k3;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) base[i * F_ROW] = x[i];
+  }
+  __syncthreads();
+  axis_pass<2, true>(V);
+  __syncthreads();
+  if (t < 512) {
+    const int i1 = t >> 4, qq = t & 15;
+    cpx<float> z[32];
+    load_merge(V + i1 * F_ROW + qq * 34, z);
+    fft32<true>(z);
+    double* o0 = a.out + (size_t)b * 32768 + (i1 * 32 + 2 * qq) * 32;
+#pragma unroll 4
+    for (int i3 = 0; i3 < 32; ++i3) {
+      o0[i3] += (double)z[i3].x;
+      o0[32 + i3] += (double)z[i3].y;
+    }
+  }
+}
+
+}  // namespace
+
+size_t fused32_workspace_bytes(int B, int G) { return (size_t)B * F_H * 8 * (1 + (size_t)G); }
+
+int fused32_default_groups(int B) {
+  // enough CTAs to fill 152 SMs several times over, at most 8 groups
+  int g = (4 * 152 + B - 1) / B;
+  return g < 1 ? 1 : (g > 8 ? 8 : g);
+}
+
+lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const double* g, double* out, int B,
+                                  void* ws, int G, int* launches) {
+  cudaError_t e = upload_twiddles();
+  if (e != cudaSuccess) return cuda_fail(e, "fused32 twiddles");
+  const size_t sm = sizeof(cpx<float>) * F_H;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_f32_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_f32_gain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_f32_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  FusedArgs a{};
+  a.params = params;
+  a.g = g;
+  a.phit = p->d_phit32;
+  a.phi = p->d_phi32;
+  a.omega = p->d_omega32;
+  a.rhat = (cpx<float>*)ws;
+  a.part = a.rhat + (size_t)B * F_H;
+  a.out = out;
+  a.h = 2.0 * p->L / F_N;
+  a.log_inv_eps = std::log(1.0 / p->eps);
+  a.cutoff = p->cutoff;
+  a.J = p->J;
+  a.G = G;
+  a.B = B;
+  a.Q = 3 * 16 * 16 + 1;
+  cudaStream_t s = p->stream;
+  LBO_LAUNCH(p, "f32_head", s, k_f32_head, B, F_THREADS, sm, a);
+  LBO_LAUNCH(p, "f32_gain", s, k_f32_gain, dim3(G + 1, B), F_THREADS, sm, a);
+  LBO_LAUNCH(p, "f32_tail", s, k_f32_tail, B, F_THREADS, sm, a);
+  *launches += 3;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "fused32 launch");
+}
+
+}  // namespace lbo

@@ -71,25 +71,48 @@ __device__ __forceinline__ double maxwellian(double d2, const InstanceParams& q)
   return q.rho * pow(2.0 * 3.141592653589793 * q.theta, -1.5) * exp(-d2 / (2.0 * q.theta));
 }
 
+// Per-instance separable Maxwellian tables, filled once per CTA:
+//   em[d*N + i] = exp(-(v_i - u_d)^2 / (2 theta)), axis 0 times the
+//   prefactor rho (2 pi theta)^{-3/2}, so M(v) = em[i1] em[N+i2] em[2N+i3];
+//   *thr = ln(1/eps) - 1.5 ln(2 pi theta), the cut-off threshold of Eq. (3.9).
+template <int N>
+__device__ __forceinline__ void fill_maxwellian_tables(double* em, double* thr, const InstanceParams& q, double h,
+                                                       double log_inv_eps) {
+  for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) {
+    int d = t / N, i = t % N;
+    double ud = d == 0 ? q.u1 : (d == 1 ? q.u2 : q.u3);
+    double v = (double)(i - N / 2) * h - ud;
+    double e = exp(-(v * v) / (2.0 * q.theta));
+    if (d == 0) e *= q.rho * pow(2.0 * 3.141592653589793 * q.theta, -1.5);
+    em[t] = e;
+  }
+  if (threadIdx.x == 0)
+    *thr = __dsub_rn(log_inv_eps, __dmul_rn(1.5, log(__dmul_rn(__dmul_rn(2.0, 3.141592653589793), q.theta))));
+  __syncthreads();
+}
+
 template <typename T, int N, int SRC>
 __device__ __forceinline__ T plane_source(const PlaneArgs& a, const InstanceParams& q, int b, int i1, int i2, int i3,
-                                          const double* ex1) {
+                                          const double* ex1, const double* em, double thr) {
   if constexpr (SRC == SRC_U) {
     // M^g(d) phit_j(d), d = cyclic displacement; ex1[i] = exp(-d_i^2/theta)
     const T* ph = (const T*)a.phit;
-    double mg = ex1[N + i1] * ex1[i2] * ex1[i3];  // ex1[N] holds the prefactor-folded axis-1 table
+    double mg = ex1[N + i1] * ex1[i2] * ex1[i3];  // ex1[N..2N) carries the prefactor
     return (T)(mg * (double)ph[(i1 * N + i2) * N + i3]);
   } else {
     size_t idx = (((size_t)b * N + i1) * N + i2) * N + i3;
     if constexpr (SRC == SRC_REAL64) {
       return (T)a.g[idx];
     } else {
-      double d2 = dist2(i1, i2, i3, N, a.h, q);
+      double M = em[i1] * em[N + i2] * em[2 * N + i3];
       if constexpr (SRC == SRC_MAXW) {
-        return (T)maxwellian(d2, q);
+        return (T)M;
       } else {  // SRC_RATIO
-        if (a.cutoff && cut_point(d2, q.theta, a.log_inv_eps)) return (T)0;
-        return (T)(a.g[idx] / maxwellian(d2, q));
+        if (a.cutoff) {
+          double d2 = dist2(i1, i2, i3, N, a.h, q);
+          if (__ddiv_rn(d2, __dmul_rn(2.0, q.theta)) > thr) return (T)0;
+        }
+        return (T)(a.g[idx] / M);
       }
     }
   }
@@ -210,14 +233,17 @@ __global__ void __launch_bounds__(256) k_plane_fwd(PlaneArgs a, cpx<T>* __restri
   cpx<T>* A = (cpx<T>*)smem_raw;
   cpx<T>* B = A + PlaneSmem<T, N, PPC>::A_ELEMS;
   __shared__ double ex[2 * N];
+  __shared__ double em[3 * N];
+  __shared__ double thr;
   const int b = blockIdx.y, i1_0 = blockIdx.x * PPC;
   const InstanceParams q = load_params(a.params, b);
   if constexpr (SRC == SRC_U) fill_mg_tables<N>(ex, q, a.h);
+  if constexpr (SRC == SRC_RATIO || SRC == SRC_MAXW) fill_maxwellian_tables<N>(em, &thr, q, a.h, a.log_inv_eps);
   for (int t = threadIdx.x; t < PPC * (N / 2) * N; t += blockDim.x) {
     int i3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
     int i1 = i1_0 + pp;
-    T x0 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq, i3, ex);
-    T x1 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq + 1, i3, ex);
+    T x0 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq, i3, ex, em, thr);
+    T x1 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq + 1, i3, ex, em, thr);
     A[(pp * (N / 2) + qq) * N + i3] = make_c(x0, x1);
   }
   __syncthreads();
@@ -325,20 +351,25 @@ __global__ void __launch_bounds__(256) k_axis1(Axis1Args a, const cpx<T>* __rest
   }
 }
 
-// out = L+ - uu M - ww g  (FP64), optional zero-mode removal done separately.
+// out = L+ - uu M - ww g  (FP64), one CTA per (i1-plane, instance);
+// zero-mode removal / conservation projection are done separately.
 template <typename T, int N>
-__global__ void k_combine(const double* __restrict__ params, const double* __restrict__ g, const T* __restrict__ Lp,
-                          const T* __restrict__ uu, const T* __restrict__ ww, double* __restrict__ out, double h,
-                          int B) {
-  const size_t n3 = (size_t)N * N * N;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)B * n3;
-       t += (size_t)gridDim.x * blockDim.x) {
-    int b = (int)(t / n3);
-    int r = (int)(t % n3);
-    int i3 = r % N, i2 = (r / N) % N, i1 = r / (N * N);
-    InstanceParams q = load_params(params, b);
-    double M = maxwellian(dist2(i1, i2, i3, N, h, q), q);
-    out[t] = (double)Lp[t] - (double)uu[t] * M - (double)ww[t] * g[t];
+__global__ void __launch_bounds__(256) k_combine(const double* __restrict__ params, const double* __restrict__ g,
+                                                 const T* __restrict__ Lp, const T* __restrict__ uu,
+                                                 const T* __restrict__ ww, double* __restrict__ out, double h,
+                                                 double log_inv_eps) {
+  __shared__ double em[3 * N];
+  __shared__ double thr;
+  const int b = blockIdx.y, i1 = blockIdx.x;
+  const InstanceParams q = load_params(params, b);
+  fill_maxwellian_tables<N>(em, &thr, q, h, log_inv_eps);
+  const double m1 = em[i1];
+  const size_t base = ((size_t)b * N + i1) * N * N;
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    int i2 = t / N, i3 = t % N;
+    double M = m1 * em[N + i2] * em[2 * N + i3];
+    size_t o = base + t;
+    out[o] = (double)Lp[o] - (double)uu[o] * M - (double)ww[o] * g[o];
   }
 }
 

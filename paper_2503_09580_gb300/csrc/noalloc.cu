@@ -159,8 +159,7 @@ lbo_status run(const lbo_plan* p, const double* params, const double* g, double*
   kf_maxw<<<gp, blk, sm, s>>>(pa, W1);
   k_axis1<T, N, CW, AX_FWD_MULT_INV><<<ga, blk, 0, s>>>(a3, W1, W1);
   ki_real<<<gp, blk, sm, s>>>(pa, W1, R3);
-  int cb = (int)(((size_t)B * n3 + 255) / 256 < 152 * 32 ? ((size_t)B * n3 + 255) / 256 : 152 * 32);
-  k_combine<T, N><<<cb, 256, 0, s>>>(params, g, R1, R2, R3, out, pa.h, B);
+  k_combine<T, N><<<dim3(N, B), 256, 0, s>>>(params, g, R1, R2, R3, out, pa.h, pa.log_inv_eps);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LBO_OK : cuda_fail(e, "noalloc launch");
 }

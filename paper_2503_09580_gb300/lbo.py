@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "liblbo.so")
 
 LBO_OPT = {"R": 0, "C": 1, "eps": 2, "cutoff": 3, "mass_fix": 4, "moment_fix": 5,
-           "hemisphere_p": 6, "precision": 7}
+           "hemisphere_p": 6, "precision": 7, "kernel": 8, "jgroups": 9}
 PRECISION = {"fp64": 0, "fp32": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "not converged",
           5: "Krylov breakdown", 6: "non-finite value", 7: "unsupported configuration"}
@@ -177,8 +177,7 @@ class Plan:
         for i in range(n):
             name, cnt, ms = ctypes.c_char_p(), ctypes.c_int(), ctypes.c_double()
             _check(lib.lbo_plan_profile_get(self._h, i, ctypes.byref(name), ctypes.byref(cnt), ctypes.byref(ms)),
-                   "lbo_plan_profile_get", "lbo_apply_linearized_noalloc", "lbo_noalloc_scratch_bytes",
-           "lbo_noalloc_bytes_per_instance")
+                   "lbo_plan_profile_get")
             out[name.value.decode()] = (cnt.value, ms.value)
         return out
 

@@ -49,3 +49,18 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.lbo_apply_linearized(None, None, None, None, 1) == 1
     assert lib.lbo_plan_sync(None) == 1
     lib.lbo_plan_destroy(None)
+
+
+def test_binding_marshals_profile_and_noalloc_calls(lib):
+    """The binding's wrappers call each entry point with its own argument
+    list (no GPU needed: a NULL plan is rejected before any launch)."""
+    plan = lbo.Plan.__new__(lbo.Plan)
+    plan._h = ctypes.c_void_p()
+    with pytest.raises(lbo.LboError):
+        plan.profile(True)
+    assert lib.lbo_plan_profile_count(None) == 0
+    name, cnt, ms = ctypes.c_char_p(), ctypes.c_int(), ctypes.c_double()
+    assert lib.lbo_plan_profile_get(None, 0, ctypes.byref(name), ctypes.byref(cnt), ctypes.byref(ms)) == 1
+    assert lib.lbo_apply_linearized_noalloc(None, None, None, None, 1) == 1
+    assert lib.lbo_noalloc_scratch_bytes() == 64 << 20
+    plan._h = None

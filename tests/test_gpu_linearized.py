@@ -168,3 +168,40 @@ def test_fp32_rounding_bound_noise_free():
     bound = 2.0 ** -24 * ratio_max(params, g, n, L)
     print("fp32 noise-free rel err %.3e (bound %.3e)" % (err, bound))
     assert err <= bound
+
+
+@pytest.mark.parametrize("jgroups", [1, 3, 8])
+def test_fused_fp32_n32_against_oracle_and_generic(jgroups):
+    """Fused FP32 kernel (one CTA per instance and group of radial nodes):
+    same u32 * max|r| bound against the FP64 oracle, and agreement with the
+    generic FP32 kernels to FP32 rounding."""
+    n, L = 32, 8.0
+    params, g = workloads.batched_instances(n, L, batch=5, seed=12, noise=0.0)
+    fused = lbo.Plan(n, L, 0.74, n, precision="fp32", jgroups=jgroups)
+    generic = lbo.Plan(n, L, 0.74, n, precision="fp32", kernel=1)
+    a = run(fused, params, g)
+    b = run(generic, params, g)
+    assert fused.last_launches == 3
+    ref = apply_linearized(tables(n, L, 0.74, n), params, g)
+    bound = 2.0 ** -24 * ratio_max(params, g, n, L)
+    err = relerr(a, ref)
+    print("fused fp32 rel err %.3e (bound %.3e), vs generic fp32 %.3e" % (err, bound, relerr(a, b)))
+    assert err <= bound
+    assert relerr(a, b) <= bound
+
+
+def test_fused_fp32_full_batch_and_moment_fix():
+    n, L = 32, 8.0
+    params, g = workloads.batched_instances(n, L, batch=256, seed=0, noise=0.0)
+    plan = lbo.Plan(n, L, 0.5, n, precision="fp32", moment_fix=1)
+    got = run(plan, params, g)
+    tab = tables(n, L, 0.5, n)
+    bound = 2.0 ** -24 * ratio_max(params[[0, 128, 255]], g[[0, 128, 255]], n, L)
+    for b in (0, 128, 255):
+        ref = apply_linearized(tab, params[b:b + 1], g[b:b + 1])
+        proj = grid.to_centred(conservation_projection(grid.to_cyclic(ref[0]), n, L))
+        assert relerr(got[b], proj) <= 2 * bound
+        # the projection makes mass, momentum and energy vanish in FP64
+        from oracle.moments import invariant_moments
+        m = invariant_moments(grid.to_cyclic(got[b]), n, L)
+        assert np.abs(m).max() <= 1e-12 * (2 * L / n) ** 3 * np.abs(got[b]).sum()
