@@ -519,6 +519,40 @@ lbo_status lbo_apply_linearized(lbo_plan* p, const double* params, const double*
   return LBO_OK;
 }
 
+lbo_status lbo_apply_quadratic(lbo_plan* p, const double* f, double* out, int batch) {
+  if (!p || batch < 0) return LBO_EINVAL;
+  if (batch == 0) {
+    p->last_launches = 0;
+    return LBO_OK;
+  }
+  if (!f || !out || out == f) return LBO_EINVAL;
+  if (p->tables_dirty) {
+    lbo_status st = build_tables(p);
+    if (st != LBO_OK) return st;
+  }
+  const size_t n3 = (size_t)p->N * p->N * p->N;
+  const bool dev = is_device_ptr(f) && is_device_ptr(out);
+  const double* df = f;
+  double* dout = out;
+  lbo_status st;
+  if (!dev) {
+    st = ensure_stage(p, (size_t)batch * n3, (size_t)batch * n3, 5);
+    if (st != LBO_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(p->stage_in, f, sizeof(double) * n3 * batch, cudaMemcpyDefault, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    df = p->stage_in;
+    dout = p->stage_out;
+  }
+  st = apply_quadratic_device(p, df, dout, batch);
+  if (st != LBO_OK) return st;
+  if (!dev) {
+    cudaError_t e = cudaMemcpyAsync(out, p->stage_out, sizeof(double) * n3 * batch, cudaMemcpyDefault, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  }
+  return LBO_OK;
+}
+
 lbo_status lbo_plan_sync(lbo_plan* p) {
   if (!p) return LBO_EINVAL;
   cudaError_t e = cudaStreamSynchronize(p->stream);

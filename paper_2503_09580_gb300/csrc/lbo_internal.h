@@ -55,6 +55,8 @@ void set_error_text(const char* msg);
 // zero-mode removal and/or FP64 conservation projection of out[B][N^3]
 lbo_status launch_fixes(lbo_plan* p, double* out, int B, int N, double h, cudaStream_t s, int* launches);
 void free_quadratic(lbo_plan* p);
+void gauss_legendre(int J, std::vector<double>& x, std::vector<double>& w);
+lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int B);
 // fused FP32 path for N = 32 (lin_fused32.cu)
 size_t fused32_workspace_bytes(int B, int G);
 int fused32_default_groups(int B);

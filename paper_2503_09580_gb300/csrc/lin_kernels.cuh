@@ -36,13 +36,15 @@ enum PlaneSrc {
   SRC_RATIO = 0,   // r = g / M, 0 where the cut-off of Eq. (3.9) applies
   SRC_REAL64 = 1,  // a double field (the ABI input g)
   SRC_MAXW = 2,    // the Maxwellian M
-  SRC_U = 3        // u_j = M^g phit_j, cyclic displacement order
+  SRC_U = 3,       // u_j = M^g phit_j, cyclic displacement order
+  SRC_REALT = 4    // a field of the transform precision T (a.src)
 };
 
 struct PlaneArgs {
   const double* params;  // [B][5]
   const double* g;       // [B][N^3] (SRC_RATIO / SRC_REAL64)
   const void* phit;      // [N^3] of T (SRC_U): phit_j, cyclic order
+  const void* src;       // [B][N^3] of T (SRC_REALT)
   double h;              // grid spacing
   double log_inv_eps;    // ln(1/eps)
   int cutoff;            // apply Eq. (3.9)
@@ -101,7 +103,9 @@ __device__ __forceinline__ T plane_source(const PlaneArgs& a, const InstancePara
     return (T)(mg * (double)ph[(i1 * N + i2) * N + i3]);
   } else {
     size_t idx = (((size_t)b * N + i1) * N + i2) * N + i3;
-    if constexpr (SRC == SRC_REAL64) {
+    if constexpr (SRC == SRC_REALT) {
+      return ((const T*)a.src)[idx];
+    } else if constexpr (SRC == SRC_REAL64) {
       return (T)a.g[idx];
     } else {
       double M = em[i1] * em[N + i2] * em[2 * N + i3];

@@ -1,0 +1,95 @@
+"""Parity of the CUDA quadratic operator Q(f,f) (M-point form, Eq. (2.14))
+with the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import grid
+from oracle.linearized import Tables
+from oracle.quadratic import apply_quadratic
+from oracle.quadrature import hemisphere_rule
+from paper_2503_09580_gb300 import lbo, workloads
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def run_q(plan, f):
+    tf = torch.from_numpy(f).to(DEV)
+    out = torch.empty_like(tf)
+    plan.apply_quadratic(tf, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def maxwell_batch(n, L, params):
+    a = workloads.velocity_axis(n, L)
+    out = []
+    for rho, u1, u2, u3, th in params:
+        d2 = (a[:, None, None] - u1) ** 2 + (a[None, :, None] - u2) ** 2 + (a[None, None, :] - u3) ** 2
+        out.append(rho * (2 * np.pi * th) ** -1.5 * np.exp(-d2 / (2 * th)))
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("n,p,omega", [(16, 4, 0.5), (16, 2, 1.0), (32, 1, 0.74)])
+def test_quadratic_fp64_matches_oracle(n, p, omega):
+    L = 8.0
+    params, g = workloads.batched_instances(n, L, batch=2, seed=31, noise=0.0)
+    f = maxwell_batch(n, L, params) + 0.3 * g
+    plan = lbo.Plan(n, L, omega, n, hemisphere_p=p)
+    got = run_q(plan, f)
+    sig, w = hemisphere_rule(p)
+    ref = apply_quadratic(Tables(n, L, omega, n), f, sig, w)
+    assert relerr(got, ref) <= 1e-12
+
+
+def test_quadratic_mass_fix_and_host_path():
+    n, L = 16, 8.0
+    params, g = workloads.batched_instances(n, L, batch=2, seed=32, noise=0.0)
+    f = maxwell_batch(n, L, params) + 0.2 * g
+    plan = lbo.Plan(n, L, 0.5, n, hemisphere_p=2, mass_fix=1)
+    got = run_q(plan, f)
+    sig, w = hemisphere_rule(2)
+    ref = apply_quadratic(Tables(n, L, 0.5, n), f, sig, w, mass_fix="zero_mode")
+    assert relerr(got, ref) <= 1e-12
+    host = np.empty_like(f)
+    plan.apply_quadratic(f, host)
+    assert np.array_equal(host, got)
+
+
+def test_quadratic_maxwellian_equilibrium_and_fp32():
+    n, L = 32, 8.0
+    params = np.array([[1.0, 0.2, 0.0, -0.1, 1.0], [1.5, -0.3, 0.1, 0.2, 0.8]])
+    M = maxwell_batch(n, L, params)
+    plan = lbo.Plan(n, L, 0.74, n, hemisphere_p=2)
+    q = run_q(plan, M)
+    for b in range(2):
+        loss = params[b, 0] * M[b]  # scale of Q^- for this instance
+        assert np.abs(q[b]).max() < 1e-5 * np.abs(loss).max()  # grid resolution at theta = 0.8
+    plan32 = lbo.Plan(n, L, 0.74, n, hemisphere_p=2, precision="fp32")
+    q32 = run_q(plan32, M)
+    f = M + 0.1 * workloads.batched_instances(n, L, batch=2, seed=3, noise=0.0)[1]
+    a, b = run_q(plan32, f), run_q(plan, f)
+    assert relerr(a, b) <= 2.0 ** -24 * 64
+    assert np.abs(q32).max() < 1e-5 * np.abs(M).max()
+
+
+def test_quadratic_bkw_rate_on_gpu():
+    """d f_BKW/dt = Q(f_BKW, f_BKW), Maxwell molecules, K = 1 - exp(-t/6)."""
+    n, L, K = 32, 8.0, 0.8
+    a = workloads.velocity_axis(n, L)
+    v2 = a[:, None, None] ** 2 + a[None, :, None] ** 2 + a[None, None, :] ** 2
+
+    def bkw(K):
+        return ((2 * np.pi * K) ** -1.5 * np.exp(-v2 / (2 * K))
+                * ((5 * K - 3) / (2 * K) + (1 - K) / (2 * K * K) * v2))
+    dK = 1e-5
+    dfdt = (bkw(K + dK) - bkw(K - dK)) / (2 * dK) * (1 - K) / 6
+    plan = lbo.Plan(n, L, 1.0, n, hemisphere_p=3)
+    q = run_q(plan, bkw(K)[None])[0]
+    assert np.abs(q - dfdt).max() < 2e-4 * np.abs(dfdt).max()
