@@ -123,6 +123,86 @@ int lbo_plan_profile_count(lbo_plan *plan);
 lbo_status lbo_plan_profile_get(lbo_plan *plan, int i, const char **name, int *launches,
                                 double *total_ms);
 
+/* ------------------------------------------------------------------------
+ * Steady-state / implicit solver (Sec. 5 and the supplement).
+ *
+ * LBO_PROBLEM_SLAB: the 1-D steady problem v1 d_x f = Q(f,f)/Kn on
+ *   (x_left, x_right), nx cells, first-order upwind finite volumes, Maxwell
+ *   diffuse walls (Eq. (5.2)) through ghost cells, total mass C (Eq. (5.3)).
+ *   State f: nx*N^3 doubles [cell][i1][i2][i3] (device pointer).
+ *   Residual R(f) = v1^+ D^- f + v1^- D^+ f - Q(f_j,f_j)/Kn.
+ *   Modified Newton (Eqs. (5.4), (5.6)): solve
+ *     A g = v1^+ D^- g + v1^- D^+ g - L_j[g_j]/Kn = R
+ *   with L_j linearised about the local Maxwellian of f_j, then f <- f - g.
+ *   The mass mode is handled by the bordered operator A g + e m(g) with
+ *   e = f/m(f), m(g) = dx h^3 sum g, and right-hand side R + e (m(f) - C).
+ * LBO_PROBLEM_HOMOGENEOUS: backward Euler for df/dt = Q(f,f) on a batch of
+ *   nx independent instances: F(f) = f - f_prev - dt Q(f,f), Newton with
+ *   (I - dt L_M) g = F(f), M the Maxwellian of f.
+ * The linear system is solved by restarted flexible GMRES with FP64 Arnoldi
+ * (classical Gram-Schmidt, two passes), FP64 residuals and norms, and a right
+ * preconditioner: none, the upwind sweep of the source iteration (Eq. (5.7),
+ * nu_j = rho_j), or the sweep plus a learned macroscopic correction
+ * (lbo_solver_set_network).  The FP64 true residual of the linear system
+ * is recomputed after the solve and reported.
+ * Norms are the discrete L2 norm sqrt(dx h^3 sum r^2) of Sec. 5.3 (dx = 1
+ * for the homogeneous problem).
+ * ------------------------------------------------------------------------ */
+typedef struct lbo_solver lbo_solver;
+
+typedef enum { LBO_PROBLEM_SLAB = 0, LBO_PROBLEM_HOMOGENEOUS = 1 } lbo_problem_kind;
+typedef enum { LBO_PRECOND_NONE = 0, LBO_PRECOND_SWEEP = 1, LBO_PRECOND_LEARNED = 2 } lbo_precond;
+typedef enum { LBO_WALL_FLUX_ANALYTIC = 0, LBO_WALL_FLUX_DISCRETE = 1 } lbo_wall_flux;
+
+typedef struct {
+  int kind;               /* lbo_problem_kind                                  */
+  int nx;                 /* cells (SLAB) or instances (HOMOGENEOUS)           */
+  double x_left, x_right; /* SLAB domain                                       */
+  double kn;              /* Knudsen number (SLAB)                             */
+  double wall_left[4];    /* theta, u1, u2, u3 of the left wall (u1 must be 0)  */
+  double wall_right[4];
+  double total_mass;      /* C of Eq. (5.3) (SLAB)                             */
+  int wall_flux;          /* lbo_wall_flux: wall density from the analytic
+                             half-range flux sqrt(theta/2pi) (Eq. (5.2), the
+                             default) or from its grid sum                     */
+  double dt;              /* HOMOGENEOUS time step                             */
+  double krylov_rtol;     /* stop when |r| <= max(rtol |r0|, atol)             */
+  double krylov_atol;
+  int krylov_restart;     /* m of GMRES(m), 1..200                             */
+  int krylov_maxit;       /* total inner iterations cap                        */
+  int precond;            /* lbo_precond                                       */
+} lbo_problem;
+
+typedef struct {
+  double residual_norm;    /* |R(f)| (or |F(f)|) at the input state             */
+  double rhs_norm;         /* |right-hand side of the linear system|            */
+  double linear_residual;  /* FP64 true |rhs - A g| after the solve             */
+  int krylov_iterations;
+  int restarts;
+  int status;              /* lbo_status of the inner solve (LBO_ENOTCONV if the
+                              cap was hit; the step is still applied)          */
+  double ms_residual;      /* time in the nonlinear residual (Q evaluations)    */
+  double ms_linear;        /* time in the linear solve                          */
+} lbo_newton_stats;
+
+/* Create a solver on top of a plan (the plan supplies N, the box, the
+ * collision kernel, the precision of L and Q and the hemisphere rule).
+ * Allocates the Krylov basis ((restart+1) * nx * N^3 doubles and as many
+ * preconditioned vectors).  LBO_EINVAL for inconsistent problem data. */
+lbo_status lbo_solver_create(const lbo_problem *problem, lbo_plan *plan, lbo_solver **out);
+
+/* One modified Newton step in place on the device state f (nx*N^3).
+ * f_prev: the previous time level (HOMOGENEOUS; ignored for SLAB).
+ * stats may be NULL. */
+lbo_status lbo_newton_step(lbo_solver *solver, double *f, const double *f_prev, lbo_newton_stats *stats);
+
+/* Evaluate the nonlinear residual R(f) (SLAB) or F(f) (HOMOGENEOUS) into
+ * out (device, nx*N^3) and return its norm in *norm (may be NULL). */
+lbo_status lbo_solver_residual(lbo_solver *solver, const double *f, const double *f_prev, double *out,
+                               double *norm);
+
+void lbo_solver_destroy(lbo_solver *solver);
+
 /* Allocation-free variant of lbo_apply_linearized (the paper has no
  * counterpart; this is a library facility).  For callers that cannot
  * allocate device memory when they apply the operator: solvers whose memory

@@ -1,0 +1,177 @@
+"""Steady 1-D Boltzmann problem and its modified Newton step (Sec. 5 and the
+supplement's fully discrete scheme).  Oracle: test infrastructure only.
+
+State f[j, i1, i2, i3]: cell j = 1..nx (array index j-1), velocity on the
+collocation grid in *centred* order (the library's layout).  Cell centres
+x_j = x_L + (j - 1/2) dx.
+
+Discrete residual (supplement, upwind finite volume):
+  R_j = v1^+ (f_j - f_{j-1})/dx + v1^- (f_{j+1} - f_j)/dx - Q(f_j, f_j)/Kn
+with ghost cells from Maxwell's diffuse walls, Eq. (5.2):
+  f_0     = W_L(v) * ( -sqrt(2 pi/theta_L) h^3 sum_v v1^- f_1 ),
+  f_{nx+1} = W_R(v) * (  sqrt(2 pi/theta_R) h^3 sum_v v1^+ f_nx ),
+  W(v) = (2 pi theta)^{-3/2} exp(-|v - u_w|^2 / (2 theta)).
+(Reading: the paper's rho_R formula uses f(x_L); the right wall uses f(x_R).)
+Modified Newton, Eqs. (5.4), (5.6): solve
+  v1^+ (g_j - g_{j-1})/dx + v1^- (g_{j+1} - g_j)/dx - L_j[g_j]/Kn = R_j
+with the same linear wall map for g's ghost cells, L_j linearised about
+the local Maxwellian of f_j; then f <- f - g.  The linear system
+is singular along the mass mode (every residual has ~zero total mass:
+diffuse walls carry no net flux and Q conserves mass), so the total-mass
+condition dx h^3 sum f = C, Eq. (5.3), is imposed inside the solve
+(reading): the bordered operator
+  A'(g) = A g + e m(g),  e = f / m(f),  m(g) = dx h^3 sum g,
+is solved with right-hand side R + e (m(f) - C), which gives A g = R and
+m(f - g) = C whenever R has zero mass.
+The inner solve uses scipy's GMRES (a library routine) on the exact
+operator; the paper's own inner solver is the source iteration, Eq. (5.7),
+whose upwind sweep is ``sweep`` below.
+"""
+import numpy as np
+
+from . import grid
+from .linearized import Tables, collision_operator
+from .moments import moments
+from .quadratic import quadratic_operator
+
+
+class Slab:
+    def __init__(self, n, L, omega, J, nx, x_left=-0.5, x_right=0.5, kn=1.0,
+                 wall_left=(1.0, 0.0, 0.0, 0.0), wall_right=(2.0, 0.0, 0.0, 0.0),
+                 hemisphere=None, wall_flux="analytic", q_mass_fix=None):
+        self.n, self.L, self.nx, self.kn = n, L, nx, kn
+        self.tab = Tables(n, L, omega, J)
+        self.dx = (x_right - x_left) / nx
+        self.xc = x_left + (np.arange(nx) + 0.5) * self.dx
+        self.h = grid.spacing(n, L)
+        a = (np.arange(n) - n // 2) * self.h
+        self.v1 = np.broadcast_to(a[:, None, None], (n, n, n))
+        self.vp = np.maximum(self.v1, 0.0)
+        self.vm = np.minimum(self.v1, 0.0)
+        self.sig, self.wm = hemisphere
+        v2 = a[None, :, None]
+        v3 = a[None, None, :]
+
+        def wall_shape(w):
+            th, u1, u2, u3 = w
+            return (2 * np.pi * th) ** -1.5 * np.exp(
+                -((a[:, None, None] - u1) ** 2 + (v2 - u2) ** 2 + (v3 - u3) ** 2) / (2 * th))
+        self.WL, self.WR = wall_shape(wall_left), wall_shape(wall_right)
+        self.thL, self.thR = wall_left[0], wall_right[0]
+        # wall-density factor per unit outgoing flux: sqrt(2 pi / theta) is the
+        # inverse half-range flux of the unit Maxwellian (the paper's formula);
+        # 'discrete' uses the grid sum instead, so the discrete net wall flux
+        # vanishes exactly
+        if wall_flux == "analytic":
+            self.kL, self.kR = np.sqrt(2 * np.pi / self.thL), np.sqrt(2 * np.pi / self.thR)
+        else:
+            h3 = self.h ** 3
+            self.kL = 1.0 / (h3 * (self.vp * self.WL).sum())
+            self.kR = 1.0 / (h3 * (-self.vm * self.WR).sum())
+        self.q_mass_fix = q_mass_fix
+
+    def ghosts(self, f):
+        h3 = self.h ** 3
+        sL = -self.kL * h3 * (self.vm * f[0]).sum()
+        sR = self.kR * h3 * (self.vp * f[-1]).sum()
+        return sL * self.WL, sR * self.WR
+
+    def transport(self, f):
+        """v1^+ (f_j - f_{j-1})/dx + v1^- (f_{j+1} - f_j)/dx with ghost cells."""
+        g0, g1 = self.ghosts(f)
+        ext = np.concatenate([g0[None], f, g1[None]], axis=0)
+        return (self.vp * (ext[1:-1] - ext[:-2]) + self.vm * (ext[2:] - ext[1:-1])) / self.dx
+
+    def collision_q(self, f):
+        return np.stack([grid.to_centred(quadratic_operator(self.tab, grid.to_cyclic(f[j]), self.sig, self.wm,
+                                                            mass_fix=self.q_mass_fix))
+                         for j in range(self.nx)])
+
+    def residual(self, f):
+        return self.transport(f) - self.collision_q(f) / self.kn
+
+    def local_params(self, f):
+        out = np.empty((self.nx, 5))
+        for j in range(self.nx):
+            rho, u, th, _, _ = moments(grid.to_cyclic(f[j]), self.n, self.L)
+            out[j] = (rho, u[0], u[1], u[2], th)
+        return out
+
+    def linear_operator(self, params):
+        """g -> transport(g) - L_j[g_j]/Kn with L_j about params[j]."""
+        def apply(g):
+            Lg = np.stack([grid.to_centred(collision_operator(
+                self.tab, p[0], p[1:4], p[4], grid.to_cyclic(g[j]))) for j, p in enumerate(params)])
+            return self.transport(g) - Lg / self.kn
+        return apply
+
+    def norm(self, r):
+        """Discrete L2 norm sqrt(dx h^3 sum r^2), Sec. 5.3."""
+        return np.sqrt(self.dx * self.h ** 3 * (r * r).sum())
+
+    def mass(self, f):
+        return self.dx * self.h ** 3 * f.sum()
+
+    def sweep(self, r, nu):
+        """Upwind sweep of the source iteration, Eq. (5.7):
+        (v1^+ D^- + v1^- D^+ + nu_j/Kn) z = r, ghost values of z taken as 0."""
+        z = np.zeros_like(r)
+        c = np.abs(self.v1) / self.dx
+        pos, neg = self.v1 > 0, self.v1 < 0
+        zero = ~(pos | neg)
+        prev = np.zeros(r.shape[1:])
+        for j in range(self.nx):
+            d = c + nu[j] / self.kn
+            zj = np.where(pos, (r[j] + c * prev) / d, 0.0)
+            z[j][pos] = zj[pos]
+            prev = np.where(pos, zj, 0.0)
+        prev = np.zeros(r.shape[1:])
+        for j in range(self.nx - 1, -1, -1):
+            d = c + nu[j] / self.kn
+            zj = np.where(neg, (r[j] + c * prev) / d, 0.0)
+            z[j][neg] = zj[neg]
+            prev = np.where(neg, zj, 0.0)
+        for j in range(self.nx):
+            z[j][zero] = r[j][zero] * self.kn / nu[j]
+        return z
+
+    def bordered_operator(self, params, f):
+        """A'(g) = A g + e m(g) with e = f / m(f)."""
+        A = self.linear_operator(params)
+        e = f / self.mass(f)
+
+        def apply(g):
+            return A(g) + e * self.mass(g)
+        return apply
+
+    def newton_step(self, f, total_mass, rtol=1e-10, restart=60, maxiter=400):
+        """One modified Newton step: returns (f_new, g, |R(f)|).  GMRES on the
+        bordered operator, preconditioned by the upwind sweep with
+        nu_j = rho_j (Eq. (5.7))."""
+        from scipy.sparse.linalg import LinearOperator, gmres
+        R = self.residual(f)
+        params = self.local_params(f)
+        A = self.bordered_operator(params, f)
+        rhs = R + (f / self.mass(f)) * (self.mass(f) - total_mass)
+        shape = f.shape
+        n = R.size
+        op = LinearOperator((n, n), matvec=lambda x: A(x.reshape(shape)).ravel(), dtype=np.float64)
+        pre = LinearOperator((n, n), matvec=lambda x: self.sweep(x.reshape(shape), params[:, 0]).ravel(),
+                             dtype=np.float64)
+        x, info = gmres(op, rhs.ravel(), rtol=rtol, atol=0.0, restart=restart, maxiter=maxiter, M=pre)
+        g = x.reshape(shape)
+        return f - g, g, self.norm(R)
+
+
+def initial_state(slab, total_mass=1.0, theta_left=1.0, theta_right=2.0):
+    """Linear temperature profile between the walls, Eq. (S.initial):
+    f_j = C/(x_R - x_L) (2 pi theta_j)^{-3/2} exp(-|v|^2/(2 theta_j))."""
+    a = (np.arange(slab.n) - slab.n // 2) * slab.h
+    v2 = a[:, None, None] ** 2 + a[None, :, None] ** 2 + a[None, None, :] ** 2
+    width = slab.nx * slab.dx
+    out = []
+    for x in slab.xc:
+        w = (x - slab.xc[0] + 0.5 * slab.dx) / width
+        th = (1 - w) * theta_left + w * theta_right
+        out.append(total_mass / width * (2 * np.pi * th) ** -1.5 * np.exp(-v2 / (2 * th)))
+    return np.stack(out)

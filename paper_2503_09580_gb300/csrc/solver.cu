@@ -1,0 +1,613 @@
+// Modified Newton / flexible GMRES solver (Sec. 5 and the supplement's fully
+// discrete scheme) on top of a plan's L[g] and Q(f,f).  Host-side Arnoldi on
+// small matrices; every long-vector operation is an FP64 kernel here.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lbo_internal.h"
+
+struct lbo_solver {
+  lbo_problem pb;
+  lbo_plan* plan = nullptr;
+  int N = 0, nx = 0, m = 0;
+  size_t n3 = 0, len = 0;
+  double h = 0, dx = 1, wnorm = 1, kL = 0, kR = 0;
+  double *V = nullptr, *Z = nullptr;           // Krylov basis (m+1) and preconditioned vectors (m)
+  double *w = nullptr, *Lv = nullptr, *rhs = nullptr, *x = nullptr, *evec = nullptr, *Qf = nullptr;
+  double *params = nullptr, *nu = nullptr, *WL = nullptr, *WR = nullptr;
+  double *part = nullptr, *res = nullptr;     // reduction partials, small results
+  double* host = nullptr;                     // pinned small results
+  // learned preconditioner (lbo_solver_set_network)
+  float* net = nullptr;
+  int net_hidden = 0;
+  double *feat = nullptr, *corr = nullptr;
+  double net_scale_in = 1, net_scale_out = 1;
+};
+
+namespace lbo {
+namespace {
+
+constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+constexpr int DOT_TILE = 8;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+// part[b*K + k] = sum over this block's elements of V_k[e] * y[e], k < K
+__global__ void __launch_bounds__(RED_THREADS) k_dots(const double* __restrict__ V, size_t ld, int K,
+                                                      const double* __restrict__ y, size_t len,
+                                                      double* __restrict__ part) {
+  __shared__ double sh[32];
+  for (int k0 = 0; k0 < K; k0 += DOT_TILE) {
+    double acc[DOT_TILE];
+#pragma unroll
+    for (int t = 0; t < DOT_TILE; ++t) acc[t] = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x) {
+      const double ye = y[e];
+#pragma unroll
+      for (int t = 0; t < DOT_TILE; ++t)
+        if (k0 + t < K) acc[t] += V[(size_t)(k0 + t) * ld + e] * ye;
+    }
+#pragma unroll
+    for (int t = 0; t < DOT_TILE; ++t) {
+      double s = block_sum(acc[t], sh);
+      if (threadIdx.x == 0 && k0 + t < K) part[blockIdx.x * K + k0 + t] = s;
+    }
+  }
+}
+
+// out[k] = sum_b part[b*K + k] (fixed order: deterministic)
+__global__ void k_reduce_parts(const double* __restrict__ part, int nb, int K, double* __restrict__ out) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double s = 0;
+    for (int b = 0; b < nb; ++b) s += part[b * K + k];
+    out[k] = s;
+  }
+}
+
+// y -= sum_k c[k] V_k
+__global__ void k_sub_combination(double* __restrict__ y, const double* __restrict__ V, size_t ld, int K,
+                                  const double* __restrict__ c, size_t len) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int k = 0; k < K; ++k) s += c[k] * V[(size_t)k * ld + e];
+    y[e] -= s;
+  }
+}
+
+// y = a x + b y  (a, b on the host)
+__global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b, size_t len) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = a * x[e] + b * y[e];
+}
+
+// y = x * (num / *den)  (scalar on the device)
+__global__ void k_scale_by(double* __restrict__ y, const double* __restrict__ x, double num,
+                           const double* __restrict__ den, size_t len) {
+  const double s = num / *den;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = x[e] * s;
+}
+
+// local Maxwellian parameters of each cell: rho, u, theta (Sec. 2.1), FP64
+__global__ void __launch_bounds__(512) k_cell_moments(const double* __restrict__ f, double* __restrict__ params,
+                                                     double* __restrict__ nu, int N, double h) {
+  __shared__ double sh[32];
+  __shared__ double mom[4];
+  const size_t n3 = (size_t)N * N * N;
+  const double* x = f + blockIdx.x * n3;
+  double m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+  for (size_t t = threadIdx.x; t < n3; t += blockDim.x) {
+    const int i3 = (int)(t % N), i2 = (int)((t / N) % N), i1 = (int)(t / ((size_t)N * N));
+    const double y = x[t];
+    m0 += y;
+    m1 += (i1 - N / 2) * h * y;
+    m2 += (i2 - N / 2) * h * y;
+    m3 += (i3 - N / 2) * h * y;
+  }
+  double r0 = block_sum(m0, sh);
+  if (threadIdx.x == 0) mom[0] = r0;
+  double r1 = block_sum(m1, sh);
+  if (threadIdx.x == 0) mom[1] = r1;
+  double r2 = block_sum(m2, sh);
+  if (threadIdx.x == 0) mom[2] = r2;
+  double r3 = block_sum(m3, sh);
+  if (threadIdx.x == 0) mom[3] = r3;
+  __syncthreads();
+  const double h3 = h * h * h, rho = h3 * mom[0];
+  const double u1 = h3 * mom[1] / rho, u2 = h3 * mom[2] / rho, u3 = h3 * mom[3] / rho;
+  double e = 0;
+  for (size_t t = threadIdx.x; t < n3; t += blockDim.x) {
+    const int i3 = (int)(t % N), i2 = (int)((t / N) % N), i1 = (int)(t / ((size_t)N * N));
+    const double c1 = (i1 - N / 2) * h - u1, c2 = (i2 - N / 2) * h - u2, c3 = (i3 - N / 2) * h - u3;
+    e += (c1 * c1 + c2 * c2 + c3 * c3) * x[t];
+  }
+  double re = block_sum(e, sh);
+  if (threadIdx.x == 0) {
+    double* p = params + 5 * blockIdx.x;
+    p[0] = rho;
+    p[1] = u1;
+    p[2] = u2;
+    p[3] = u3;
+    p[4] = h3 * re / (3.0 * rho);
+    if (nu) nu[blockIdx.x] = rho;
+  }
+}
+
+// res[0] = -kL h^3 sum v1^- v_1, res[1] = kR h^3 sum v1^+ v_nx (wall densities),
+// res[2] = dx h^3 sum v (total mass); blocks 0, 1 the walls, the rest the mass
+__global__ void __launch_bounds__(RED_THREADS) k_wall_mass(const double* __restrict__ v, int N, int nx, double h,
+                                                           double dx, double kL, double kR,
+                                                           double* __restrict__ part, double* __restrict__ res) {
+  __shared__ double sh[32];
+  const size_t n3 = (size_t)N * N * N, len = n3 * nx;
+  const double h3 = h * h * h;
+  if (blockIdx.x < 2) {
+    const double* x = v + (blockIdx.x == 0 ? 0 : (size_t)(nx - 1) * n3);
+    double a = 0;
+    for (size_t t = threadIdx.x; t < n3; t += blockDim.x) {
+      const double v1 = (int(t / ((size_t)N * N)) - N / 2) * h;
+      a += (blockIdx.x == 0 ? fmin(v1, 0.0) : fmax(v1, 0.0)) * x[t];
+    }
+    double s = block_sum(a, sh);
+    if (threadIdx.x == 0) res[blockIdx.x] = blockIdx.x == 0 ? -kL * h3 * s : kR * h3 * s;
+  } else {
+    double a = 0;
+    const int nb = gridDim.x - 2, b = blockIdx.x - 2;
+    for (size_t e = b * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)nb * blockDim.x) a += v[e];
+    double s = block_sum(a, sh);
+    if (threadIdx.x == 0) part[b] = s;
+  }
+}
+
+__global__ void k_mass_finish(const double* __restrict__ part, int nb, double w, double* __restrict__ res) {
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    res[2] = w * s;
+  }
+}
+
+// out = T v * cT + y * cY + e * m(v) * cE, T the upwind transport with
+// diffuse-wall ghost cells (densities res[0], res[1]), m(v) = res[2].
+__global__ void k_transport(const double* __restrict__ v, const double* __restrict__ y,
+                            const double* __restrict__ e, const double* __restrict__ res,
+                            const double* __restrict__ WL, const double* __restrict__ WR,
+                            double* __restrict__ out, int N, int nx, double h, double dx, double cT, double cY,
+                            double cE) {
+  const size_t n3 = (size_t)N * N * N, len = n3 * nx;
+  const double sL = res[0], sR = res[1], mv = res[2];
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len; t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t / n3);
+    const size_t k = t % n3;
+    const double v1 = (int(k / ((size_t)N * N)) - N / 2) * h;
+    const double c = v[t];
+    double tv;
+    if (v1 > 0) {
+      const double left = j == 0 ? sL * WL[k] : v[t - n3];
+      tv = v1 * (c - left) / dx;
+    } else {
+      const double right = j == nx - 1 ? sR * WR[k] : v[t + n3];
+      tv = v1 * (right - c) / dx;
+    }
+    double o = cT * tv;
+    if (y) o += cY * y[t];
+    if (e) o += cE * mv * e[t];
+    out[t] = o;
+  }
+}
+
+// Upwind sweep of the source iteration (Eq. (5.7)):
+// (v1^+ D^- + v1^- D^+ + nu_j/Kn) z = r, ghost values of z taken as 0.
+__global__ void k_sweep(const double* __restrict__ r, double* __restrict__ z, const double* __restrict__ nu, int N,
+                        int nx, double h, double dx, double kn) {
+  const size_t n3 = (size_t)N * N * N;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n3; k += (size_t)gridDim.x * blockDim.x) {
+    const double v1 = (int(k / ((size_t)N * N)) - N / 2) * h;
+    const double c = fabs(v1) / dx;
+    if (v1 > 0) {
+      double prev = 0;
+      for (int j = 0; j < nx; ++j) {
+        prev = (r[(size_t)j * n3 + k] + c * prev) / (c + nu[j] / kn);
+        z[(size_t)j * n3 + k] = prev;
+      }
+    } else if (v1 < 0) {
+      double prev = 0;
+      for (int j = nx - 1; j >= 0; --j) {
+        prev = (r[(size_t)j * n3 + k] + c * prev) / (c + nu[j] / kn);
+        z[(size_t)j * n3 + k] = prev;
+      }
+    } else {
+      for (int j = 0; j < nx; ++j) z[(size_t)j * n3 + k] = r[(size_t)j * n3 + k] * kn / nu[j];
+    }
+  }
+}
+
+int grid_for(size_t len) {
+  size_t b = (len + 255) / 256;
+  return (int)(b < 152 * 8 ? b : 152 * 8);
+}
+
+// Euclidean dot products res[k] = <V_k, y>, k < K; result copied to host.
+lbo_status dots(lbo_solver* S, const double* Vb, size_t ld, int K, const double* y, double* host_out) {
+  cudaStream_t s = S->plan->stream;
+  LBO_LAUNCH(S->plan, "solver_dots", s, k_dots, RED_BLOCKS, RED_THREADS, 0, Vb, ld, K, y, S->len, S->part);
+  LBO_LAUNCH(S->plan, "solver_reduce", s, k_reduce_parts, 1, 256, 0, S->part, RED_BLOCKS, K, S->res + 8);
+  cudaError_t e = cudaMemcpyAsync(host_out, S->res + 8, sizeof(double) * K, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "solver dots");
+}
+
+double norm2(lbo_solver* S, const double* y, lbo_status* st) {
+  double v = 0;
+  *st = dots(S, y, 0, 1, y, &v);
+  return std::sqrt(v);
+}
+
+// wall densities and total mass of v into S->res[0..2]
+void wall_mass(lbo_solver* S, const double* v) {
+  cudaStream_t s = S->plan->stream;
+  const int nb = RED_BLOCKS;
+  LBO_LAUNCH(S->plan, "solver_wall_mass", s, k_wall_mass, nb + 2, RED_THREADS, 0, v, S->N, S->nx, S->h, S->dx,
+             S->kL, S->kR, S->part, S->res);
+  LBO_LAUNCH(S->plan, "solver_mass_finish", s, k_mass_finish, 1, 32, 0, S->part, nb, S->dx * S->h * S->h * S->h,
+             S->res);
+}
+
+// out = A' v:  SLAB: T v - L v / Kn + e m(v);  HOMOGENEOUS: v - dt L v
+lbo_status apply_op(lbo_solver* S, const double* v, double* out) {
+  lbo_status st = lbo_apply_linearized(S->plan, S->params, v, S->Lv, S->nx);
+  if (st != LBO_OK) return st;
+  cudaStream_t s = S->plan->stream;
+  if (S->pb.kind == LBO_PROBLEM_SLAB) {
+    wall_mass(S, v);
+    LBO_LAUNCH(S->plan, "solver_transport", s, k_transport, grid_for(S->len), 256, 0, v, S->Lv, S->evec, S->res,
+               S->WL, S->WR, out, S->N, S->nx, S->h, S->dx, 1.0, -1.0 / S->pb.kn, 1.0);
+  } else {
+    if (out != v) cudaMemcpyAsync(out, v, sizeof(double) * S->len, cudaMemcpyDeviceToDevice, s);
+    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, out, S->Lv, -S->pb.dt, 1.0, S->len);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "solver operator");
+}
+
+lbo_status apply_precond(lbo_solver* S, const double* v, double* z);
+
+// Nonlinear residual into out (and its weighted norm).
+lbo_status residual(lbo_solver* S, const double* f, const double* f_prev, double* out, double* nrm) {
+  lbo_status st = lbo_apply_quadratic(S->plan, f, S->Qf, S->nx);
+  if (st != LBO_OK) return st;
+  cudaStream_t s = S->plan->stream;
+  if (S->pb.kind == LBO_PROBLEM_SLAB) {
+    wall_mass(S, f);
+    LBO_LAUNCH(S->plan, "solver_transport", s, k_transport, grid_for(S->len), 256, 0, f, S->Qf, (const double*)nullptr,
+               S->res, S->WL, S->WR, out, S->N, S->nx, S->h, S->dx, 1.0, -1.0 / S->pb.kn, 0.0);
+  } else {
+    // F = f - f_prev - dt Q
+    cudaMemcpyAsync(out, f, sizeof(double) * S->len, cudaMemcpyDeviceToDevice, s);
+    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, out, f_prev, -1.0, 1.0, S->len);
+    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, out, S->Qf, -S->pb.dt, 1.0, S->len);
+  }
+  if (nrm) {
+    double v = norm2(S, out, &st);
+    if (st != LBO_OK) return st;
+    *nrm = v * std::sqrt(S->wnorm);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "solver residual");
+}
+
+// Restarted flexible GMRES on A' x = rhs, x0 = 0 (right preconditioning).
+lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
+  const int m = S->m;
+  const size_t len = S->len;
+  cudaStream_t s = S->plan->stream;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gam(m + 1), y(m), hv(m + 1), hv2(m + 1);
+  lbo_status st;
+  cudaMemsetAsync(S->x, 0, sizeof(double) * len, s);
+  double rhs_norm = norm2(S, S->rhs, &st);
+  if (st != LBO_OK) return st;
+  ns->rhs_norm = rhs_norm * std::sqrt(S->wnorm);
+  const double tol = std::fmax(S->pb.krylov_rtol * rhs_norm, S->pb.krylov_atol / std::sqrt(S->wnorm));
+  ns->krylov_iterations = 0;
+  ns->restarts = 0;
+  ns->status = LBO_OK;
+  if (rhs_norm == 0.0) return LBO_OK;
+  if (!std::isfinite(rhs_norm)) {
+    ns->status = LBO_ENAN;
+    return LBO_ENAN;
+  }
+  // r0 = rhs
+  cudaMemcpyAsync(S->V, S->rhs, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+  double beta = rhs_norm;
+  bool done = false;
+  while (!done) {
+    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(len), 256, 0, S->V, S->V, 1.0 / beta, 0.0, len);
+    std::fill(gam.begin(), gam.end(), 0.0);
+    gam[0] = beta;
+    int k = 0;
+    for (; k < m; ++k) {
+      double* vk = S->V + (size_t)k * len;
+      double* zk = S->Z + (size_t)k * len;
+      st = apply_precond(S, vk, zk);
+      if (st != LBO_OK) return st;
+      st = apply_op(S, zk, S->w);
+      if (st != LBO_OK) return st;
+      // classical Gram-Schmidt, two passes, FP64
+      for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        st = dots(S, S->V, len, k + 1, S->w, hv.data());
+        if (st != LBO_OK) return st;
+        cudaMemcpyAsync(S->res + 8, hv.data(), sizeof(double) * (k + 1), cudaMemcpyHostToDevice, s);
+        LBO_LAUNCH(S->plan, "solver_sub", s, k_sub_combination, grid_for(len), 256, 0, S->w, S->V, len, k + 1,
+                   S->res + 8, len);
+        for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] += hv[i];
+      }
+      double hn = norm2(S, S->w, &st);
+      if (st != LBO_OK) return st;
+      H[(size_t)(k + 1) * m + k] = hn;
+      if (!std::isfinite(hn)) {
+        ns->status = LBO_ENAN;
+        return LBO_ENAN;
+      }
+      if (hn > 0)
+        LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(len), 256, 0, S->V + (size_t)(k + 1) * len, S->w,
+                   1.0 / hn, 0.0, len);
+      // Givens rotations
+      for (int i = 0; i < k; ++i) {
+        double a = H[(size_t)i * m + k], b = H[(size_t)(i + 1) * m + k];
+        H[(size_t)i * m + k] = cs[i] * a + sn[i] * b;
+        H[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
+      }
+      double a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
+      double rr = std::hypot(a, b);
+      cs[k] = rr > 0 ? a / rr : 1.0;
+      sn[k] = rr > 0 ? b / rr : 0.0;
+      H[(size_t)k * m + k] = rr;
+      H[(size_t)(k + 1) * m + k] = 0.0;
+      gam[k + 1] = -sn[k] * gam[k];
+      gam[k] = cs[k] * gam[k];
+      ns->krylov_iterations++;
+      if (std::fabs(gam[k + 1]) <= tol || hn == 0.0) {
+        done = true;
+        ++k;
+        break;
+      }
+      if (ns->krylov_iterations >= S->pb.krylov_maxit) {
+        done = true;
+        ns->status = LBO_ENOTCONV;
+        ++k;
+        break;
+      }
+    }
+    // x += Z y,  H(0:k,0:k) y = gam(0:k)
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = gam[i];
+      for (int j = i + 1; j < k; ++j) acc -= H[(size_t)i * m + j] * y[j];
+      y[i] = H[(size_t)i * m + i] != 0 ? acc / H[(size_t)i * m + i] : 0.0;
+    }
+    for (int i = 0; i < k; ++i) hv2[i] = -y[i];
+    cudaMemcpyAsync(S->res + 8, hv2.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s);
+    LBO_LAUNCH(S->plan, "solver_sub", s, k_sub_combination, grid_for(len), 256, 0, S->x, S->Z, len, k, S->res + 8, len);
+    if (done) break;
+    // restart from the true residual
+    ns->restarts++;
+    st = apply_op(S, S->x, S->w);
+    if (st != LBO_OK) return st;
+    cudaMemcpyAsync(S->V, S->rhs, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(len), 256, 0, S->V, S->w, -1.0, 1.0, len);
+    beta = norm2(S, S->V, &st);
+    if (st != LBO_OK) return st;
+    if (beta <= tol) break;
+  }
+  return LBO_OK;
+}
+
+}  // namespace
+
+// learned part of the preconditioner (network.cu)
+lbo_status network_correction(lbo_solver* S, const double* v, double* z);
+
+namespace {
+lbo_status apply_precond(lbo_solver* S, const double* v, double* z) {
+  cudaStream_t s = S->plan->stream;
+  const int pc = S->pb.precond;
+  if (pc == LBO_PRECOND_NONE || S->pb.kind != LBO_PROBLEM_SLAB) {
+    cudaMemcpyAsync(z, v, sizeof(double) * S->len, cudaMemcpyDeviceToDevice, s);
+  } else {
+    LBO_LAUNCH(S->plan, "solver_sweep", s, k_sweep, grid_for(S->n3), 256, 0, v, z, S->nu, S->N, S->nx, S->h, S->dx,
+               S->pb.kn);
+    if (pc == LBO_PRECOND_LEARNED && S->net) {
+      lbo_status st = network_correction(S, v, z);
+      if (st != LBO_OK) return st;
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "preconditioner");
+}
+}  // namespace
+
+}  // namespace lbo
+
+using namespace lbo;
+
+extern "C" {
+
+lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver** out) {
+  if (!pb || !plan || !out) return LBO_EINVAL;
+  *out = nullptr;
+  if (pb->nx < 1 || pb->krylov_restart < 1 || pb->krylov_restart > 200 || pb->krylov_maxit < 1) return LBO_EINVAL;
+  if (pb->kind == LBO_PROBLEM_SLAB) {
+    if (!(pb->x_right > pb->x_left) || !(pb->kn > 0) || !(pb->wall_left[0] > 0) || !(pb->wall_right[0] > 0) ||
+        pb->wall_left[1] != 0.0 || pb->wall_right[1] != 0.0 || !(pb->total_mass > 0))
+      return LBO_EINVAL;
+  } else if (pb->kind == LBO_PROBLEM_HOMOGENEOUS) {
+    if (!(pb->dt > 0)) return LBO_EINVAL;
+  } else {
+    return LBO_EINVAL;
+  }
+  if (pb->precond < 0 || pb->precond > 2) return LBO_EINVAL;
+  lbo_solver* S = new lbo_solver();
+  S->pb = *pb;
+  S->plan = plan;
+  S->N = plan->N;
+  S->nx = pb->nx;
+  S->m = pb->krylov_restart;
+  S->n3 = (size_t)S->N * S->N * S->N;
+  S->len = S->n3 * S->nx;
+  S->h = 2.0 * plan->L / S->N;
+  S->dx = pb->kind == LBO_PROBLEM_SLAB ? (pb->x_right - pb->x_left) / pb->nx : 1.0;
+  S->wnorm = S->dx * S->h * S->h * S->h;
+  const size_t len = S->len;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](double** p, size_t n) {
+    if (e == cudaSuccess) e = cudaMalloc(p, sizeof(double) * n);
+  };
+  alloc(&S->V, (size_t)(S->m + 1) * len);
+  alloc(&S->Z, (size_t)S->m * len);
+  alloc(&S->w, len);
+  alloc(&S->Lv, len);
+  alloc(&S->rhs, len);
+  alloc(&S->x, len);
+  alloc(&S->evec, len);
+  alloc(&S->Qf, len);
+  alloc(&S->params, 5 * (size_t)S->nx);
+  alloc(&S->nu, S->nx);
+  alloc(&S->WL, S->n3);
+  alloc(&S->WR, S->n3);
+  alloc(&S->part, (size_t)RED_BLOCKS * 256);
+  alloc(&S->res, 8 + 256);
+  if (e == cudaSuccess) e = cudaMallocHost(&S->host, sizeof(double) * 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    lbo_solver_destroy(S);
+    set_error_text("solver allocation");
+    return LBO_ENOMEM;
+  }
+  if (pb->kind == LBO_PROBLEM_SLAB) {
+    // wall Maxwellian shapes W(v) = (2 pi theta)^{-3/2} exp(-|v-u_w|^2 / (2 theta))
+    std::vector<double> wl(S->n3), wr(S->n3);
+    const int N = S->N;
+    double sumL = 0, sumR = 0;
+    for (size_t k = 0; k < S->n3; ++k) {
+      const int i1 = (int)(k / ((size_t)N * N)), i2 = (int)((k / N) % N), i3 = (int)(k % N);
+      const double v[3] = {(i1 - N / 2) * S->h, (i2 - N / 2) * S->h, (i3 - N / 2) * S->h};
+      for (int side = 0; side < 2; ++side) {
+        const double* wp = side == 0 ? pb->wall_left : pb->wall_right;
+        const double d2 = (v[0] - wp[1]) * (v[0] - wp[1]) + (v[1] - wp[2]) * (v[1] - wp[2]) +
+                          (v[2] - wp[3]) * (v[2] - wp[3]);
+        const double W = std::pow(2.0 * 3.141592653589793 * wp[0], -1.5) * std::exp(-d2 / (2.0 * wp[0]));
+        (side == 0 ? wl : wr)[k] = W;
+      }
+      if (v[0] > 0) sumL += v[0] * wl[k];
+      if (v[0] < 0) sumR -= v[0] * wr[k];
+    }
+    const double h3 = S->h * S->h * S->h;
+    if (pb->wall_flux == LBO_WALL_FLUX_DISCRETE) {
+      S->kL = 1.0 / (h3 * sumL);
+      S->kR = 1.0 / (h3 * sumR);
+    } else {
+      S->kL = std::sqrt(2.0 * 3.141592653589793 / pb->wall_left[0]);
+      S->kR = std::sqrt(2.0 * 3.141592653589793 / pb->wall_right[0]);
+    }
+    e = cudaMemcpy(S->WL, wl.data(), sizeof(double) * S->n3, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(S->WR, wr.data(), sizeof(double) * S->n3, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      lbo_solver_destroy(S);
+      return cuda_fail(e, "solver tables");
+    }
+  }
+  *out = S;
+  return LBO_OK;
+}
+
+lbo_status lbo_solver_residual(lbo_solver* S, const double* f, const double* f_prev, double* out, double* nrm) {
+  if (!S || !f || !out) return LBO_EINVAL;
+  if (S->pb.kind == LBO_PROBLEM_HOMOGENEOUS && !f_prev) return LBO_EINVAL;
+  return residual(S, f, f_prev, out, nrm);
+}
+
+lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_newton_stats* stats) {
+  if (!S || !f) return LBO_EINVAL;
+  if (S->pb.kind == LBO_PROBLEM_HOMOGENEOUS && !f_prev) return LBO_EINVAL;
+  lbo_newton_stats local{};
+  lbo_newton_stats* ns = stats ? stats : &local;
+  std::memset(ns, 0, sizeof(*ns));
+  cudaStream_t s = S->plan->stream;
+  cudaEvent_t t0, t1, t2;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventCreate(&t2);
+  cudaEventRecord(t0, s);
+  // local Maxwellians (FP64 moments) and the nonlinear residual
+  LBO_LAUNCH(S->plan, "solver_moments", s, k_cell_moments, S->nx, 512, 0, f, S->params, S->nu, S->N, S->h);
+  double rn = 0;
+  lbo_status st = residual(S, f, f_prev, S->rhs, &rn);
+  cudaEventRecord(t1, s);
+  if (st == LBO_OK) {
+    ns->residual_norm = rn;
+    if (S->pb.kind == LBO_PROBLEM_SLAB) {
+      // bordered system: e = f / m(f), rhs = R + e (m(f) - C)
+      wall_mass(S, f);
+      double mf = 0;
+      cudaMemcpyAsync(&mf, S->res + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, S->evec, f, 1.0 / mf, 0.0, S->len);
+      LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, S->rhs, S->evec,
+                 mf - S->pb.total_mass, 1.0, S->len);
+    }
+    st = fgmres(S, ns);
+    if (st == LBO_OK || st == LBO_ENOTCONV) {
+      // FP64 true residual of the linear system
+      lbo_status st2 = apply_op(S, S->x, S->w);
+      if (st2 == LBO_OK) {
+        LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, S->w, S->rhs, 1.0, -1.0, S->len);
+        double lr = norm2(S, S->w, &st2);
+        ns->linear_residual = lr * std::sqrt(S->wnorm);
+      }
+      // f <- f - g
+      LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, f, S->x, -1.0, 1.0, S->len);
+      if (st2 != LBO_OK) st = st2;
+    }
+  }
+  cudaEventRecord(t2, s);
+  cudaEventSynchronize(t2);
+  float a = 0, b = 0;
+  cudaEventElapsedTime(&a, t0, t1);
+  cudaEventElapsedTime(&b, t1, t2);
+  ns->ms_residual = a;
+  ns->ms_linear = b;
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaEventDestroy(t2);
+  if (st == LBO_OK && ns->status != LBO_OK) return (lbo_status)ns->status;
+  cudaError_t e = cudaGetLastError();
+  if (st == LBO_OK && e != cudaSuccess) return cuda_fail(e, "newton step");
+  return st;
+}
+
+void lbo_solver_destroy(lbo_solver* S) {
+  if (!S) return;
+  double* bufs[] = {S->V, S->Z, S->w, S->Lv, S->rhs, S->x, S->evec, S->Qf, S->params, S->nu, S->WL, S->WR,
+                    S->part, S->res, S->feat, S->corr};
+  for (double* p : bufs)
+    if (p) cudaFree(p);
+  if (S->net) cudaFree(S->net);
+  if (S->host) cudaFreeHost(S->host);
+  delete S;
+}
+
+}  // extern "C"

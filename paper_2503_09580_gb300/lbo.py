@@ -27,9 +27,35 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_apply_quadratic", "lbo_plan_sync", "lbo_plan_last_launches", "lbo_plan_destroy",
            "lbo_status_string", "lbo_last_error", "lbo_plan_profile", "lbo_plan_profile_count",
            "lbo_plan_profile_get", "lbo_apply_linearized_noalloc", "lbo_noalloc_scratch_bytes",
-           "lbo_noalloc_bytes_per_instance")
+           "lbo_noalloc_bytes_per_instance", "lbo_solver_create", "lbo_newton_step", "lbo_solver_residual",
+           "lbo_solver_destroy")
 
 _lib = None
+
+
+class Problem(ctypes.Structure):
+    """lbo_problem"""
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("x_left", ctypes.c_double),
+                ("x_right", ctypes.c_double), ("kn", ctypes.c_double), ("wall_left", ctypes.c_double * 4),
+                ("wall_right", ctypes.c_double * 4), ("total_mass", ctypes.c_double), ("wall_flux", ctypes.c_int),
+                ("dt", ctypes.c_double), ("krylov_rtol", ctypes.c_double), ("krylov_atol", ctypes.c_double),
+                ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int), ("precond", ctypes.c_int)]
+
+
+class NewtonStats(ctypes.Structure):
+    """lbo_newton_stats"""
+    _fields_ = [("residual_norm", ctypes.c_double), ("rhs_norm", ctypes.c_double),
+                ("linear_residual", ctypes.c_double), ("krylov_iterations", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("status", ctypes.c_int), ("ms_residual", ctypes.c_double),
+                ("ms_linear", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PROBLEM = {"slab": 0, "homogeneous": 1}
+PRECOND = {"none": 0, "sweep": 1, "learned": 2}
+WALL_FLUX = {"analytic": 0, "discrete": 1}
 
 
 class LboError(RuntimeError):
@@ -82,6 +108,14 @@ def load():
     lib.lbo_noalloc_scratch_bytes.restype = ctypes.c_size_t
     lib.lbo_noalloc_bytes_per_instance.argtypes = [vp]
     lib.lbo_noalloc_bytes_per_instance.restype = ctypes.c_size_t
+    lib.lbo_solver_create.argtypes = [ctypes.POINTER(Problem), vp, ctypes.POINTER(vp)]
+    lib.lbo_solver_create.restype = ip
+    lib.lbo_newton_step.argtypes = [vp, dp, dp, ctypes.POINTER(NewtonStats)]
+    lib.lbo_newton_step.restype = ip
+    lib.lbo_solver_residual.argtypes = [vp, dp, dp, dp, ctypes.POINTER(ctypes.c_double)]
+    lib.lbo_solver_residual.restype = ip
+    lib.lbo_solver_destroy.argtypes = [vp]
+    lib.lbo_solver_destroy.restype = None
     lib.lbo_last_error.argtypes = []
     lib.lbo_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -165,6 +199,9 @@ class Plan:
     def sync(self):
         _check(load().lbo_plan_sync(self._h), "lbo_plan_sync")
 
+    def solver(self, **kw):
+        return Solver(self, **kw)
+
     def profile(self, enable=True):
         """Start (clearing counters) or stop per-kernel event timing."""
         _check(load().lbo_plan_profile(self._h, 1 if enable else 0), "lbo_plan_profile")
@@ -188,6 +225,61 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load().lbo_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """lbo_solver: modified Newton with flexible GMRES on a plan."""
+
+    def __init__(self, plan, kind="slab", nx=1, x_left=-0.5, x_right=0.5, kn=1.0,
+                 wall_left=(1.0, 0.0, 0.0, 0.0), wall_right=(1.0, 0.0, 0.0, 0.0), total_mass=1.0,
+                 wall_flux="analytic", dt=0.0, krylov_rtol=1e-3, krylov_atol=1e-7, krylov_restart=30,
+                 krylov_maxit=300, precond="sweep"):
+        lib = load()
+        pb = Problem()
+        pb.kind = PROBLEM[kind]
+        pb.nx = int(nx)
+        pb.x_left, pb.x_right, pb.kn = float(x_left), float(x_right), float(kn)
+        for i in range(4):
+            pb.wall_left[i] = float(wall_left[i])
+            pb.wall_right[i] = float(wall_right[i])
+        pb.total_mass = float(total_mass)
+        pb.wall_flux = WALL_FLUX[wall_flux]
+        pb.dt = float(dt)
+        pb.krylov_rtol, pb.krylov_atol = float(krylov_rtol), float(krylov_atol)
+        pb.krylov_restart, pb.krylov_maxit = int(krylov_restart), int(krylov_maxit)
+        pb.precond = PRECOND[precond]
+        h = ctypes.c_void_p()
+        _check(lib.lbo_solver_create(ctypes.byref(pb), plan._h, ctypes.byref(h)), "lbo_solver_create")
+        self._h, self.plan, self.problem = h, plan, pb
+
+    def newton_step(self, f, f_prev=None):
+        """One modified Newton step in place on the device tensor f; returns the stats dict."""
+        st = NewtonStats()
+        self.plan._stream(f)
+        rc = load().lbo_newton_step(self._h, _ptr(f), None if f_prev is None else _ptr(f_prev), ctypes.byref(st))
+        if rc not in (0, 4):
+            _check(rc, "lbo_newton_step")
+        d = st.as_dict()
+        d["converged_inner"] = rc == 0
+        return d
+
+    def residual(self, f, out, f_prev=None):
+        nrm = ctypes.c_double()
+        self.plan._stream(f)
+        _check(load().lbo_solver_residual(self._h, _ptr(f), None if f_prev is None else _ptr(f_prev), _ptr(out),
+                                          ctypes.byref(nrm)), "lbo_solver_residual")
+        return nrm.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lbo_solver_destroy(self._h)
             self._h = None
 
     def __del__(self):
