@@ -179,6 +179,8 @@ typedef struct {
   double linear_residual;  /* FP64 true |rhs - A g| after the solve             */
   int krylov_iterations;
   int restarts;
+  int fallbacks;           /* 1 if the learned preconditioner was replaced by the
+                              plain sweep after half of krylov_maxit iterations */
   int status;              /* lbo_status of the inner solve (LBO_ENOTCONV if the
                               cap was hit; the step is still applied)          */
   double ms_residual;      /* time in the nonlinear residual (Q evaluations)    */
@@ -202,6 +204,42 @@ lbo_status lbo_solver_residual(lbo_solver *solver, const double *f, const double
                                double *norm);
 
 void lbo_solver_destroy(lbo_solver *solver);
+
+/* Learned preconditioner (SLAB only; no counterpart in the paper: a learned
+ * form of the synthetic acceleration the paper points to for small Kn,
+ * Sec. 5.2).  A two-layer width-5 convolutional network over the cells maps
+ * 13 moments per cell ({1, v, |v|^2}, the traceless stress v1v2, v1v3, v2v3,
+ * v1^2-v2^2, v2^2-v3^2 and the heat flux v|v|^2) of a Krylov vector v and of
+ * its upwind sweep s to a macroscopic correction,
+ * z = s + sum_a c_{j,a} phi_a(v) M_j(v), phi_a in {1, v, |v|^2}.
+ * Training pairs are (A z_k, z_k) from the solver's own FGMRES iterations;
+ * the target of cell j solves G_j c_j = m(z_j) - m(s_j), G_j the moment
+ * matrix of phi_a phi_b M_j.  Parameters: FP32, packed as
+ * [W1 (H,26,5), b1 (H), W2 (5,H,5), b2 (5)]; scales: 31 floats (26 input,
+ * 5 output channel scales of the normalisation).
+ *
+ * lbo_solver_collect(s, max_pairs): keep up to max_pairs pairs from the next
+ *   solves (0 stops collecting; changing max_pairs clears the store).
+ * lbo_solver_train_network: full-batch Adam on the mean squared error of the
+ *   normalised targets, on the GPU; *final_loss (may be NULL) receives it.
+ * hidden = 0 selects the global linear form instead: one linear
+ *   convolution of width 2 nx - 1 over the cells (every cell sees the whole
+ *   slab), which can represent the nonlocal macroscopic response at small
+ *   Kn with 130 (2 nx - 1) + 5 parameters (lbo_solver_network_param_count).
+ * lbo_network_loss_grad: loss and gradient of the same network for given
+ *   device arrays x [pairs][nx][26], t [pairs][nx][5] (for checking the
+ *   hand-written backward pass); grad: device array of
+ *   lbo_network_param_count(hidden) floats (hidden >= 1 there). */
+int lbo_network_param_count(int hidden);
+lbo_status lbo_network_loss_grad(int hidden, const float *theta, const float *x, const float *t, int pairs,
+                                 int nx, double *loss, float *grad);
+lbo_status lbo_solver_collect(lbo_solver *solver, int max_pairs);
+int lbo_solver_pair_count(lbo_solver *solver);
+lbo_status lbo_solver_train_network(lbo_solver *solver, int hidden, int epochs, double lr, unsigned seed,
+                                    double *final_loss);
+lbo_status lbo_solver_get_network(lbo_solver *solver, int *hidden, float *params, float *scales);
+lbo_status lbo_solver_set_network(lbo_solver *solver, int hidden, const float *params, const float *scales);
+int lbo_solver_network_param_count(lbo_solver *solver, int hidden);
 
 /* Allocation-free variant of lbo_apply_linearized (the paper has no
  * counterpart; this is a library facility).  For callers that cannot

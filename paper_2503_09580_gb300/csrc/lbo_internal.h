@@ -49,8 +49,28 @@ struct lbo_plan {
   std::vector<ProfTotal> prof_totals;
 };
 
+struct lbo_solver {
+  lbo_problem pb;
+  lbo_plan* plan = nullptr;
+  int N = 0, nx = 0, m = 0;
+  size_t n3 = 0, len = 0;
+  double h = 0, dx = 1, wnorm = 1, kL = 0, kR = 0;
+  double *V = nullptr, *Z = nullptr;  // Krylov basis (m+1) and preconditioned vectors (m)
+  double *w = nullptr, *Lv = nullptr, *rhs = nullptr, *x = nullptr, *evec = nullptr, *Qf = nullptr;
+  double *params = nullptr, *nu = nullptr, *WL = nullptr, *WR = nullptr;
+  double *part = nullptr, *res = nullptr;  // reduction partials, small results
+  double* host = nullptr;                  // pinned small results
+  void* netstate = nullptr;                // learned preconditioner (network.cu)
+  bool force_sweep = false;                // fallback from the learned preconditioner
+};
+
 namespace lbo {
 lbo_status cuda_fail(cudaError_t e, const char* where);
+// learned preconditioner (network.cu)
+lbo_status network_correction(lbo_solver* S, const double* v, double* z);
+lbo_status network_record(lbo_solver* S, const double* w, const double* zk, double* s_scratch,
+                          lbo_status (*sweep)(lbo_solver*, const double*, double*));
+void free_network(lbo_solver* S);
 void set_error_text(const char* msg);
 // zero-mode removal and/or FP64 conservation projection of out[B][N^3]
 lbo_status launch_fixes(lbo_plan* p, double* out, int B, int N, double h, cudaStream_t s, int* launches);

@@ -7,24 +7,6 @@
 
 #include "lbo_internal.h"
 
-struct lbo_solver {
-  lbo_problem pb;
-  lbo_plan* plan = nullptr;
-  int N = 0, nx = 0, m = 0;
-  size_t n3 = 0, len = 0;
-  double h = 0, dx = 1, wnorm = 1, kL = 0, kR = 0;
-  double *V = nullptr, *Z = nullptr;           // Krylov basis (m+1) and preconditioned vectors (m)
-  double *w = nullptr, *Lv = nullptr, *rhs = nullptr, *x = nullptr, *evec = nullptr, *Qf = nullptr;
-  double *params = nullptr, *nu = nullptr, *WL = nullptr, *WR = nullptr;
-  double *part = nullptr, *res = nullptr;     // reduction partials, small results
-  double* host = nullptr;                     // pinned small results
-  // learned preconditioner (lbo_solver_set_network)
-  float* net = nullptr;
-  int net_hidden = 0;
-  double *feat = nullptr, *corr = nullptr;
-  double net_scale_in = 1, net_scale_out = 1;
-};
-
 namespace lbo {
 namespace {
 
@@ -286,6 +268,13 @@ lbo_status apply_op(lbo_solver* S, const double* v, double* out) {
 
 lbo_status apply_precond(lbo_solver* S, const double* v, double* z);
 
+lbo_status sweep_only(lbo_solver* S, const double* v, double* z) {
+  LBO_LAUNCH(S->plan, "solver_sweep", S->plan->stream, k_sweep, grid_for(S->n3), 256, 0, v, z, S->nu, S->N, S->nx,
+             S->h, S->dx, S->pb.kn);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "sweep");
+}
+
 // Nonlinear residual into out (and its weighted norm).
 lbo_status residual(lbo_solver* S, const double* f, const double* f_prev, double* out, double* nrm) {
   lbo_status st = lbo_apply_quadratic(S->plan, f, S->Qf, S->nx);
@@ -334,6 +323,12 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
   cudaMemcpyAsync(S->V, S->rhs, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
   double beta = rhs_norm;
   bool done = false;
+  // the learned preconditioner gets half the iteration budget; if it has not
+  // converged by then, the solve continues from the current iterate with the
+  // plain sweep (the exact operator stays the judge)
+  S->force_sweep = false;
+  const bool learned = S->pb.precond == LBO_PRECOND_LEARNED;
+  const int learned_budget = S->pb.krylov_maxit / 2;
   while (!done) {
     LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(len), 256, 0, S->V, S->V, 1.0 / beta, 0.0, len);
     std::fill(gam.begin(), gam.end(), 0.0);
@@ -346,6 +341,11 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
       if (st != LBO_OK) return st;
       st = apply_op(S, zk, S->w);
       if (st != LBO_OK) return st;
+      if (S->pb.kind == LBO_PROBLEM_SLAB) {
+        // training pair (A z_k, z_k) for the learned preconditioner, if collecting
+        st = network_record(S, S->w, zk, S->Lv, sweep_only);
+        if (st != LBO_OK) return st;
+      }
       // classical Gram-Schmidt, two passes, FP64
       for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = 0.0;
       for (int pass = 0; pass < 2; ++pass) {
@@ -392,6 +392,10 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
         ++k;
         break;
       }
+      if (learned && !S->force_sweep && ns->krylov_iterations >= learned_budget) {
+        ++k;  // end this cycle; the restart below switches to the sweep
+        break;
+      }
     }
     // x += Z y,  H(0:k,0:k) y = gam(0:k)
     for (int i = k - 1; i >= 0; --i) {
@@ -403,6 +407,10 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
     cudaMemcpyAsync(S->res + 8, hv2.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s);
     LBO_LAUNCH(S->plan, "solver_sub", s, k_sub_combination, grid_for(len), 256, 0, S->x, S->Z, len, k, S->res + 8, len);
     if (done) break;
+    if (learned && !S->force_sweep && ns->krylov_iterations >= learned_budget) {
+      S->force_sweep = true;
+      ns->fallbacks++;
+    }
     // restart from the true residual
     ns->restarts++;
     st = apply_op(S, S->x, S->w);
@@ -418,8 +426,6 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
 
 }  // namespace
 
-// learned part of the preconditioner (network.cu)
-lbo_status network_correction(lbo_solver* S, const double* v, double* z);
 
 namespace {
 lbo_status apply_precond(lbo_solver* S, const double* v, double* z) {
@@ -430,7 +436,7 @@ lbo_status apply_precond(lbo_solver* S, const double* v, double* z) {
   } else {
     LBO_LAUNCH(S->plan, "solver_sweep", s, k_sweep, grid_for(S->n3), 256, 0, v, z, S->nu, S->N, S->nx, S->h, S->dx,
                S->pb.kn);
-    if (pc == LBO_PRECOND_LEARNED && S->net) {
+    if (pc == LBO_PRECOND_LEARNED && !S->force_sweep) {
       lbo_status st = network_correction(S, v, z);
       if (st != LBO_OK) return st;
     }
@@ -602,10 +608,10 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
 void lbo_solver_destroy(lbo_solver* S) {
   if (!S) return;
   double* bufs[] = {S->V, S->Z, S->w, S->Lv, S->rhs, S->x, S->evec, S->Qf, S->params, S->nu, S->WL, S->WR,
-                    S->part, S->res, S->feat, S->corr};
+                    S->part, S->res};
   for (double* p : bufs)
     if (p) cudaFree(p);
-  if (S->net) cudaFree(S->net);
+  free_network(S);
   if (S->host) cudaFreeHost(S->host);
   delete S;
 }

@@ -28,7 +28,9 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_status_string", "lbo_last_error", "lbo_plan_profile", "lbo_plan_profile_count",
            "lbo_plan_profile_get", "lbo_apply_linearized_noalloc", "lbo_noalloc_scratch_bytes",
            "lbo_noalloc_bytes_per_instance", "lbo_solver_create", "lbo_newton_step", "lbo_solver_residual",
-           "lbo_solver_destroy")
+           "lbo_solver_destroy", "lbo_network_param_count", "lbo_network_loss_grad", "lbo_solver_collect",
+           "lbo_solver_pair_count", "lbo_solver_train_network", "lbo_solver_get_network", "lbo_solver_set_network",
+           "lbo_solver_network_param_count")
 
 _lib = None
 
@@ -46,7 +48,8 @@ class NewtonStats(ctypes.Structure):
     """lbo_newton_stats"""
     _fields_ = [("residual_norm", ctypes.c_double), ("rhs_norm", ctypes.c_double),
                 ("linear_residual", ctypes.c_double), ("krylov_iterations", ctypes.c_int),
-                ("restarts", ctypes.c_int), ("status", ctypes.c_int), ("ms_residual", ctypes.c_double),
+                ("restarts", ctypes.c_int), ("fallbacks", ctypes.c_int), ("status", ctypes.c_int),
+                ("ms_residual", ctypes.c_double),
                 ("ms_linear", ctypes.c_double)]
 
     def as_dict(self):
@@ -116,6 +119,23 @@ def load():
     lib.lbo_solver_residual.restype = ip
     lib.lbo_solver_destroy.argtypes = [vp]
     lib.lbo_solver_destroy.restype = None
+    lib.lbo_network_param_count.argtypes = [ip]
+    lib.lbo_network_param_count.restype = ip
+    lib.lbo_network_loss_grad.argtypes = [ip, vp, vp, vp, ip, ip, ctypes.POINTER(ctypes.c_double), vp]
+    lib.lbo_network_loss_grad.restype = ip
+    lib.lbo_solver_collect.argtypes = [vp, ip]
+    lib.lbo_solver_collect.restype = ip
+    lib.lbo_solver_pair_count.argtypes = [vp]
+    lib.lbo_solver_pair_count.restype = ip
+    lib.lbo_solver_train_network.argtypes = [vp, ip, ip, ctypes.c_double, ctypes.c_uint,
+                                             ctypes.POINTER(ctypes.c_double)]
+    lib.lbo_solver_train_network.restype = ip
+    lib.lbo_solver_get_network.argtypes = [vp, ctypes.POINTER(ip), vp, vp]
+    lib.lbo_solver_get_network.restype = ip
+    lib.lbo_solver_set_network.argtypes = [vp, ip, vp, vp]
+    lib.lbo_solver_set_network.restype = ip
+    lib.lbo_solver_network_param_count.argtypes = [vp, ip]
+    lib.lbo_solver_network_param_count.restype = ip
     lib.lbo_last_error.argtypes = []
     lib.lbo_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -277,6 +297,38 @@ class Solver:
                                           ctypes.byref(nrm)), "lbo_solver_residual")
         return nrm.value
 
+    def collect(self, max_pairs):
+        """Keep up to max_pairs (A z_k, z_k) training pairs from the next solves."""
+        _check(load().lbo_solver_collect(self._h, int(max_pairs)), "lbo_solver_collect")
+
+    @property
+    def pair_count(self):
+        return load().lbo_solver_pair_count(self._h)
+
+    def train_network(self, hidden=32, epochs=500, lr=3e-3, seed=0):
+        loss = ctypes.c_double()
+        _check(load().lbo_solver_train_network(self._h, int(hidden), int(epochs), float(lr), int(seed),
+                                               ctypes.byref(loss)), "lbo_solver_train_network")
+        return loss.value
+
+    def get_network(self):
+        lib = load()
+        hid = ctypes.c_int()
+        _check(lib.lbo_solver_get_network(self._h, ctypes.byref(hid), None, None), "lbo_solver_get_network")
+        if hid.value < 0:
+            return None
+        params = np.empty(lib.lbo_solver_network_param_count(self._h, hid.value), dtype=np.float32)
+        scales = np.empty(31, dtype=np.float32)
+        _check(lib.lbo_solver_get_network(self._h, ctypes.byref(hid), params.ctypes.data_as(ctypes.c_void_p),
+                                          scales.ctypes.data_as(ctypes.c_void_p)), "lbo_solver_get_network")
+        return hid.value, params, scales
+
+    def set_network(self, hidden, params, scales):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        scales = np.ascontiguousarray(scales, dtype=np.float32)
+        _check(load().lbo_solver_set_network(self._h, int(hidden), params.ctypes.data_as(ctypes.c_void_p),
+                                             scales.ctypes.data_as(ctypes.c_void_p)), "lbo_solver_set_network")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load().lbo_solver_destroy(self._h)
@@ -287,3 +339,14 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def network_loss_grad(hidden, theta, x, t):
+    """lbo_network_loss_grad on CUDA float32 tensors; returns (loss, grad tensor)."""
+    import torch
+    grad = torch.empty_like(theta)
+    loss = ctypes.c_double()
+    _check(load().lbo_network_loss_grad(int(hidden), ctypes.c_void_p(theta.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(t.data_ptr()), int(x.shape[0]), int(x.shape[1]),
+                                        ctypes.byref(loss), ctypes.c_void_p(grad.data_ptr())), "lbo_network_loss_grad")
+    return loss.value, grad
