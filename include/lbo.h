@@ -76,7 +76,7 @@ typedef enum {
 /* Create a plan for N^3 grids on [-box, box]^3, VHS exponent vhs_omega in
  * [0.5, 1], radial_nodes Gauss-Legendre nodes on [0, R] (Eq. (2.13)).
  * Builds the tables of Algorithm 1 (its precomputation step) on the current
- * CUDA device.  N must be 16, 32 or 64.  On success *out owns device memory
+ * CUDA device.  N must be 16, 24, 32, 48 or 64.  On success *out owns device memory
  * until lbo_plan_destroy.  Errors: LBO_EINVAL, LBO_EUNSUPPORTED, LBO_ENOMEM,
  * LBO_ECUDA (then *out is NULL). */
 lbo_status lbo_plan_create(int N, double box, double vhs_omega, int radial_nodes,
@@ -263,6 +263,32 @@ lbo_status lbo_apply_linearized_noalloc(lbo_plan *plan, const double *maxwellian
                                         const double *g, double *out, int batch);
 size_t lbo_noalloc_scratch_bytes(void);
 size_t lbo_noalloc_bytes_per_instance(const lbo_plan *plan);
+
+/* Launch-shape autotuner.  Times the candidate shapes of the plan's fastest
+ * kernel set on the given device arrays (for the fused FP32 N = 32 kernels:
+ * 1, 2, 3, 4, 6 or 8 groups of radial nodes per instance), keeps the
+ * fastest in the plan (as LBO_OPT_JGROUPS) and returns it in *choice (0 when
+ * the plan has nothing to tune).  Overwrites out. */
+lbo_status lbo_plan_autotune(lbo_plan *plan, const double *maxwellian_params, const double *g, double *out,
+                             int batch, int *choice);
+
+/* Groups: several plans (e.g. grids of different N, each cell with its own
+ * Maxwellian) applied together.  Each member runs on its own stream forked
+ * from and joined back into the group's stream, so different grid sizes
+ * overlap on the GPU.  With lbo_group_use_graph(group, 1) and a non-NULL
+ * group stream, the second call with the same arrays and batch sizes
+ * records the whole application into a CUDA graph and later calls replay it
+ * (the first call runs eagerly, so tables and workspaces exist before any
+ * capture).  Arrays are device pointers; params[i], g[i], out[i], batch[i]
+ * belong to member i.  Member plans must not be used concurrently
+ * elsewhere. */
+typedef struct lbo_group lbo_group;
+lbo_status lbo_group_create(lbo_plan *const *plans, int nplans, lbo_group **out);
+lbo_status lbo_group_set_stream(lbo_group *group, void *stream);
+lbo_status lbo_group_use_graph(lbo_group *group, int enable);
+lbo_status lbo_group_apply_linearized(lbo_group *group, const double *const *params, const double *const *g,
+                                      double *const *out, const int *batch);
+void lbo_group_destroy(lbo_group *group);
 
 /* Free a plan (NULL is allowed). */
 void lbo_plan_destroy(lbo_plan *plan);

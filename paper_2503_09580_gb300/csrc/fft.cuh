@@ -1,4 +1,4 @@
-// Small batched FFT building blocks for N = 16, 32, 64 (sm_103a).
+// Small batched FFT building blocks for N = 16, 24, 32, 48, 64 (sm_103a).
 //
 // A length-N transform (N = R1*R2) is done in place on pencils held in
 // shared memory, in two in-place stages:
@@ -55,20 +55,39 @@ __device__ __forceinline__ cpx<T> mul_mi(cpx<T> a) {
 // copy (no relocatable device code); upload_twiddles() fills it once.
 static __constant__ double2 c_tw64_d[64];
 static __constant__ float2 c_tw64_f[64];
+// W_48^m, for the radix-3 sizes N = 24, 48
+static __constant__ double2 c_tw48_d[48];
+static __constant__ float2 c_tw48_f[48];
 
-static cudaError_t upload_twiddles() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  double2 d[64];
-  float2 f[64];
+static cudaError_t upload_twiddles_now() {
+  double2 d[64], d48[48];
+  float2 f[64], f48[48];
   for (int m = 0; m < 64; ++m) {
     long double a = -2.0L * 3.14159265358979323846264338327950288L * m / 64.0L;
     d[m] = make_double2((double)cosl(a), (double)sinl(a));
     f[m] = make_float2((float)d[m].x, (float)d[m].y);
   }
+  for (int m = 0; m < 48; ++m) {
+    long double a = -2.0L * 3.14159265358979323846264338327950288L * m / 48.0L;
+    d48[m] = make_double2((double)cosl(a), (double)sinl(a));
+    f48[m] = make_float2((float)d48[m].x, (float)d48[m].y);
+  }
   cudaError_t e = cudaMemcpyToSymbol(c_tw64_d, d, sizeof(d));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw64_f, f, sizeof(f));
-  if (e == cudaSuccess) done = true;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw48_d, d48, sizeof(d48));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw48_f, f48, sizeof(f48));
+  return e;
+}
+
+// Uploads this translation unit's tables once per device.
+static cudaError_t upload_twiddles() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = upload_twiddles_now();
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
 
@@ -83,6 +102,26 @@ template <>
 __device__ __forceinline__ cpx<float> tw64<float>(int m) {
   float2 t = c_tw64_f[m & 63];
   return make_c(t.x, t.y);
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> tw48(int m);
+template <>
+__device__ __forceinline__ cpx<double> tw48<double>(int m) {
+  double2 t = c_tw48_d[m % 48];
+  return make_c(t.x, t.y);
+}
+template <>
+__device__ __forceinline__ cpx<float> tw48<float>(int m) {
+  float2 t = c_tw48_f[m % 48];
+  return make_c(t.x, t.y);
+}
+
+// W_N^m for N dividing 64 or 48
+template <typename T, int N>
+__device__ __forceinline__ cpx<T> twN(int m) {
+  if constexpr (64 % N == 0) return tw64<T>((64 / N) * m);
+  else return tw48<T>((48 / N) * m);
 }
 
 // ----------------------------------------------------------- small DFTs
@@ -126,12 +165,48 @@ __device__ __forceinline__ void dft8(cpx<T>* a) {
   a[7] = e[3] - o3;
 }
 
+// W3 = exp(-+2 pi i/3): X1 = m + s, X2 = m - s, m = a0 - (a1+a2)/2,
+// s = -+i (sqrt3/2)(a1 - a2)
+template <typename T, bool INV>
+__device__ __forceinline__ void dft3(cpx<T>* a) {
+  const T c = (T)0.86602540378443864676372317075293618347140262690519;
+  cpx<T> t1 = a[1] + a[2], t2 = a[1] - a[2];
+  cpx<T> m = make_c(a[0].x - (T)0.5 * t1.x, a[0].y - (T)0.5 * t1.y);
+  cpx<T> sv = INV ? make_c(-c * t2.y, c * t2.x) : make_c(c * t2.y, -c * t2.x);
+  a[0] = a[0] + t1;
+  a[1] = m + sv;
+  a[2] = m - sv;
+}
+
+// 6 = 2 x 3: E = DFT3(even), O = DFT3(odd), X[k] = E[k] + W6^k O[k],
+// X[k+3] = E[k] - W6^k O[k]
+template <typename T, bool INV>
+__device__ __forceinline__ void dft6(cpx<T>* a) {
+  const T c = (T)0.86602540378443864676372317075293618347140262690519;
+  cpx<T> e[3] = {a[0], a[2], a[4]};
+  cpx<T> o[3] = {a[1], a[3], a[5]};
+  dft3<T, INV>(e);
+  dft3<T, INV>(o);
+  // W6 = 1/2 -+ i sqrt3/2, W6^2 = -1/2 -+ i sqrt3/2
+  const T s = INV ? c : -c;
+  cpx<T> o1 = cmul(o[1], make_c((T)0.5, s));
+  cpx<T> o2 = cmul(o[2], make_c((T)-0.5, s));
+  a[0] = e[0] + o[0];
+  a[3] = e[0] - o[0];
+  a[1] = e[1] + o1;
+  a[4] = e[1] - o1;
+  a[2] = e[2] + o2;
+  a[5] = e[2] - o2;
+}
+
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void dft_small(cpx<T>* a) {
   if constexpr (R == 2) dft2<T, INV>(a);
+  else if constexpr (R == 3) dft3<T, INV>(a);
   else if constexpr (R == 4) dft4<T, INV>(a);
+  else if constexpr (R == 6) dft6<T, INV>(a);
   else if constexpr (R == 8) dft8<T, INV>(a);
-  else static_assert(R == 2 || R == 4 || R == 8, "radix");
+  else static_assert(R == 2 || R == 3 || R == 4 || R == 6 || R == 8, "radix");
 }
 
 template <int N>
@@ -142,6 +217,10 @@ template <>
 struct Split<32> { static constexpr int R1 = 4, R2 = 8; };
 template <>
 struct Split<64> { static constexpr int R1 = 8, R2 = 8; };
+template <>
+struct Split<24> { static constexpr int R1 = 3, R2 = 8; };
+template <>
+struct Split<48> { static constexpr int R1 = 6, R2 = 8; };
 
 // frequency held at digit-reversed position p, and the position of frequency k
 template <int N>
@@ -163,7 +242,6 @@ __device__ __forceinline__ int centred(int k) { return k < N / 2 ? k : k - N; }
 template <typename T, int N, bool INV, bool PMAJOR>
 __device__ __forceinline__ void smem_fft(cpx<T>* base, int npen, int ps, int es) {
   constexpr int R1 = Split<N>::R1, R2 = Split<N>::R2;
-  constexpr int TWS = 64 / N;
   if constexpr (!INV) {
     for (int t = threadIdx.x; t < npen * R1; t += blockDim.x) {
       int p = PMAJOR ? t % npen : t / R1;
@@ -174,7 +252,7 @@ __device__ __forceinline__ void smem_fft(cpx<T>* base, int npen, int ps, int es)
       for (int i = 0; i < R2; ++i) v[i] = x[(n1 + R1 * i) * es];
       dft_small<T, R2, false>(v);
 #pragma unroll
-      for (int k = 0; k < R2; ++k) x[(n1 + R1 * k) * es] = k == 0 ? v[0] : cmul(v[k], tw64<T>(TWS * n1 * k));
+      for (int k = 0; k < R2; ++k) x[(n1 + R1 * k) * es] = k == 0 ? v[0] : cmul(v[k], twN<T, N>(n1 * k));
     }
     __syncthreads();
     for (int t = threadIdx.x; t < npen * R2; t += blockDim.x) {
@@ -210,7 +288,7 @@ __device__ __forceinline__ void smem_fft(cpx<T>* base, int npen, int ps, int es)
 #pragma unroll
       for (int k = 0; k < R2; ++k) {
         cpx<T> a = x[(n1 + R1 * k) * es];
-        v[k] = k == 0 ? a : cmulc(a, tw64<T>(TWS * n1 * k));
+        v[k] = k == 0 ? a : cmulc(a, twN<T, N>(n1 * k));
       }
       dft_small<T, R2, true>(v);
 #pragma unroll

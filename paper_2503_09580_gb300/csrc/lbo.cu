@@ -155,7 +155,9 @@ static lbo_status build_tables(lbo_plan* p) {
   lbo_status s2;
   switch (N) {
     case 16: s2 = build_phit<double, 16>(p, d_stab, p->d_phit64); break;
+    case 24: s2 = build_phit<double, 24>(p, d_stab, p->d_phit64); break;
     case 32: s2 = build_phit<double, 32>(p, d_stab, p->d_phit64); break;
+    case 48: s2 = build_phit<double, 48>(p, d_stab, p->d_phit64); break;
     case 64: s2 = build_phit<double, 64>(p, d_stab, p->d_phit64); break;
     default: s2 = LBO_EUNSUPPORTED;
   }
@@ -219,7 +221,7 @@ static void set_smem(K kernel, size_t bytes) {
 }
 
 template <int N>
-struct PlanePPC { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : 1); };
+struct PlanePPC { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : (N == 24 ? 4 : (N == 48 ? 2 : 1))); };
 
 // phit_j = IDFT(s_j) for all j, FP64, then an FP32 copy.
 template <typename T, int N>
@@ -360,7 +362,9 @@ template <typename T>
 static lbo_status dispatch_lin(lbo_plan* p, const double* params, const double* g, double* out, int B) {
   switch (p->N) {
     case 16: return run_linearized<T, 16>(p, params, g, out, B);
+    case 24: return run_linearized<T, 24>(p, params, g, out, B);
     case 32: return run_linearized<T, 32>(p, params, g, out, B);
+    case 48: return run_linearized<T, 48>(p, params, g, out, B);
     case 64: return run_linearized<T, 64>(p, params, g, out, B);
     default: return LBO_EUNSUPPORTED;
   }
@@ -398,7 +402,7 @@ const char* lbo_last_error(void) { return g_last_error.c_str(); }
 lbo_status lbo_plan_create(int N, double box, double vhs_omega, int radial_nodes, lbo_plan** out) {
   if (!out) return LBO_EINVAL;
   *out = nullptr;
-  if (N != 16 && N != 32 && N != 64) return LBO_EUNSUPPORTED;
+  if (N != 16 && N != 24 && N != 32 && N != 48 && N != 64) return LBO_EUNSUPPORTED;
   if (!(box > 0.0) || !(vhs_omega >= 0.5 && vhs_omega <= 1.0) || radial_nodes < 1 || radial_nodes > 256)
     return LBO_EINVAL;
   lbo_plan* p = new lbo_plan();

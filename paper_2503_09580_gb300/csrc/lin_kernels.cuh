@@ -144,7 +144,7 @@ __device__ __forceinline__ void plane_forward_from_A(cpx<T>* A, cpx<T>* B) {
   for (int t = threadIdx.x; t < PPC * (N / 2) * HC; t += blockDim.x) {
     int k3 = t % HC, rest = t / HC, qq = rest % (N / 2), pp = rest / (N / 2);
     const cpx<T>* z = A + (pp * (N / 2) + qq) * N;
-    cpx<T> z1 = z[pos_of_freq<N>(k3)], z2 = conjc(z[pos_of_freq<N>((N - k3) & (N - 1))]);
+    cpx<T> z1 = z[pos_of_freq<N>(k3)], z2 = conjc(z[pos_of_freq<N>((N - k3) % N)]);
     cpx<T> xa = cscale(z1 + z2, (T)0.5);
     cpx<T> d = z1 - z2;
     cpx<T> xb = make_c((T)0.5 * d.y, (T)-0.5 * d.x);  // (z1 - conj z2) / (2i)

@@ -58,15 +58,7 @@ lbo_status setup_device(int dev) {
   void* ptr = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
   if (e != cudaSuccess || ptr == nullptr) return cuda_fail(e, "noalloc: cudaGetSymbolAddress");
-  double2 d[64];
-  float2 f[64];
-  for (int m = 0; m < 64; ++m) {
-    long double a = -2.0L * 3.14159265358979323846264338327950288L * m / 64.0L;
-    d[m] = make_double2((double)cosl(a), (double)sinl(a));
-    f[m] = make_float2((float)d[m].x, (float)d[m].y);
-  }
-  e = cudaMemcpyToSymbol(c_tw64_d, d, sizeof(d));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw64_f, f, sizeof(f));
+  e = upload_twiddles_now();
   if (e != cudaSuccess) return cuda_fail(e, "noalloc: twiddle upload");
   g_scratch_ptr[dev] = ptr;
   g_ready[dev] = true;
@@ -89,7 +81,7 @@ bool on_device(const void* ptr) {
 }
 
 template <int N>
-struct PPC_ { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : 1); };
+struct PPC_ { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : (N == 24 ? 4 : (N == 48 ? 2 : 1))); };
 
 template <typename K>
 void smem_attr(K kernel, size_t bytes) {
@@ -169,7 +161,9 @@ lbo_status dispatch(const lbo_plan* p, const double* params, const double* g, do
                     unsigned char* ws) {
   switch (p->N) {
     case 16: return run<T, 16>(p, params, g, out, B, ws);
+    case 24: return run<T, 24>(p, params, g, out, B, ws);
     case 32: return run<T, 32>(p, params, g, out, B, ws);
+    case 48: return run<T, 48>(p, params, g, out, B, ws);
     case 64: return run<T, 64>(p, params, g, out, B, ws);
     default: return LBO_EUNSUPPORTED;
   }

@@ -29,7 +29,7 @@ struct QuadState {
 namespace {
 
 template <int N>
-struct PPCq { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : 1); };
+struct PPCq { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : (N == 24 ? 4 : (N == 48 ? 2 : 1))); };
 
 // Product hemisphere rule: p Gauss-Legendre nodes in cos(theta) on (0, 1)
 // times 2p equispaced azimuths; weights sum to 1 (Eq. (2.13) carries 2 pi).
@@ -232,7 +232,9 @@ template <typename T>
 lbo_status dispatch_q(lbo_plan* p, QuadState* qs, const double* f, double* out, int B) {
   switch (p->N) {
     case 16: return run_quadratic<T, 16>(p, qs, f, out, B);
+    case 24: return run_quadratic<T, 24>(p, qs, f, out, B);
     case 32: return run_quadratic<T, 32>(p, qs, f, out, B);
+    case 48: return run_quadratic<T, 48>(p, qs, f, out, B);
     case 64: return run_quadratic<T, 64>(p, qs, f, out, B);
     default: return LBO_EUNSUPPORTED;
   }

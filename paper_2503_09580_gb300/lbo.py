@@ -30,7 +30,8 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_noalloc_bytes_per_instance", "lbo_solver_create", "lbo_newton_step", "lbo_solver_residual",
            "lbo_solver_destroy", "lbo_network_param_count", "lbo_network_loss_grad", "lbo_solver_collect",
            "lbo_solver_pair_count", "lbo_solver_train_network", "lbo_solver_get_network", "lbo_solver_set_network",
-           "lbo_solver_network_param_count")
+           "lbo_solver_network_param_count", "lbo_plan_autotune", "lbo_group_create", "lbo_group_set_stream",
+           "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy")
 
 _lib = None
 
@@ -136,6 +137,19 @@ def load():
     lib.lbo_solver_set_network.restype = ip
     lib.lbo_solver_network_param_count.argtypes = [vp, ip]
     lib.lbo_solver_network_param_count.restype = ip
+    lib.lbo_plan_autotune.argtypes = [vp, dp, dp, dp, ip, ctypes.POINTER(ip)]
+    lib.lbo_plan_autotune.restype = ip
+    lib.lbo_group_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
+    lib.lbo_group_create.restype = ip
+    lib.lbo_group_set_stream.argtypes = [vp, vp]
+    lib.lbo_group_set_stream.restype = ip
+    lib.lbo_group_use_graph.argtypes = [vp, ip]
+    lib.lbo_group_use_graph.restype = ip
+    lib.lbo_group_apply_linearized.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                               ctypes.POINTER(ip)]
+    lib.lbo_group_apply_linearized.restype = ip
+    lib.lbo_group_destroy.argtypes = [vp]
+    lib.lbo_group_destroy.restype = None
     lib.lbo_last_error.argtypes = []
     lib.lbo_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -218,6 +232,15 @@ class Plan:
 
     def sync(self):
         _check(load().lbo_plan_sync(self._h), "lbo_plan_sync")
+
+    def autotune(self, params, g, out):
+        """lbo_plan_autotune on device tensors; returns the chosen shape."""
+        batch = int(params.shape[0])
+        ch = ctypes.c_int()
+        self._stream(params, g, out)
+        _check(load().lbo_plan_autotune(self._h, _ptr(params), _ptr(g), _ptr(out), batch, ctypes.byref(ch)),
+               "lbo_plan_autotune")
+        return ch.value
 
     def solver(self, **kw):
         return Solver(self, **kw)
@@ -350,3 +373,40 @@ def network_loss_grad(hidden, theta, x, t):
                                         ctypes.c_void_p(t.data_ptr()), int(x.shape[0]), int(x.shape[1]),
                                         ctypes.byref(loss), ctypes.c_void_p(grad.data_ptr())), "lbo_network_loss_grad")
     return loss.value, grad
+
+
+class Group:
+    """lbo_group: plans (e.g. of different N) applied together, optionally
+    replayed from a CUDA graph."""
+
+    def __init__(self, plans, graph=False):
+        lib = load()
+        arr = (ctypes.c_void_p * len(plans))(*[p._h.value for p in plans])
+        h = ctypes.c_void_p()
+        _check(lib.lbo_group_create(arr, len(plans), ctypes.byref(h)), "lbo_group_create")
+        self._h, self.plans = h, list(plans)
+        _check(lib.lbo_group_use_graph(h, 1 if graph else 0), "lbo_group_use_graph")
+
+    def apply_linearized(self, params, gs, outs):
+        import torch
+        n = len(self.plans)
+        lib = load()
+        _check(lib.lbo_group_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+               "lbo_group_set_stream")
+        P = (ctypes.c_void_p * n)(*[_ptr(x).value for x in params])
+        G = (ctypes.c_void_p * n)(*[_ptr(x).value for x in gs])
+        O = (ctypes.c_void_p * n)(*[_ptr(x).value for x in outs])
+        B = (ctypes.c_int * n)(*[int(x.shape[0]) for x in params])
+        _check(lib.lbo_group_apply_linearized(self._h, P, G, O, B), "lbo_group_apply_linearized")
+        return outs
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lbo_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -205,3 +205,17 @@ def test_fused_fp32_full_batch_and_moment_fix():
         from oracle.moments import invariant_moments
         m = invariant_moments(grid.to_cyclic(got[b]), n, L)
         assert np.abs(m).max() <= 1e-12 * (2 * L / n) ** 3 * np.abs(got[b]).sum()
+
+
+@pytest.mark.parametrize("n", [24, 48])
+def test_radix3_sizes_fp64(n):
+    """N = 24 and 48 (radix-3 and radix-6 stages) against the oracle."""
+    L = 8.0
+    params, g = workloads.batched_instances(n, L, batch=2, seed=40 + n, noise=0.0)
+    plan = lbo.Plan(n, L, 0.5, n)
+    got = run(plan, params, g)
+    ref = apply_linearized(tables(n, L, 0.5, n), params, g)
+    assert relerr(got, ref) <= 1e-12
+    plan32 = lbo.Plan(n, L, 0.5, n, precision="fp32")
+    got32 = run(plan32, params, g)
+    assert relerr(got32, ref) <= 2.0 ** -24 * ratio_max(params, g, n, L)

@@ -93,3 +93,14 @@ def test_quadratic_bkw_rate_on_gpu():
     plan = lbo.Plan(n, L, 1.0, n, hemisphere_p=3)
     q = run_q(plan, bkw(K)[None])[0]
     assert np.abs(q - dfdt).max() < 2e-4 * np.abs(dfdt).max()
+
+
+def test_quadratic_radix3_size():
+    n, L = 24, 8.0
+    params, g = workloads.batched_instances(n, L, batch=1, seed=33, noise=0.0)
+    f = maxwell_batch(n, L, params) + 0.3 * g
+    plan = lbo.Plan(n, L, 0.74, n, hemisphere_p=1)
+    got = run_q(plan, f)
+    sig, w = hemisphere_rule(1)
+    ref = apply_quadratic(Tables(n, L, 0.74, n), f, sig, w)
+    assert relerr(got, ref) <= 1e-12
