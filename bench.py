@@ -202,6 +202,65 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def newton_leg(precision, kn, nx=128, n=32, L=8.0):
+    """One modified Newton step of the 1-D steady problem: x in [0, 1], nx
+    cells, hard spheres, diffuse walls at theta 1 and 2, initial global
+    Maxwellian rho = 1, u = 0, theta = 1.5, sweep-preconditioned FGMRES."""
+    import torch
+    from paper_2503_09580_gb300 import lbo
+    a = (np.arange(n) - n // 2) * (2 * L / n)
+    v2 = a[:, None, None] ** 2 + a[None, :, None] ** 2 + a[None, None, :] ** 2
+    f0 = np.broadcast_to((2 * np.pi * 1.5) ** -1.5 * np.exp(-v2 / 3.0), (nx, n, n, n)).copy()
+    mass = (1.0 / nx) * (2 * L / n) ** 3 * f0.sum()
+    plan = lbo.Plan(n, L, 0.5, n, precision=precision, hemisphere_p=4)
+    solver = plan.solver(kind="slab", nx=nx, x_left=0.0, x_right=1.0, kn=kn, wall_left=(1.0, 0, 0, 0),
+                         wall_right=(2.0, 0, 0, 0), total_mass=mass, krylov_rtol=1e-3, krylov_atol=1e-7,
+                         krylov_restart=40, krylov_maxit=400, precond="sweep")
+    f = torch.from_numpy(f0).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = solver.newton_step(f)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"ms": 1e3 * dt, "ms_residual": st["ms_residual"], "ms_linear": st["ms_linear"],
+           "krylov_iterations": st["krylov_iterations"], "residual_before": st["residual_norm"],
+           "linear_residual": st["linear_residual"]}
+    solver.close()
+    plan.close()
+    return out
+
+
+def mixed_leg(steps=5):
+    """512 cells with N in {24, 32, 48} (about 50/35/15 %, seeded), FP32,
+    one plan per N applied as a group replayed from a CUDA graph."""
+    import torch
+    from paper_2503_09580_gb300 import lbo, workloads
+    rng = np.random.Generator(np.random.PCG64(7))
+    sizes = rng.choice([24, 32, 48], size=512, p=[0.5, 0.35, 0.15])
+    counts = {n: int((sizes == n).sum()) for n in (24, 32, 48)}
+    plans, ps, gs, outs = [], [], [], []
+    for i, n in enumerate((24, 32, 48)):
+        p, g = workloads.batched_instances(n, 8.0, batch=counts[n], seed=100 + i, noise=1e-3)
+        plans.append(lbo.Plan(n, 8.0, 0.5, n, precision="fp32"))
+        ps.append(torch.from_numpy(p).cuda())
+        gs.append(torch.from_numpy(g).cuda())
+        outs.append(torch.empty_like(gs[-1]))
+    grp = lbo.Group(plans, graph=True)
+    for _ in range(3):
+        grp.apply_linearized(ps, gs, outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        grp.apply_linearized(ps, gs, outs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    grp.close()
+    return {"cells": 512, "counts": counts, "ms_per_step": ms, "value": 512 / (ms * 1e-3), "unit": UNIT,
+            "precision": "fp32", "graph": True}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2503_09580_gb300 import lbo, workloads
@@ -316,6 +375,11 @@ def run_ours(args, world, rank, local):
             got64 = out64.cpu().numpy()[:k]
             line["fp64_plain"]["rel_err_vs_oracle"] = float(np.abs(got64 - ref).max() / np.abs(ref).max())
         p64.close()
+    if rank == 0 and world == 1 and not args.no_extra:
+        line["newton_step"] = {"workload": "1-D steady slab, 128 cells, N=32, hard spheres, walls theta 1/2, "
+                                           "Kn=1, first step from a global Maxwellian theta=1.5",
+                               "fp32": newton_leg("fp32", 1.0), "fp64": newton_leg("fp64", 1.0)}
+        line["mixed_n"] = mixed_leg()
     line["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -339,6 +403,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-instances", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the Newton-step and mixed-N legs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
