@@ -82,6 +82,9 @@ size_t fused32_workspace_bytes(int B, int G);
 int fused32_default_groups(int B);
 lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const double* g, double* out, int B,
                                   void* ws, int G, int* launches);
+size_t quad_fused32_workspace_bytes(int B, int G);
+lbo_status run_quadratic_fused32(lbo_plan* p, const double* f, double* out, int B, void* ws, const double* d_gsw,
+                                 int M, int G, int* launches);
 void free_profile(lbo_plan* p);
 
 // Event bracket around one launch when profiling is on.

@@ -11,6 +11,7 @@
 // The sum over m is taken in real space before the forward transform of
 // each j (the transform is linear), so one application costs 2 J M inverse
 // transforms + J forward transforms + 4.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -24,6 +25,9 @@ struct QuadState {
   std::vector<double> sig, wm;  // M x 3, M
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  double* d_gsw = nullptr;      // device copy: radial nodes, sigma, w_m (fused path)
+  int gsw_p = -1;
+  const void* gsw_plan_tables = nullptr;
 };
 
 namespace {
@@ -246,6 +250,7 @@ void free_quadratic(lbo_plan* p) {
   QuadState* qs = (QuadState*)p->quad;
   if (!qs) return;
   if (qs->ws) cudaFree(qs->ws);
+  if (qs->d_gsw) cudaFree(qs->d_gsw);
   delete qs;
   p->quad = nullptr;
 }
@@ -262,8 +267,10 @@ lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int
     hemisphere_rule(p->hemi_p, qs->sig, qs->wm);
     qs->p = p->hemi_p;
   }
+  const bool fused = p->precision == LBO_PREC_FP32 && p->N == 32 && p->kernel_choice == 0;
+  const int G = fused ? (p->jgroups > 0 ? std::min(p->jgroups, p->J) : std::min(fused32_default_groups(B), p->J)) : 0;
   const size_t N = p->N, H = N * N * (N / 2 + 1), n3 = N * N * N;
-  const size_t need = (size_t)B * (4 * H * 16 + 3 * n3 * 8);
+  const size_t need = fused ? quad_fused32_workspace_bytes(B, G) : (size_t)B * (4 * H * 16 + 3 * n3 * 8);
   if (need > qs->ws_bytes) {
     if (qs->ws) cudaFree(qs->ws);
     qs->ws = nullptr;
@@ -275,6 +282,27 @@ lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int
       return LBO_ENOMEM;
     }
     qs->ws_bytes = need;
+  }
+  if (fused) {
+    // radial nodes, hemisphere nodes and weights on the device
+    if (qs->gsw_p != qs->p || qs->gsw_plan_tables != (const void*)p->d_phi32) {
+      if (qs->d_gsw) cudaFree(qs->d_gsw);
+      qs->d_gsw = nullptr;
+      std::vector<double> h(p->gj);
+      h.insert(h.end(), qs->sig.begin(), qs->sig.end());
+      h.insert(h.end(), qs->wm.begin(), qs->wm.end());
+      e = cudaMalloc(&qs->d_gsw, sizeof(double) * h.size());
+      if (e == cudaSuccess) e = cudaMemcpy(qs->d_gsw, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "quadrature nodes upload");
+      qs->gsw_p = qs->p;
+      qs->gsw_plan_tables = p->d_phi32;
+    }
+    int launches = 0;
+    lbo_status st = run_quadratic_fused32(p, f, out, B, qs->ws, qs->d_gsw, (int)qs->wm.size(), G, &launches);
+    if (st == LBO_OK && (p->mass_fix || p->moment_fix))
+      st = launch_fixes(p, out, B, p->N, 2.0 * p->L / p->N, p->stream, &launches);
+    p->last_launches = launches;
+    return st;
   }
   return p->precision == LBO_PREC_FP64 ? dispatch_q<double>(p, qs, f, out, B) : dispatch_q<float>(p, qs, f, out, B);
 }

@@ -104,3 +104,22 @@ def test_quadratic_radix3_size():
     sig, w = hemisphere_rule(1)
     ref = apply_quadratic(Tables(n, L, 0.74, n), f, sig, w)
     assert relerr(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("jgroups", [1, 3])
+def test_fused_fp32_quadratic_n32(jgroups):
+    """Fused FP32 Q at N = 32 (one block per instance and group of radial
+    nodes) against the FP64 oracle and the generic FP32 kernels."""
+    n, L, p = 32, 8.0, 2
+    params, g = workloads.batched_instances(n, L, batch=3, seed=34, noise=0.0)
+    f = maxwell_batch(n, L, params) + 0.3 * g
+    fused = lbo.Plan(n, L, 0.5, n, hemisphere_p=p, precision="fp32", jgroups=jgroups)
+    generic = lbo.Plan(n, L, 0.5, n, hemisphere_p=p, precision="fp32", kernel=1)
+    a = run_q(fused, f)
+    assert fused.last_launches == 3
+    b = run_q(generic, f)
+    sig, w = hemisphere_rule(p)
+    ref = apply_quadratic(Tables(n, L, 0.5, n), f[:1], sig, w)
+    print("fused Q fp32 vs oracle %.2e, vs generic fp32 %.2e" % (relerr(a[:1], ref), relerr(a, b)))
+    assert relerr(a[:1], ref) <= 2.0 ** -24 * 64
+    assert relerr(a, b) <= 2.0 ** -24 * 64
