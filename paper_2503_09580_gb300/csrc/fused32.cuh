@@ -1,8 +1,12 @@
 // Helpers of the fused FP32 kernels for N = 32 (one block holds a whole
 // instance's half spectrum, 32 x 32 x 17 complex, in shared memory; every
 // axis pass is an in-register 32-point FFT per thread, 544 threads).
-// Shared-memory index of (i1, i2, k3) = i1*544 + i2*17 + k3; the packed row
-// pair (i1, q) occupies the 34 slots of half rows 2q and 2q+1.
+// Shared-memory index of (i1, i2, k3) = i1*561 + (i2/2)*35 + (i2%2)*17 + k3:
+// the packed row pair (i1, q) occupies half rows 2q and 2q+1 (34 slots) of
+// a 35-slot pair, planes are 561 slots apart.  With the odd pair stride the
+// row pass (16 threads of one plane on 16 pairs) and with the odd plane
+// stride the axis passes are free of shared-memory bank conflicts.
+// Global spectra keep the natural index i1*544 + i2*17 + k3.
 #pragma once
 #include "lin_kernels.cuh"
 
@@ -10,6 +14,10 @@ namespace lbo {
 namespace f32 {
 
 constexpr int F_N = 32, F_HC = 17, F_ROW = 544, F_H = 32 * 544, F_THREADS = 544;
+constexpr int S_PAIR = 35, S_PLANE = 16 * S_PAIR + 1, S_TOTAL = 32 * S_PLANE;
+
+// offset of half row i2 inside a shared-memory plane
+__device__ __forceinline__ int srow(int i2) { return (i2 >> 1) * S_PAIR + (i2 & 1) * F_HC; }
 
 // x <- DFT_32(x) (forward: exp(-2 pi i nk/32); inverse: conjugate, unnormalised)
 template <bool INV>
@@ -68,20 +76,19 @@ __device__ __forceinline__ int ksq(int k1, int k2, int k3) {
   return a * a + b * b + k3 * k3;
 }
 
-// In-place axis pass over pencils of V: AXIS 2 -> pencil (i1, k3), stride 17;
-// AXIS 1 -> pencil (i2, k3), stride 544.
+// In-place axis pass over pencils of V: AXIS 2 -> pencil (i1, k3) along i2;
+// AXIS 1 -> pencil (i2, k3) along i1.
 template <int AXIS, bool INV>
 __device__ __forceinline__ void axis_pass(cpx<float>* V) {
   const int t = threadIdx.x;
   const int a = t / F_HC, k3 = t % F_HC;
-  cpx<float>* base = AXIS == 2 ? V + a * F_ROW + k3 : V + a * F_HC + k3;
-  constexpr int st = AXIS == 2 ? F_HC : F_ROW;
+  cpx<float>* base = AXIS == 2 ? V + a * S_PLANE + k3 : V + srow(a) + k3;
   cpx<float> x[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) x[i] = base[i * st];
+  for (int i = 0; i < 32; ++i) x[i] = base[AXIS == 2 ? srow(i) : i * S_PLANE];
   fft32<INV>(x);
 #pragma unroll
-  for (int i = 0; i < 32; ++i) base[i * st] = x[i];
+  for (int i = 0; i < 32; ++i) base[AXIS == 2 ? srow(i) : i * S_PLANE] = x[i];
 }
 
 

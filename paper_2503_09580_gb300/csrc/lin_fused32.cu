@@ -87,7 +87,7 @@ __device__ __forceinline__ void rows_forward(cpx<float>* V, Src src) {
 #pragma unroll
     for (int i3 = 0; i3 < 32; ++i3) z[i3] = src(i1, qq, i3);
     fft32<false>(z);
-    split_store(z, V + i1 * F_ROW + qq * 34);
+    split_store(z, V + i1 * S_PLANE + qq * S_PAIR);
   }
   __syncthreads();
   axis_pass<2, false>(V);
@@ -116,10 +116,10 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_head(FusedArgs a) {
     return make_c(v[0], v[1]);
   });
   const int i2 = t / F_HC, k3 = t % F_HC;
-  cpx<float>* base = V + i2 * F_HC + k3;
+  cpx<float>* base = V + srow(i2) + k3;
   cpx<float> x[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+  for (int i = 0; i < 32; ++i) x[i] = base[i * S_PLANE];
   fft32<false>(x);
   cpx<float>* dst = a.rhat + (size_t)b * F_H + i2 * F_HC + k3;
   const float s = 1.0f / 32768.0f;
@@ -141,16 +141,16 @@ __device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T
     });
     {
       const int i2 = t / F_HC, k3 = t % F_HC;
-      cpx<float>* base = V + i2 * F_HC + k3;
+      cpx<float>* base = V + srow(i2) + k3;
       cpx<float> x[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+      for (int i = 0; i < 32; ++i) x[i] = base[i * S_PLANE];
       fft32<false>(x);
 #pragma unroll
       for (int i = 0; i < 32; ++i) x[i] = cscale(x[i], __ldg(a.omega + ksq(i, i2, k3)));
       fft32<true>(x);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) base[i * F_ROW] = x[i];
+      for (int i = 0; i < 32; ++i) base[i * S_PLANE] = x[i];
     }
     __syncthreads();
     axis_pass<2, true>(V);
@@ -158,7 +158,7 @@ __device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T
     if (t < 512) {
       const int i1 = t >> 4, qq = t & 15;
       cpx<float> z[32];
-      load_merge(V + i1 * F_ROW + qq * 34, z);
+      load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
       fft32<true>(z);
       double* o0 = ob + (i1 * 32 + 2 * qq) * 32;
       const double* g0 = gb + (i1 * 32 + 2 * qq) * 32;
@@ -228,31 +228,31 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
         z[i3 + 3] = make_c(ma * mg[i3 + 3] * p0.w, mb * mg[i3 + 3] * p1.w);
       }
       fft32<false>(z);
-      split_store(z, V + i1 * F_ROW + qq * 34);
+      split_store(z, V + i1 * S_PLANE + qq * S_PAIR);
     }
     __syncthreads();
     axis_pass<2, false>(V);
     __syncthreads();
     {  // axis 1: forward, x r^ (scaled), inverse
       const int i2 = t / F_HC, k3 = t % F_HC;
-      cpx<float>* base = V + i2 * F_HC + k3;
+      cpx<float>* base = V + srow(i2) + k3;
       const cpx<float>* rr = rh + i2 * F_HC + k3;
       cpx<float> x[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+      for (int i = 0; i < 32; ++i) x[i] = base[i * S_PLANE];
       fft32<false>(x);
 #pragma unroll
       for (int i = 0; i < 32; ++i) x[i] = cmul(x[i], rr[i * F_ROW]);
       fft32<true>(x);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) base[i * F_ROW] = x[i];
+      for (int i = 0; i < 32; ++i) base[i * S_PLANE] = x[i];
     }
     __syncthreads();
     axis_pass<2, true>(V);
     __syncthreads();
     if (t < 512) {  // rows: inverse, x M^h, forward
       const int i1 = t >> 4, qq = t & 15;
-      cpx<float>* row = V + i1 * F_ROW + qq * 34;
+      cpx<float>* row = V + i1 * S_PLANE + qq * S_PAIR;
       cpx<float> z[32];
       load_merge(row, z);
       fft32<true>(z);
@@ -270,12 +270,12 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
     __syncthreads();
     {  // axis 1 forward, accumulate phi_j(|k|^2) psi^_j
       const int i2 = t / F_HC, k3 = t % F_HC;
-      cpx<float>* base = V + i2 * F_HC + k3;
+      cpx<float>* base = V + srow(i2) + k3;
       cpx<float>* ac = acc + i2 * F_HC + k3;
       const float* ph = a.phi + (size_t)j * a.Q;
       cpx<float> x[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+      for (int i = 0; i < 32; ++i) x[i] = base[i * S_PLANE];
       fft32<false>(x);
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
@@ -303,9 +303,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_tail(FusedArgs a) {
       for (int i = 0; i < 32; ++i) x[i] = x[i] + src[i * F_ROW];
     }
     fft32<true>(x);
-    cpx<float>* base = V + i2 * F_HC + k3;
+    cpx<float>* base = V + srow(i2) + k3;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) base[i * F_ROW] = x[i];
+    for (int i = 0; i < 32; ++i) base[i * S_PLANE] = x[i];
   }
   __syncthreads();
   axis_pass<2, true>(V);
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_tail(FusedArgs a) {
   if (t < 512) {
     const int i1 = t >> 4, qq = t & 15;
     cpx<float> z[32];
-    load_merge(V + i1 * F_ROW + qq * 34, z);
+    load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
     fft32<true>(z);
     double* o0 = a.out + (size_t)b * 32768 + (i1 * 32 + 2 * qq) * 32;
 #pragma unroll 4
@@ -338,7 +338,7 @@ lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const doubl
                                   void* ws, int G, int* launches) {
   cudaError_t e = upload_twiddles();
   if (e != cudaSuccess) return cuda_fail(e, "fused32 twiddles");
-  const size_t sm = sizeof(cpx<float>) * F_H;
+  const size_t sm = sizeof(cpx<float>) * S_TOTAL;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_f32_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

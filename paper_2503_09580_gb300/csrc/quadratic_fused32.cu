@@ -50,16 +50,16 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_head(QArgs a) {
     for (int i3 = 0; i3 < 32; ++i3)
       z[i3] = make_c((float)fb[(i1 * 32 + 2 * qq) * 32 + i3], (float)fb[(i1 * 32 + 2 * qq + 1) * 32 + i3]);
     fft32<false>(z);
-    split_store(z, V + i1 * F_ROW + qq * 34);
+    split_store(z, V + i1 * S_PLANE + qq * S_PAIR);
   }
   __syncthreads();
   axis_pass<2, false>(V);
   __syncthreads();
   const int i2 = t / F_HC, k3 = t % F_HC;
-  cpx<float>* base = V + i2 * F_HC + k3;
+  cpx<float>* base = V + srow(i2) + k3;
   cpx<float> x[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+  for (int i = 0; i < 32; ++i) x[i] = base[i * S_PLANE];
   fft32<false>(x);
   cpx<float>* dst = a.F + (size_t)b * F_H + i2 * F_HC + k3;
   const float s = 1.0f / 32768.0f;
@@ -80,9 +80,9 @@ __device__ __forceinline__ void phase_axis1(cpx<float>* V, const cpx<float>* Fb,
     x[i] = CONJ ? cmulc(src[i * F_ROW], m) : cmul(src[i * F_ROW], m);
   }
   fft32<true>(x);
-  cpx<float>* base = V + i2 * F_HC + k3;
+  cpx<float>* base = V + srow(i2) + k3;
 #pragma unroll
-  for (int i = 0; i < 32; ++i) base[i * F_ROW] = x[i];
+  for (int i = 0; i < 32; ++i) base[i * S_PLANE] = x[i];
 }
 
 // Scratch layout of a block: element (i3, r) of the row pair owned by thread
@@ -91,7 +91,7 @@ __device__ __forceinline__ void phase_axis1(cpx<float>* V, const cpx<float>* Fb,
 __device__ __forceinline__ void rows_store_tplus(const cpx<float>* V, float* Tp, int t) {
   const int i1 = t >> 4, qq = t & 15;
   cpx<float> z[32];
-  load_merge(V + i1 * F_ROW + qq * 34, z);
+  load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
   fft32<true>(z);
 #pragma unroll
   for (int i3 = 0; i3 < 32; ++i3) {
@@ -104,7 +104,7 @@ __device__ __forceinline__ void rows_accumulate(const cpx<float>* V, const float
                                                 bool first) {
   const int i1 = t >> 4, qq = t & 15;
   cpx<float> z[32];
-  load_merge(V + i1 * F_ROW + qq * 34, z);
+  load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
   fft32<true>(z);
 #pragma unroll
   for (int i3 = 0; i3 < 32; ++i3) {
@@ -130,9 +130,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_gain(QArgs a) {
 #pragma unroll
       for (int i = 0; i < 32; ++i) x[i] = cscale(src[i * F_ROW], 32768.0f * __ldg(a.omega + ksq(i, i2, k3)));
       fft32<true>(x);
-      cpx<float>* base = V + i2 * F_HC + k3;
+      cpx<float>* base = V + srow(i2) + k3;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) base[i * F_ROW] = x[i];
+      for (int i = 0; i < 32; ++i) base[i * S_PLANE] = x[i];
     }
     __syncthreads();
     axis_pass<2, true>(V);
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_gain(QArgs a) {
     if (t < 512) {
       const int i1 = t >> 4, qq = t & 15;
       cpx<float> z[32];
-      load_merge(V + i1 * F_ROW + qq * 34, z);
+      load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
       fft32<true>(z);
       double* o0 = a.out + (size_t)b * 32768 + (i1 * 32 + 2 * qq) * 32;
       const double* f0 = fb + (i1 * 32 + 2 * qq) * 32;
@@ -195,19 +195,19 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_gain(QArgs a) {
 #pragma unroll
       for (int i3 = 0; i3 < 32; ++i3) z[i3] = make_c(Pm[(2 * i3) * 512 + t], Pm[(2 * i3 + 1) * 512 + t]);
       fft32<false>(z);
-      split_store(z, V + i1 * F_ROW + qq * 34);
+      split_store(z, V + i1 * S_PLANE + qq * S_PAIR);
     }
     __syncthreads();
     axis_pass<2, false>(V);
     __syncthreads();
     {
       const int i2 = t / F_HC, k3 = t % F_HC;
-      cpx<float>* base = V + i2 * F_HC + k3;
+      cpx<float>* base = V + srow(i2) + k3;
       cpx<float>* ac = acc + i2 * F_HC + k3;
       const float* ph = a.phi + (size_t)j * a.Q;
       cpx<float> x[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) x[i] = base[i * F_ROW];
+      for (int i = 0; i < 32; ++i) x[i] = base[i * S_PLANE];
       fft32<false>(x);
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
@@ -234,9 +234,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_tail(QArgs a) {
       for (int i = 0; i < 32; ++i) x[i] = x[i] + src[i * F_ROW];
     }
     fft32<true>(x);
-    cpx<float>* base = V + i2 * F_HC + k3;
+    cpx<float>* base = V + srow(i2) + k3;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) base[i * F_ROW] = x[i];
+    for (int i = 0; i < 32; ++i) base[i * S_PLANE] = x[i];
   }
   __syncthreads();
   axis_pass<2, true>(V);
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_tail(QArgs a) {
   if (t < 512) {
     const int i1 = t >> 4, qq = t & 15;
     cpx<float> z[32];
-    load_merge(V + i1 * F_ROW + qq * 34, z);
+    load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
     fft32<true>(z);
     double* o0 = a.out + (size_t)b * 32768 + (i1 * 32 + 2 * qq) * 32;
 #pragma unroll 4
@@ -265,7 +265,7 @@ lbo_status run_quadratic_fused32(lbo_plan* p, const double* f, double* out, int 
                                  int M, int G, int* launches) {
   cudaError_t e = upload_twiddles();
   if (e != cudaSuccess) return cuda_fail(e, "fused Q twiddles");
-  const size_t sm = sizeof(cpx<float>) * F_H;
+  const size_t sm = sizeof(cpx<float>) * S_TOTAL;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_q32_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
