@@ -230,6 +230,41 @@ def newton_leg(precision, kn, nx=128, n=32, L=8.0):
     return out
 
 
+def bkw_leg(precision, steps=1, n=64, L=8.0, dt=0.05):
+    """Backward-Euler steps of the homogeneous equation with the quadratic
+    operator (Maxwell molecules, BKW initial data at K = 0.6), Newton with the
+    linearized operator; error against the BKW closed form."""
+    import torch
+    from paper_2503_09580_gb300 import lbo
+    a = (np.arange(n) - n // 2) * (2 * L / n)
+    v2 = a[:, None, None] ** 2 + a[None, :, None] ** 2 + a[None, None, :] ** 2
+
+    def bkw(t):
+        K = 1 - np.exp(-t / 6)
+        return ((2 * np.pi * K) ** -1.5 * np.exp(-v2 / (2 * K))
+                * ((5 * K - 3) / (2 * K) + (1 - K) / (2 * K * K) * v2))
+    t = 6 * np.log(2.5)
+    plan = lbo.Plan(n, L, 1.0, n, hemisphere_p=4, precision=precision)
+    solver = plan.solver(kind="homogeneous", nx=1, dt=dt, krylov_rtol=1e-10, krylov_atol=0.0,
+                         krylov_restart=20, krylov_maxit=100, precond="none")
+    fn = torch.from_numpy(bkw(t)[None]).cuda()
+    f = fn.clone()
+    newton_ms, iters = [], 0
+    for _ in range(steps):
+        for _ in range(4):
+            st = solver.newton_step(f, fn)
+            newton_ms.append(st["ms_residual"] + st["ms_linear"])
+            iters += 1
+        t += dt
+        fn.copy_(f)
+    ex = bkw(t)
+    err = float(np.abs(f.cpu().numpy()[0] - ex).max() / np.abs(ex).max())
+    solver.close()
+    plan.close()
+    return {"newton_step_ms": float(np.median(newton_ms)), "newton_iterations": iters, "steps": steps,
+            "final_residual": st["residual_norm"], "rel_err_vs_bkw": err}
+
+
 def mixed_leg(steps=5):
     """512 cells with N in {24, 32, 48} (about 50/35/15 %, seeded), FP32,
     one plan per N applied as a group replayed from a CUDA graph."""
@@ -380,6 +415,9 @@ def run_ours(args, world, rank, local):
                                            "Kn=1, first step from a global Maxwellian theta=1.5",
                                "fp32": newton_leg("fp32", 1.0), "fp64": newton_leg("fp64", 1.0)}
         line["mixed_n"] = mixed_leg()
+        line["bkw_n64"] = {"workload": "homogeneous BKW relaxation, Maxwell molecules, N=64, J=64, M=32, "
+                                       "one backward-Euler step dt=0.05 (4 Newton iterations)",
+                           "fp32": bkw_leg("fp32"), "fp64": bkw_leg("fp64")}
     line["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -116,3 +116,30 @@ def test_homogeneous_implicit_euler_bkw():
     err = np.abs(f1 - exact).max() / np.abs(exact).max()
     change = np.abs(exact - fn[0]).max() / np.abs(exact).max()
     assert err < 0.2 * change  # backward Euler: O(dt^2) local error, well below the O(dt) change
+
+
+def test_homogeneous_bkw_n64_fp32_step():
+    """Config of the BKW relaxation at N = 64 (J = 64, M = 32): one backward
+    Euler step in FP32 transforms, Newton to |F| < 1e-8, error against the
+    closed form at the level of the time discretisation."""
+    n, L, dt = 64, 8.0, 0.05
+    a = (np.arange(n) - n // 2) * (2 * L / n)
+    v2 = a[:, None, None] ** 2 + a[None, :, None] ** 2 + a[None, None, :] ** 2
+
+    def bkw(t):
+        K = 1 - np.exp(-t / 6)
+        return ((2 * np.pi * K) ** -1.5 * np.exp(-v2 / (2 * K))
+                * ((5 * K - 3) / (2 * K) + (1 - K) / (2 * K * K) * v2))
+    t0 = 6 * np.log(2.5)
+    plan = lbo.Plan(n, L, 1.0, n, hemisphere_p=4, precision="fp32")
+    solver = plan.solver(kind="homogeneous", nx=1, dt=dt, krylov_rtol=1e-8, krylov_atol=0.0,
+                         krylov_restart=20, krylov_maxit=100, precond="none")
+    fn = torch.from_numpy(bkw(t0)[None]).to(DEV)
+    f = fn.clone()
+    for _ in range(4):
+        st = solver.newton_step(f, fn)
+    assert st["residual_norm"] < 1e-8
+    ex = bkw(t0 + dt)
+    change = np.abs(ex - bkw(t0)).max()
+    err = np.abs(f.cpu().numpy()[0] - ex).max()
+    assert err < 0.2 * change
