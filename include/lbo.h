@@ -151,8 +151,23 @@ lbo_status lbo_plan_profile_get(lbo_plan *plan, int i, const char **name, int *l
 typedef struct lbo_solver lbo_solver;
 
 typedef enum { LBO_PROBLEM_SLAB = 0, LBO_PROBLEM_HOMOGENEOUS = 1 } lbo_problem_kind;
-typedef enum { LBO_PRECOND_NONE = 0, LBO_PRECOND_SWEEP = 1, LBO_PRECOND_LEARNED = 2 } lbo_precond;
+/* NONE: plain FGMRES; SWEEP: the upwind sweep of the source iteration,
+   Eq. (5.7); LEARNED: sweep plus a network-predicted macroscopic correction;
+   MOMENT: sweep plus a Galerkin coarse correction on the five collision
+   invariants of every cell (synthetic acceleration, Sec. 5.2), assembled
+   from the operator once per Newton step and solved by banded LU          */
+typedef enum {
+  LBO_PRECOND_NONE = 0,
+  LBO_PRECOND_SWEEP = 1,
+  LBO_PRECOND_LEARNED = 2,
+  LBO_PRECOND_MOMENT = 3
+} lbo_precond;
 typedef enum { LBO_WALL_FLUX_ANALYTIC = 0, LBO_WALL_FLUX_DISCRETE = 1 } lbo_wall_flux;
+/* Inflow boundary (not in the paper, which treats walls only): the ghost
+ * cell holds the given Maxwellian for the residual and zero for the Newton
+ * correction; with inflow on both sides the total mass C fixes the position
+ * of a steady shock (same bordered constraint as for walls). */
+typedef enum { LBO_BC_WALL = 0, LBO_BC_INFLOW = 1 } lbo_boundary;
 
 typedef struct {
   int kind;               /* lbo_problem_kind                                  */
@@ -161,7 +176,7 @@ typedef struct {
   double kn;              /* Knudsen number (SLAB)                             */
   double wall_left[4];    /* theta, u1, u2, u3 of the left wall (u1 must be 0)  */
   double wall_right[4];
-  double total_mass;      /* C of Eq. (5.3) (SLAB)                             */
+  double total_mass;      /* C of Eq. (5.3) (SLAB; unused when a side is inflow) */
   int wall_flux;          /* lbo_wall_flux: wall density from the analytic
                              half-range flux sqrt(theta/2pi) (Eq. (5.2), the
                              default) or from its grid sum                     */
@@ -171,6 +186,21 @@ typedef struct {
   int krylov_restart;     /* m of GMRES(m), 1..200                             */
   int krylov_maxit;       /* total inner iterations cap                        */
   int precond;            /* lbo_precond                                       */
+  int bc_left, bc_right;  /* lbo_boundary (SLAB): diffuse wall (default) or
+                             inflow of a given Maxwellian                      */
+  double inflow_left[5];  /* rho, u1, u2, u3, theta of the inflow state        */
+  double inflow_right[5];
+  int line_search;        /* 0..60; 0: full Newton steps (the paper's iteration);
+                             k > 0: up to k halvings of the step until the
+                             residual norm decreases (Armijo, c = 1e-4)      */
+  double pseudo_dt;       /* SLAB: 0 for the plain modified Newton step; > 0
+                             turns on pseudo-transient continuation: each step
+                             solves (I/dtau + A) g = R with
+                             dtau = pseudo_dt |R_first| / |R_k|, the shift
+                             also entering the sweep's diagonal             */
+  int coarse_moments;     /* MOMENT preconditioner: 5 (collision invariants)
+                             or 13 (plus traceless stress and heat flux);
+                             other values mean 5                            */
 } lbo_problem;
 
 typedef struct {
@@ -180,11 +210,15 @@ typedef struct {
   int krylov_iterations;
   int restarts;
   int fallbacks;           /* 1 if the learned preconditioner was replaced by the
-                              plain sweep after half of krylov_maxit iterations */
+                              plain sweep after half of krylov_maxit iterations,
+                              or the MOMENT coarse operator was singular and
+                              the sweep ran alone                             */
   int status;              /* lbo_status of the inner solve (LBO_ENOTCONV if the
                               cap was hit; the step is still applied)          */
   double ms_residual;      /* time in the nonlinear residual (Q evaluations)    */
   double ms_linear;        /* time in the linear solve                          */
+  double step_length;      /* lambda of f <- f - lambda g (1 without line search) */
+  double shift;            /* 1/dtau of the step (0 without continuation)       */
 } lbo_newton_stats;
 
 /* Create a solver on top of a plan (the plan supplies N, the box, the

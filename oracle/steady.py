@@ -38,7 +38,7 @@ from .quadratic import quadratic_operator
 class Slab:
     def __init__(self, n, L, omega, J, nx, x_left=-0.5, x_right=0.5, kn=1.0,
                  wall_left=(1.0, 0.0, 0.0, 0.0), wall_right=(2.0, 0.0, 0.0, 0.0),
-                 hemisphere=None, wall_flux="analytic", q_mass_fix=None):
+                 hemisphere=None, wall_flux="analytic", q_mass_fix=None, inflow_left=None, inflow_right=None):
         self.n, self.L, self.nx, self.kn = n, L, nx, kn
         self.tab = Tables(n, L, omega, J)
         self.dx = (x_right - x_left) / nx
@@ -69,16 +69,32 @@ class Slab:
             self.kL = 1.0 / (h3 * (self.vp * self.WL).sum())
             self.kR = 1.0 / (h3 * (-self.vm * self.WR).sum())
         self.q_mass_fix = q_mass_fix
+        # inflow sides (library extension for the shock workload): ghost cell =
+        # the given Maxwellian (rho, u1, u2, u3, theta) for the residual, zero
+        # for a Newton correction
 
-    def ghosts(self, f):
+        def maxwell(st):
+            rho, u1, u2, u3, th = st
+            return rho * (2 * np.pi * th) ** -1.5 * np.exp(
+                -((a[:, None, None] - u1) ** 2 + (v2 - u2) ** 2 + (v3 - u3) ** 2) / (2 * th))
+        self.inL = None if inflow_left is None else maxwell(inflow_left)
+        self.inR = None if inflow_right is None else maxwell(inflow_right)
+
+    def ghosts(self, f, linear=False):
         h3 = self.h ** 3
-        sL = -self.kL * h3 * (self.vm * f[0]).sum()
-        sR = self.kR * h3 * (self.vp * f[-1]).sum()
-        return sL * self.WL, sR * self.WR
+        if self.inL is not None:
+            gl = 0.0 * self.WL if linear else self.inL
+        else:
+            gl = -self.kL * h3 * (self.vm * f[0]).sum() * self.WL
+        if self.inR is not None:
+            gr = 0.0 * self.WR if linear else self.inR
+        else:
+            gr = self.kR * h3 * (self.vp * f[-1]).sum() * self.WR
+        return gl, gr
 
-    def transport(self, f):
+    def transport(self, f, linear=False):
         """v1^+ (f_j - f_{j-1})/dx + v1^- (f_{j+1} - f_j)/dx with ghost cells."""
-        g0, g1 = self.ghosts(f)
+        g0, g1 = self.ghosts(f, linear)
         ext = np.concatenate([g0[None], f, g1[None]], axis=0)
         return (self.vp * (ext[1:-1] - ext[:-2]) + self.vm * (ext[2:] - ext[1:-1])) / self.dx
 
@@ -102,7 +118,7 @@ class Slab:
         def apply(g):
             Lg = np.stack([grid.to_centred(collision_operator(
                 self.tab, p[0], p[1:4], p[4], grid.to_cyclic(g[j]))) for j, p in enumerate(params)])
-            return self.transport(g) - Lg / self.kn
+            return self.transport(g, linear=True) - Lg / self.kn
         return apply
 
     def norm(self, r):
@@ -112,27 +128,27 @@ class Slab:
     def mass(self, f):
         return self.dx * self.h ** 3 * f.sum()
 
-    def sweep(self, r, nu):
+    def sweep(self, r, nu, shift=0.0):
         """Upwind sweep of the source iteration, Eq. (5.7):
-        (v1^+ D^- + v1^- D^+ + nu_j/Kn) z = r, ghost values of z taken as 0."""
+        (v1^+ D^- + v1^- D^+ + nu_j/Kn + shift) z = r, ghost values of z taken as 0."""
         z = np.zeros_like(r)
         c = np.abs(self.v1) / self.dx
         pos, neg = self.v1 > 0, self.v1 < 0
         zero = ~(pos | neg)
         prev = np.zeros(r.shape[1:])
         for j in range(self.nx):
-            d = c + nu[j] / self.kn
+            d = c + nu[j] / self.kn + shift
             zj = np.where(pos, (r[j] + c * prev) / d, 0.0)
             z[j][pos] = zj[pos]
             prev = np.where(pos, zj, 0.0)
         prev = np.zeros(r.shape[1:])
         for j in range(self.nx - 1, -1, -1):
-            d = c + nu[j] / self.kn
+            d = c + nu[j] / self.kn + shift
             zj = np.where(neg, (r[j] + c * prev) / d, 0.0)
             z[j][neg] = zj[neg]
             prev = np.where(neg, zj, 0.0)
         for j in range(self.nx):
-            z[j][zero] = r[j][zero] * self.kn / nu[j]
+            z[j][zero] = r[j][zero] / (nu[j] / self.kn + shift)
         return z
 
     def bordered_operator(self, params, f):
@@ -144,19 +160,29 @@ class Slab:
             return A(g) + e * self.mass(g)
         return apply
 
-    def newton_step(self, f, total_mass, rtol=1e-10, restart=60, maxiter=400):
+    def newton_step(self, f, total_mass, rtol=1e-10, restart=60, maxiter=400, shift=0.0):
         """One modified Newton step: returns (f_new, g, |R(f)|).  GMRES on the
         bordered operator, preconditioned by the upwind sweep with
-        nu_j = rho_j (Eq. (5.7))."""
+        nu_j = rho_j (Eq. (5.7)).  shift > 0 solves (A + shift I) g = R
+        instead: one step of pseudo-transient continuation with
+        dtau = 1/shift (a library extension; the paper's step has shift 0)."""
         from scipy.sparse.linalg import LinearOperator, gmres
         R = self.residual(f)
         params = self.local_params(f)
-        A = self.bordered_operator(params, f)
-        rhs = R + (f / self.mass(f)) * (self.mass(f) - total_mass)
+        if self.inL is None and self.inR is None:
+            A = self.bordered_operator(params, f)
+            rhs = R + (f / self.mass(f)) * (self.mass(f) - total_mass)
+        else:
+            # an inflow side fixes the incoming ghost values: no mass null
+            # mode, and the mass in the slab is set by the boundary fluxes
+            A, rhs = self.linear_operator(params), R
+        if shift:
+            A0 = A
+            A = lambda g: A0(g) + shift * g  # noqa: E731
         shape = f.shape
         n = R.size
         op = LinearOperator((n, n), matvec=lambda x: A(x.reshape(shape)).ravel(), dtype=np.float64)
-        pre = LinearOperator((n, n), matvec=lambda x: self.sweep(x.reshape(shape), params[:, 0]).ravel(),
+        pre = LinearOperator((n, n), matvec=lambda x: self.sweep(x.reshape(shape), params[:, 0], shift).ravel(),
                              dtype=np.float64)
         x, info = gmres(op, rhs.ravel(), rtol=rtol, atol=0.0, restart=restart, maxiter=maxiter, M=pre)
         g = x.reshape(shape)

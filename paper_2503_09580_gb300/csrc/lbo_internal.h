@@ -61,7 +61,9 @@ struct lbo_solver {
   double *part = nullptr, *res = nullptr;  // reduction partials, small results
   double* host = nullptr;                  // pinned small results
   void* netstate = nullptr;                // learned preconditioner (network.cu)
+  void* coarse = nullptr;                  // moment coarse correction (coarse.cu)
   bool force_sweep = false;                // fallback from the learned preconditioner
+  double shift = 0, r_first = 0;           // pseudo-transient shift 1/dtau, first residual norm
 };
 
 namespace lbo {
@@ -71,6 +73,14 @@ lbo_status network_correction(lbo_solver* S, const double* v, double* z);
 lbo_status network_record(lbo_solver* S, const double* w, const double* zk, double* s_scratch,
                           lbo_status (*sweep)(lbo_solver*, const double*, double*));
 void free_network(lbo_solver* S);
+// slab operator A' (with or without the mass border) and y = a x + b y (solver.cu)
+lbo_status solver_apply_op(lbo_solver* S, const double* v, double* out, bool border);
+void solver_axpby(lbo_solver* S, double* y, const double* x, double a, double b);
+// moment coarse correction (coarse.cu)
+lbo_status coarse_assemble(lbo_solver* S, bool border);
+bool coarse_valid(const lbo_solver* S);
+lbo_status coarse_correct(lbo_solver* S, const double* v, double* z);
+void free_coarse(lbo_solver* S);
 void set_error_text(const char* msg);
 // zero-mode removal and/or FP64 conservation projection of out[B][N^3]
 lbo_status launch_fixes(lbo_plan* p, double* out, int B, int N, double h, cudaStream_t s, int* launches);

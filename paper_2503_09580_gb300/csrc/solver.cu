@@ -165,13 +165,15 @@ __global__ void k_mass_finish(const double* __restrict__ part, int nb, double w,
 
 // out = T v * cT + y * cY + e * m(v) * cE, T the upwind transport with
 // diffuse-wall ghost cells (densities res[0], res[1]), m(v) = res[2].
+// Inflow sides pass a fixed ghost factor gL / gR >= 0 (1 for the residual,
+// 0 for the Newton correction); walls pass -1 and use res[0], res[1].
 __global__ void k_transport(const double* __restrict__ v, const double* __restrict__ y,
                             const double* __restrict__ e, const double* __restrict__ res,
                             const double* __restrict__ WL, const double* __restrict__ WR,
                             double* __restrict__ out, int N, int nx, double h, double dx, double cT, double cY,
-                            double cE) {
+                            double cE, double gL, double gR, double cV) {
   const size_t n3 = (size_t)N * N * N, len = n3 * nx;
-  const double sL = res[0], sR = res[1], mv = res[2];
+  const double sL = gL >= 0 ? gL : res[0], sR = gR >= 0 ? gR : res[1], mv = res[2];
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len; t += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(t / n3);
     const size_t k = t % n3;
@@ -185,7 +187,7 @@ __global__ void k_transport(const double* __restrict__ v, const double* __restri
       const double right = j == nx - 1 ? sR * WR[k] : v[t + n3];
       tv = v1 * (right - c) / dx;
     }
-    double o = cT * tv;
+    double o = cT * tv + cV * c;
     if (y) o += cY * y[t];
     if (e) o += cE * mv * e[t];
     out[t] = o;
@@ -195,7 +197,7 @@ __global__ void k_transport(const double* __restrict__ v, const double* __restri
 // Upwind sweep of the source iteration (Eq. (5.7)):
 // (v1^+ D^- + v1^- D^+ + nu_j/Kn) z = r, ghost values of z taken as 0.
 __global__ void k_sweep(const double* __restrict__ r, double* __restrict__ z, const double* __restrict__ nu, int N,
-                        int nx, double h, double dx, double kn) {
+                        int nx, double h, double dx, double kn, double sh) {
   const size_t n3 = (size_t)N * N * N;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n3; k += (size_t)gridDim.x * blockDim.x) {
     const double v1 = (int(k / ((size_t)N * N)) - N / 2) * h;
@@ -203,17 +205,17 @@ __global__ void k_sweep(const double* __restrict__ r, double* __restrict__ z, co
     if (v1 > 0) {
       double prev = 0;
       for (int j = 0; j < nx; ++j) {
-        prev = (r[(size_t)j * n3 + k] + c * prev) / (c + nu[j] / kn);
+        prev = (r[(size_t)j * n3 + k] + c * prev) / (c + nu[j] / kn + sh);
         z[(size_t)j * n3 + k] = prev;
       }
     } else if (v1 < 0) {
       double prev = 0;
       for (int j = nx - 1; j >= 0; --j) {
-        prev = (r[(size_t)j * n3 + k] + c * prev) / (c + nu[j] / kn);
+        prev = (r[(size_t)j * n3 + k] + c * prev) / (c + nu[j] / kn + sh);
         z[(size_t)j * n3 + k] = prev;
       }
     } else {
-      for (int j = 0; j < nx; ++j) z[(size_t)j * n3 + k] = r[(size_t)j * n3 + k] * kn / nu[j];
+      for (int j = 0; j < nx; ++j) z[(size_t)j * n3 + k] = r[(size_t)j * n3 + k] / (nu[j] / kn + sh);
     }
   }
 }
@@ -249,15 +251,23 @@ void wall_mass(lbo_solver* S, const double* v) {
              S->res);
 }
 
-// out = A' v:  SLAB: T v - L v / Kn + e m(v);  HOMOGENEOUS: v - dt L v
-lbo_status apply_op(lbo_solver* S, const double* v, double* out) {
+bool bordered(const lbo_solver* S) {
+  return S->pb.kind == LBO_PROBLEM_SLAB && S->pb.bc_left == LBO_BC_WALL && S->pb.bc_right == LBO_BC_WALL;
+}
+
+// out = A' v:  SLAB: T v - L v / Kn + e m(v) + v / dtau;  HOMOGENEOUS: v - dt L v
+lbo_status apply_op(lbo_solver* S, const double* v, double* out, bool border = true) {
   lbo_status st = lbo_apply_linearized(S->plan, S->params, v, S->Lv, S->nx);
   if (st != LBO_OK) return st;
   cudaStream_t s = S->plan->stream;
   if (S->pb.kind == LBO_PROBLEM_SLAB) {
     wall_mass(S, v);
-    LBO_LAUNCH(S->plan, "solver_transport", s, k_transport, grid_for(S->len), 256, 0, v, S->Lv, S->evec, S->res,
-               S->WL, S->WR, out, S->N, S->nx, S->h, S->dx, 1.0, -1.0 / S->pb.kn, 1.0);
+    // the mass border e m(v) only where both sides are walls: an inflow side
+    // fixes the incoming ghost values, so the operator has no mass null mode
+    const double* ev = border && bordered(S) ? S->evec : nullptr;
+    LBO_LAUNCH(S->plan, "solver_transport", s, k_transport, grid_for(S->len), 256, 0, v, S->Lv, ev, S->res,
+               S->WL, S->WR, out, S->N, S->nx, S->h, S->dx, 1.0, -1.0 / S->pb.kn, 1.0,
+               S->pb.bc_left == LBO_BC_INFLOW ? 0.0 : -1.0, S->pb.bc_right == LBO_BC_INFLOW ? 0.0 : -1.0, S->shift);
   } else {
     if (out != v) cudaMemcpyAsync(out, v, sizeof(double) * S->len, cudaMemcpyDeviceToDevice, s);
     LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, out, S->Lv, -S->pb.dt, 1.0, S->len);
@@ -270,7 +280,7 @@ lbo_status apply_precond(lbo_solver* S, const double* v, double* z);
 
 lbo_status sweep_only(lbo_solver* S, const double* v, double* z) {
   LBO_LAUNCH(S->plan, "solver_sweep", S->plan->stream, k_sweep, grid_for(S->n3), 256, 0, v, z, S->nu, S->N, S->nx,
-             S->h, S->dx, S->pb.kn);
+             S->h, S->dx, S->pb.kn, S->shift);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LBO_OK : cuda_fail(e, "sweep");
 }
@@ -283,7 +293,8 @@ lbo_status residual(lbo_solver* S, const double* f, const double* f_prev, double
   if (S->pb.kind == LBO_PROBLEM_SLAB) {
     wall_mass(S, f);
     LBO_LAUNCH(S->plan, "solver_transport", s, k_transport, grid_for(S->len), 256, 0, f, S->Qf, (const double*)nullptr,
-               S->res, S->WL, S->WR, out, S->N, S->nx, S->h, S->dx, 1.0, -1.0 / S->pb.kn, 0.0);
+               S->res, S->WL, S->WR, out, S->N, S->nx, S->h, S->dx, 1.0, -1.0 / S->pb.kn, 0.0,
+               S->pb.bc_left == LBO_BC_INFLOW ? 1.0 : -1.0, S->pb.bc_right == LBO_BC_INFLOW ? 1.0 : -1.0, 0.0);
   } else {
     // F = f - f_prev - dt Q
     cudaMemcpyAsync(out, f, sizeof(double) * S->len, cudaMemcpyDeviceToDevice, s);
@@ -426,6 +437,14 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
 
 }  // namespace
 
+lbo_status solver_apply_op(lbo_solver* S, const double* v, double* out, bool border) {
+  return apply_op(S, v, out, border);
+}
+
+void solver_axpby(lbo_solver* S, double* y, const double* x, double a, double b) {
+  LBO_LAUNCH(S->plan, "solver_axpby", S->plan->stream, k_axpby, grid_for(S->len), 256, 0, y, x, a, b, S->len);
+}
+
 
 namespace {
 lbo_status apply_precond(lbo_solver* S, const double* v, double* z) {
@@ -435,9 +454,13 @@ lbo_status apply_precond(lbo_solver* S, const double* v, double* z) {
     cudaMemcpyAsync(z, v, sizeof(double) * S->len, cudaMemcpyDeviceToDevice, s);
   } else {
     LBO_LAUNCH(S->plan, "solver_sweep", s, k_sweep, grid_for(S->n3), 256, 0, v, z, S->nu, S->N, S->nx, S->h, S->dx,
-               S->pb.kn);
+               S->pb.kn, S->shift);
     if (pc == LBO_PRECOND_LEARNED && !S->force_sweep) {
       lbo_status st = network_correction(S, v, z);
+      if (st != LBO_OK) return st;
+    }
+    if (pc == LBO_PRECOND_MOMENT) {
+      lbo_status st = coarse_correct(S, v, z);
       if (st != LBO_OK) return st;
     }
   }
@@ -457,15 +480,26 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
   *out = nullptr;
   if (pb->nx < 1 || pb->krylov_restart < 1 || pb->krylov_restart > 200 || pb->krylov_maxit < 1) return LBO_EINVAL;
   if (pb->kind == LBO_PROBLEM_SLAB) {
-    if (!(pb->x_right > pb->x_left) || !(pb->kn > 0) || !(pb->wall_left[0] > 0) || !(pb->wall_right[0] > 0) ||
-        pb->wall_left[1] != 0.0 || pb->wall_right[1] != 0.0 || !(pb->total_mass > 0))
-      return LBO_EINVAL;
+    if (!(pb->x_right > pb->x_left) || !(pb->kn > 0) || !(pb->total_mass > 0)) return LBO_EINVAL;
+    for (int side = 0; side < 2; ++side) {
+      const int bc = side == 0 ? pb->bc_left : pb->bc_right;
+      const double* w = side == 0 ? pb->wall_left : pb->wall_right;
+      const double* in = side == 0 ? pb->inflow_left : pb->inflow_right;
+      if (bc == LBO_BC_WALL) {
+        if (!(w[0] > 0) || w[1] != 0.0) return LBO_EINVAL;
+      } else if (bc == LBO_BC_INFLOW) {
+        if (!(in[0] > 0) || !(in[4] > 0)) return LBO_EINVAL;
+      } else {
+        return LBO_EINVAL;
+      }
+    }
   } else if (pb->kind == LBO_PROBLEM_HOMOGENEOUS) {
     if (!(pb->dt > 0)) return LBO_EINVAL;
   } else {
     return LBO_EINVAL;
   }
-  if (pb->precond < 0 || pb->precond > 2) return LBO_EINVAL;
+  if (pb->precond < 0 || pb->precond > 3) return LBO_EINVAL;
+  if (pb->line_search < 0 || pb->line_search > 60 || !(pb->pseudo_dt >= 0)) return LBO_EINVAL;
   lbo_solver* S = new lbo_solver();
   S->pb = *pb;
   S->plan = plan;
@@ -512,10 +546,15 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
       const int i1 = (int)(k / ((size_t)N * N)), i2 = (int)((k / N) % N), i3 = (int)(k % N);
       const double v[3] = {(i1 - N / 2) * S->h, (i2 - N / 2) * S->h, (i3 - N / 2) * S->h};
       for (int side = 0; side < 2; ++side) {
+        const bool inflow = (side == 0 ? pb->bc_left : pb->bc_right) == LBO_BC_INFLOW;
         const double* wp = side == 0 ? pb->wall_left : pb->wall_right;
-        const double d2 = (v[0] - wp[1]) * (v[0] - wp[1]) + (v[1] - wp[2]) * (v[1] - wp[2]) +
-                          (v[2] - wp[3]) * (v[2] - wp[3]);
-        const double W = std::pow(2.0 * 3.141592653589793 * wp[0], -1.5) * std::exp(-d2 / (2.0 * wp[0]));
+        const double* in = side == 0 ? pb->inflow_left : pb->inflow_right;
+        // wall: unit-density Maxwellian (theta_w, u_w); inflow: the given state
+        const double th = inflow ? in[4] : wp[0], rho = inflow ? in[0] : 1.0;
+        const double* u = inflow ? in + 1 : wp + 1;
+        const double d2 = (v[0] - u[0]) * (v[0] - u[0]) + (v[1] - u[1]) * (v[1] - u[1]) +
+                          (v[2] - u[2]) * (v[2] - u[2]);
+        const double W = rho * std::pow(2.0 * 3.141592653589793 * th, -1.5) * std::exp(-d2 / (2.0 * th));
         (side == 0 ? wl : wr)[k] = W;
       }
       if (v[0] > 0) sumL += v[0] * wl[k];
@@ -526,8 +565,8 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
       S->kL = 1.0 / (h3 * sumL);
       S->kR = 1.0 / (h3 * sumR);
     } else {
-      S->kL = std::sqrt(2.0 * 3.141592653589793 / pb->wall_left[0]);
-      S->kR = std::sqrt(2.0 * 3.141592653589793 / pb->wall_right[0]);
+      S->kL = pb->bc_left == LBO_BC_WALL ? std::sqrt(2.0 * 3.141592653589793 / pb->wall_left[0]) : 0.0;
+      S->kR = pb->bc_right == LBO_BC_WALL ? std::sqrt(2.0 * 3.141592653589793 / pb->wall_right[0]) : 0.0;
     }
     e = cudaMemcpy(S->WL, wl.data(), sizeof(double) * S->n3, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(S->WR, wr.data(), sizeof(double) * S->n3, cudaMemcpyHostToDevice);
@@ -565,7 +604,15 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
   cudaEventRecord(t1, s);
   if (st == LBO_OK) {
     ns->residual_norm = rn;
-    if (S->pb.kind == LBO_PROBLEM_SLAB) {
+    // pseudo-transient continuation: dtau = pseudo_dt |R_first| / |R_k|
+    // (switched evolution relaxation); the shift 1/dtau fades as |R| falls
+    S->shift = 0.0;
+    if (S->pb.kind == LBO_PROBLEM_SLAB && S->pb.pseudo_dt > 0 && rn > 0) {
+      if (S->r_first <= 0) S->r_first = rn;
+      S->shift = rn / (S->pb.pseudo_dt * S->r_first);
+    }
+    ns->shift = S->shift;
+    if (bordered(S)) {
       // bordered system: e = f / m(f), rhs = R + e (m(f) - C)
       wall_mass(S, f);
       double mf = 0;
@@ -575,7 +622,12 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
       LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, S->rhs, S->evec,
                  mf - S->pb.total_mass, 1.0, S->len);
     }
-    st = fgmres(S, ns);
+    if (S->pb.kind == LBO_PROBLEM_SLAB && S->pb.precond == LBO_PRECOND_MOMENT) {
+      // coarse operator about this step's cell parameters (and shift)
+      st = coarse_assemble(S, bordered(S));
+      if (st == LBO_OK && !coarse_valid(S)) ns->fallbacks++;  // singular: sweep alone
+    }
+    if (st == LBO_OK) st = fgmres(S, ns);
     if (st == LBO_OK || st == LBO_ENOTCONV) {
       // FP64 true residual of the linear system
       lbo_status st2 = apply_op(S, S->x, S->w);
@@ -584,8 +636,23 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
         double lr = norm2(S, S->w, &st2);
         ns->linear_residual = lr * std::sqrt(S->wnorm);
       }
-      // f <- f - g
+      // f <- f - lambda g; with line search, halve lambda until the residual
+      // norm decreases by the Armijo factor (the trial residual lands in S->w)
       LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, f, S->x, -1.0, 1.0, S->len);
+      double lambda = 1.0;
+      for (int ls = 0; st2 == LBO_OK && ls < S->pb.line_search; ++ls) {
+        LBO_LAUNCH(S->plan, "solver_moments", s, k_cell_moments, S->nx, 512, 0, f, S->params, (double*)nullptr,
+                   S->N, S->h);
+        double rt = 0;
+        st2 = residual(S, f, f_prev, S->w, &rt);
+        if (st2 != LBO_OK) break;
+        if (std::isfinite(rt) && rt <= (1.0 - 1e-4 * lambda) * rn) break;
+        // back off: f += (lambda / 2) g
+        LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, f, S->x, 0.5 * lambda, 1.0,
+                   S->len);
+        lambda *= 0.5;
+      }
+      ns->step_length = lambda;
       if (st2 != LBO_OK) st = st2;
     }
   }
@@ -612,6 +679,7 @@ void lbo_solver_destroy(lbo_solver* S) {
   for (double* p : bufs)
     if (p) cudaFree(p);
   free_network(S);
+  free_coarse(S);
   if (S->host) cudaFreeHost(S->host);
   delete S;
 }

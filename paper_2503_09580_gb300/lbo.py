@@ -42,7 +42,10 @@ class Problem(ctypes.Structure):
                 ("x_right", ctypes.c_double), ("kn", ctypes.c_double), ("wall_left", ctypes.c_double * 4),
                 ("wall_right", ctypes.c_double * 4), ("total_mass", ctypes.c_double), ("wall_flux", ctypes.c_int),
                 ("dt", ctypes.c_double), ("krylov_rtol", ctypes.c_double), ("krylov_atol", ctypes.c_double),
-                ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int), ("precond", ctypes.c_int),
+                ("bc_left", ctypes.c_int), ("bc_right", ctypes.c_int), ("inflow_left", ctypes.c_double * 5),
+                ("inflow_right", ctypes.c_double * 5), ("line_search", ctypes.c_int),
+                ("pseudo_dt", ctypes.c_double), ("coarse_moments", ctypes.c_int)]
 
 
 class NewtonStats(ctypes.Structure):
@@ -51,14 +54,15 @@ class NewtonStats(ctypes.Structure):
                 ("linear_residual", ctypes.c_double), ("krylov_iterations", ctypes.c_int),
                 ("restarts", ctypes.c_int), ("fallbacks", ctypes.c_int), ("status", ctypes.c_int),
                 ("ms_residual", ctypes.c_double),
-                ("ms_linear", ctypes.c_double)]
+                ("ms_linear", ctypes.c_double), ("step_length", ctypes.c_double),
+                ("shift", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 PROBLEM = {"slab": 0, "homogeneous": 1}
-PRECOND = {"none": 0, "sweep": 1, "learned": 2}
+PRECOND = {"none": 0, "sweep": 1, "learned": 2, "moment": 3}
 WALL_FLUX = {"analytic": 0, "discrete": 1}
 
 
@@ -283,7 +287,8 @@ class Solver:
     def __init__(self, plan, kind="slab", nx=1, x_left=-0.5, x_right=0.5, kn=1.0,
                  wall_left=(1.0, 0.0, 0.0, 0.0), wall_right=(1.0, 0.0, 0.0, 0.0), total_mass=1.0,
                  wall_flux="analytic", dt=0.0, krylov_rtol=1e-3, krylov_atol=1e-7, krylov_restart=30,
-                 krylov_maxit=300, precond="sweep"):
+                 krylov_maxit=300, precond="sweep", inflow_left=None, inflow_right=None, line_search=0,
+                 pseudo_dt=0.0, coarse_moments=5):
         lib = load()
         pb = Problem()
         pb.kind = PROBLEM[kind]
@@ -298,6 +303,15 @@ class Solver:
         pb.krylov_rtol, pb.krylov_atol = float(krylov_rtol), float(krylov_atol)
         pb.krylov_restart, pb.krylov_maxit = int(krylov_restart), int(krylov_maxit)
         pb.precond = PRECOND[precond]
+        # inflow_left / inflow_right: (rho, u1, u2, u3, theta) replaces the wall on that side
+        pb.bc_left = 0 if inflow_left is None else 1
+        pb.bc_right = 0 if inflow_right is None else 1
+        for i in range(5):
+            pb.inflow_left[i] = 0.0 if inflow_left is None else float(inflow_left[i])
+            pb.inflow_right[i] = 0.0 if inflow_right is None else float(inflow_right[i])
+        pb.line_search = int(line_search)
+        pb.pseudo_dt = float(pseudo_dt)
+        pb.coarse_moments = int(coarse_moments)
         h = ctypes.c_void_p()
         _check(lib.lbo_solver_create(ctypes.byref(pb), plan._h, ctypes.byref(h)), "lbo_solver_create")
         self._h, self.plan, self.problem = h, plan, pb

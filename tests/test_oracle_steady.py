@@ -1,0 +1,80 @@
+"""Pins of the oracle's discrete slab problem (Sec. 5, the supplement's upwind
+finite-volume scheme) against properties fixed by its definition: the sweep
+solves its upwind system, diffuse walls conserve mass, a uniform inflow state
+is transport-free, and the continuation step tends to the explicit pseudo-time
+step as dtau -> 0."""
+import numpy as np
+import pytest
+
+from oracle.quadrature import hemisphere_rule
+from oracle.steady import Slab
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def _maxwell(a, st):
+    rho, u1, u2, u3, th = st
+    return rho * (2 * np.pi * th) ** -1.5 * np.exp(
+        -((a[:, None, None] - u1) ** 2 + (a[None, :, None] - u2) ** 2 + (a[None, None, :] - u3) ** 2) / (2 * th))
+
+
+def test_sweep_solves_upwind_system():
+    """z = sweep(r) satisfies v1^+ D^- z + v1^- D^+ z + (nu_j/Kn + s) z = r
+    with zero ghost values, checked cell by cell with explicit neighbours."""
+    S = Slab(8, 5.0, 1.0, 4, nx=5, kn=0.3, hemisphere=hemisphere_rule(1))
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal((5, 8, 8, 8))
+    nu = rng.uniform(0.5, 2.0, 5)
+    for shift in (0.0, 1.7):
+        z = S.sweep(r, nu, shift)
+        for j in range(5):
+            left = z[j - 1] if j > 0 else 0.0 * z[0]
+            right = z[j + 1] if j < 4 else 0.0 * z[0]
+            lhs = (S.vp * (z[j] - left) + S.vm * (right - z[j])) / S.dx + (nu[j] / S.kn + shift) * z[j]
+            assert np.abs(lhs - r[j]).max() <= 1e-12 * np.abs(r).max()
+
+
+def test_discrete_diffuse_walls_conserve_mass():
+    """With the grid-sum wall factor, each wall re-emits exactly the mass
+    that reaches it, so the transport term has zero total mass."""
+    S = Slab(8, 5.0, 1.0, 4, nx=4, kn=1.0, hemisphere=hemisphere_rule(1), wall_flux="discrete",
+             wall_left=(1.0, 0.0, 0.3, 0.0), wall_right=(2.0, 0.0, 0.0, -0.2))
+    rng = np.random.default_rng(4)
+    f = rng.uniform(0.0, 1.0, (4, 8, 8, 8))
+    assert abs(S.mass(S.transport(f))) <= 1e-13 * S.mass(np.abs(S.transport(f)))
+    # a correction's ghost values follow the same linear wall map
+    assert abs(S.mass(S.transport(f - 0.5, linear=True))) <= 1e-12 * S.mass(np.abs(f))
+
+
+def test_uniform_inflow_state_is_transport_free():
+    """Both inflow sides carrying the state that fills the slab: every upwind
+    difference vanishes, and the residual reduces to -Q(M, M)/Kn per cell."""
+    st = (1.3, 0.8, 0.0, 0.0, 1.1)
+    S = Slab(8, 6.0, 0.5, 4, nx=3, kn=0.2, hemisphere=hemisphere_rule(1), inflow_left=st, inflow_right=st)
+    a = (np.arange(8) - 4) * S.h
+    f = np.stack([_maxwell(a, st)] * 3)
+    assert np.abs(S.transport(f)).max() <= 1e-15 * np.abs(f).max() / S.dx
+    # the linear (correction) ghosts are zero: only the boundary cells feel them
+    g = np.stack([_maxwell(a, st)] * 3)
+    tg = S.transport(g, linear=True)
+    assert np.abs(tg[1]).max() <= 1e-15 * np.abs(g).max() / S.dx
+    assert np.allclose(tg[0], S.vp * g[0] / S.dx, rtol=0, atol=1e-15 * np.abs(g).max() / S.dx)
+    assert np.allclose(tg[2], -S.vm * g[2] / S.dx, rtol=0, atol=1e-15 * np.abs(g).max() / S.dx)
+
+
+def test_large_shift_gives_explicit_pseudo_time_step():
+    """(A + s I) g = R with s -> infinity: s g -> R (forward Euler in pseudo
+    time); the deviation is O(|A| / s)."""
+    up = (1.0, 1.2, 0.0, 0.0, 1.0)
+    down = (1.5, 0.8, 0.0, 0.0, 1.3)
+    S = Slab(8, 6.0, 0.5, 4, nx=3, kn=0.5, hemisphere=hemisphere_rule(1), inflow_left=up, inflow_right=down)
+    a = (np.arange(8) - 4) * S.h
+    f = np.stack([_maxwell(a, up), _maxwell(a, (1.2, 1.0, 0.0, 0.0, 1.15)), _maxwell(a, down)])
+    R = S.residual(f)
+    errs = []
+    for s in (1e4, 1e6):
+        _, g, rn = S.newton_step(f.copy(), 0.0, rtol=1e-12, shift=s)
+        assert abs(rn - S.norm(R)) <= 1e-12 * rn
+        errs.append(np.abs(s * g - R).max() / np.abs(R).max())
+    assert errs[1] < 1e-3
+    assert errs[1] < 0.05 * errs[0]  # shrinks like 1/s
