@@ -38,7 +38,7 @@ PEAK_TFLOPS = {"fp64": 4 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12,
                "fp32": 256 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12}
 # DRAM bytes (read + write) per launch of the dominant kernel at the benchmark
 # workload, from ncu (profiles/*.md); None when not captured for this build.
-NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456, ("f32_gain", 32, "fp32"): 252587776}
+NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456}
 
 
 def transform_axis_flops(n):
@@ -58,10 +58,13 @@ KERNEL_POINTWISE = {  # flops per grid point per instance
     "plane_inv_mh_fwd": 2, "axis1_fwd_mul_inv": 3, "axis1_fwd_acc": 4,
 }
 # Fused FP32 kernels (N = 32): whole real 3-D transforms per instance.
-#   head: r^ (1);  gain: 3 per radial node (u^_j, psi_j, psi^_j) plus the
-#   loss term's 4 (g, M forward and back);  tail: the inverse of L^+ (1).
-FUSED_TRANSFORMS = {"f32_head": lambda J: 1, "f32_gain": lambda J: 3 * J + 4, "f32_tail": lambda J: 1}
-FUSED_POINTWISE = {"f32_gain": lambda J: 12 * J}
+#   head: r^ (1);  uhat: u^_j for every radial node (J; computed as a DCT-I
+#   of one octant, counted as the transform it replaces);  gain: 2 per
+#   radial node (psi_j, psi^_j) plus the loss term's 4 (g, M forward and
+#   back);  tail: the inverse of L^+ (1).
+FUSED_TRANSFORMS = {"f32_head": lambda J: 1, "f32_uhat": lambda J: J, "f32_gain": lambda J: 2 * J + 4,
+                    "f32_tail": lambda J: 1}
+FUSED_POINTWISE = {"f32_gain": lambda J: 10 * J, "f32_uhat": lambda J: 2 * J}
 
 
 def kernel_flops_per_instance(name, n, J=None):

@@ -503,7 +503,7 @@ lbo_status lbo_apply_linearized(lbo_plan* p, const double* params, const double*
   }
   if (p->precision == LBO_PREC_FP32 && p->N == 32 && p->kernel_choice == 0) {
     int G = p->jgroups > 0 ? std::min(p->jgroups, p->J) : std::min(fused32_default_groups(batch), p->J);
-    st = ensure_ws_bytes(p, fused32_workspace_bytes(batch, G));
+    st = ensure_ws_bytes(p, fused32_workspace_bytes(batch, G, p->J));
     if (st != LBO_OK) return st;
     int launches = 0;
     st = run_linearized_fused32(p, dp, dg, dout, batch, p->ws, G, &launches);

@@ -88,7 +88,7 @@ void free_quadratic(lbo_plan* p);
 void gauss_legendre(int J, std::vector<double>& x, std::vector<double>& w);
 lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int B);
 // fused FP32 path for N = 32 (lin_fused32.cu)
-size_t fused32_workspace_bytes(int B, int G);
+size_t fused32_workspace_bytes(int B, int G, int J);
 int fused32_default_groups(int B);
 lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const double* g, double* out, int B,
                                   void* ws, int G, int* launches);

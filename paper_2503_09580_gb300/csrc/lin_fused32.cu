@@ -7,15 +7,15 @@
 //   rows   (i1, q):  two real rows 2q, 2q+1 packed as one complex row,
 //                    transformed along i3 and split into two half rows;
 //   axis 2 (i1, k3): pencil along i2;   axis 1 (i2, k3): pencil along i1.
-// Shared-memory index of (i1, i2, k3) = i1*544 + i2*17 + k3; the packed
-// row pair (i1, q) occupies the 34 slots of half rows 2q and 2q+1.
-// Spectra are in natural frequency order (the register FFT has no
-// permutation cost), so r^ and the partial sums use the same index.
+// The shared-memory layout is the one of fused32.cuh.  Spectra are in
+// natural frequency order (the register FFT has no permutation cost), so r^
+// and the partial sums use the same index.
 //
 // Kernels per application of a batch: k_f32_head (r^ = FFT(r) / N^3),
-// k_f32_gain (grid = (j-groups + 1) x batch: partial L^+ per group, and the
-// loss term written into out by the extra block), k_f32_tail (sum of the
-// partials, inverse transform, added to out in FP64).
+// k_f32_uhat (u^_j = FFT(M^g phit_j) of every instance and radial node, as
+// a DCT-I of one octant), k_f32_gain (grid = (j-groups + 1) x batch: partial
+// L^+ per group, and the loss term written into out by the extra block),
+// k_f32_tail (sum of the partials, inverse transform, added to out in FP64).
 #include <cmath>
 
 #include "fused32.cuh"
@@ -33,10 +33,59 @@ struct FusedArgs {
   const float* omega;  // [QMAX], pre-scaled by N^-3
   cpx<float>* rhat;    // [B][F_H], pre-scaled by N^-3
   cpx<float>* part;    // [G][B][F_H] partial L^+ per j-group
+  float* uhat;         // [B][J][U_STRIDE] u^_j = FFT(M^g phit_j) on the octant k in [0,16]^3
   double* out;         // [B][N^3]
   double h, log_inv_eps;
   int cutoff, J, G, B, Q;
 };
+
+// u^_j is real and even in each component of k: M^g phit_j is a real function
+// of |d| on the cyclic grid, so its DFT is the separable DCT-I of the octant
+// d in [0,16]^3 (weights 1 at d = 0 and d = 16, 2 in between), stored for
+// k in [0,16]^3 and read back through k -> min(k, 32 - k).
+constexpr int U_N = 17, U_SZ = U_N * U_N * U_N;
+constexpr int U_STRIDE = 4916;  // U_SZ rounded up to 16-byte rows
+constexpr int U_THREADS = 320;
+
+__device__ __forceinline__ int fold32(int i) { return i <= 16 ? i : 32 - i; }
+
+// c_d cos(pi k d / 16) for k = 0..16, d = 0..7 (c_0 = 1, c_d = 2 otherwise).
+// Pairing d with 16 - d (cos(pi k (16 - d) / 16) = (-1)^k cos(pi k d / 16))
+// splits the length-17 DCT-I into 9 even outputs over x_d + x_(16-d) (plus
+// the middle term 2 x_8 cos(pi k / 2)) and 8 odd outputs over x_d - x_(16-d).
+static __constant__ float c_dct17[17 * 8];
+
+static cudaError_t upload_dct() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  float t[17 * 8];
+  for (int k = 0; k <= 16; ++k)
+    for (int d = 0; d < 8; ++d)
+      t[k * 8 + d] = (float)((d == 0 ? 1.0 : 2.0) * std::cos(3.14159265358979323846 * k * d / 16.0));
+  e = cudaMemcpyToSymbol(c_dct17, t, sizeof(t));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
+// y_k of the DCT-I of x, written to dst[k * stride] as soon as it is formed
+__device__ __forceinline__ void dct17(const float (&x)[U_N], float* dst, int stride) {
+  float ev[8], od[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    ev[d] = x[d] + x[16 - d];
+    od[d] = x[d] - x[16 - d];
+  }
+#pragma unroll
+  for (int k = 0; k <= 16; ++k) {
+    float acc = (k & 1) ? 0.f : ((k & 2) ? -2.f * x[8] : 2.f * x[8]);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) acc = fmaf(c_dct17[k * 8 + d], (k & 1) ? od[d] : ev[d], acc);
+    dst[k * stride] = acc;
+  }
+}
 
 // Per-instance FP64 tables of a CTA.  With a_d(i) = (v_i - u_d)^2 rounded as
 // in the definition, |v-u|^2 = (a_1 + a_2) + a_3 exactly as the oracle forms
@@ -127,6 +176,47 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_head(FusedArgs a) {
   for (int i = 0; i < 32; ++i) dst[i * F_ROW] = cscale(x[i], s);
 }
 
+// u^_j of instance b (block (j, b)): w(d) = rho (pi theta)^-3/2
+// exp(-|d h|^2/theta) phit_j(d) on the octant, then the DCT-I along each axis.
+__global__ void __launch_bounds__(U_THREADS, 4) k_f32_uhat(FusedArgs a) {
+  __shared__ float W[U_SZ];
+  __shared__ float mg[U_N + 1];  // mg[17] = rho (pi theta)^-3/2
+  const int j = blockIdx.x, b = blockIdx.y, t = threadIdx.x;
+  if (t <= U_N) {
+    const double rho = a.params[5 * b], theta = a.params[5 * b + 4];
+    if (t < U_N) {
+      const double x = t * a.h;
+      mg[t] = (float)exp(-(x * x) / theta);
+    } else {
+      mg[U_N] = (float)(rho * pow(3.141592653589793 * theta, -1.5));
+    }
+  }
+  __syncthreads();
+  const float pref = mg[U_N];
+  const float* ph = a.phit + (size_t)j * 32768;
+  for (int e = t; e < U_SZ; e += U_THREADS) {
+    const int d1 = e / (U_N * U_N), d2 = (e / U_N) % U_N, d3 = e % U_N;
+    W[e] = pref * (mg[d1] * mg[d2]) * mg[d3] * __ldg(ph + (d1 * 32 + d2) * 32 + d3);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int axis = 3; axis >= 1; --axis) {
+    if (t < U_N * U_N) {
+      const int p0 = t / U_N, p1 = t % U_N;
+      // pencil start and stride along the transformed axis
+      const int base = axis == 3 ? t * U_N : (axis == 2 ? p0 * U_N * U_N + p1 : t);
+      const int stride = axis == 3 ? 1 : (axis == 2 ? U_N : U_N * U_N);
+      float x[U_N];
+#pragma unroll
+      for (int d = 0; d < U_N; ++d) x[d] = W[base + d * stride];
+      dct17(x, W + base, stride);
+    }
+    __syncthreads();
+  }
+  float* dst = a.uhat + ((size_t)b * a.J + j) * U_STRIDE;
+  for (int e = t; e < U_SZ; e += U_THREADS) dst[e] = W[e];
+}
+
 // Loss term of one instance: out = -InvFFT(FFT(g) omega) M - InvFFT(FFT(M) omega) g.
 __device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T, int b) {
   const int t = threadIdx.x;
@@ -184,7 +274,7 @@ __device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T
 __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   cpx<float>* V = (cpx<float>*)smem;
-  __shared__ float mg[F_N], mh[3 * F_N];
+  __shared__ float mh[3 * F_N];
   __shared__ PrepTables T;
   const int grp = blockIdx.x, b = blockIdx.y, t = threadIdx.x;
   const InstanceParams q = load_params(a.params, b);
@@ -194,55 +284,26 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
     return;
   }
   const int j0 = (a.J * grp) / a.G, j1 = (a.J * (grp + 1)) / a.G;
-  if (t < F_N) {
-    // exp(-|d|^2/theta) for the cyclic displacement d of M^g
-    double d = (double)(t < 16 ? t : t - 32) * a.h;
-    mg[t] = (float)exp(-(d * d) / q.theta);
-  } else if (t < 4 * F_N) {
-    int u = t - F_N, dd = u / F_N, i = u % F_N;
+  if (t < 3 * F_N) {
+    int dd = t / F_N, i = t % F_N;
     double ud = dd == 0 ? q.u1 : (dd == 1 ? q.u2 : q.u3);
     double v = (double)(i - 16) * a.h - ud;
     double e = exp(-(v * v) / q.theta);
     if (dd == 0) e *= q.rho * pow(3.141592653589793 * q.theta, -1.5);
-    mh[u] = (float)e;
+    mh[t] = (float)e;
   }
-  const float pref_g = (float)(q.rho * pow(3.141592653589793 * q.theta, -1.5));
   __syncthreads();
   const cpx<float>* rh = a.rhat + (size_t)b * F_H;
   cpx<float>* acc = a.part + ((size_t)grp * a.B + b) * F_H;
   for (int j = j0; j < j1; ++j) {
-    // u_j = M^g phit_j (cyclic displacement order) -> forward rows, axis 2
-    if (t < 512) {
-      const int i1 = t >> 4, qq = t & 15;
-      const float* ph = a.phit + (size_t)j * 32768 + (i1 * F_N + 2 * qq) * F_N;
-      const float m1 = pref_g * mg[i1];
-      const float ma = m1 * mg[2 * qq], mb = m1 * mg[2 * qq + 1];
-      cpx<float> z[32];
-#pragma unroll
-      for (int i3 = 0; i3 < 32; i3 += 4) {
-        float4 p0 = *(const float4*)(ph + i3);
-        float4 p1 = *(const float4*)(ph + F_N + i3);
-        z[i3 + 0] = make_c(ma * mg[i3 + 0] * p0.x, mb * mg[i3 + 0] * p1.x);
-        z[i3 + 1] = make_c(ma * mg[i3 + 1] * p0.y, mb * mg[i3 + 1] * p1.y);
-        z[i3 + 2] = make_c(ma * mg[i3 + 2] * p0.z, mb * mg[i3 + 2] * p1.z);
-        z[i3 + 3] = make_c(ma * mg[i3 + 3] * p0.w, mb * mg[i3 + 3] * p1.w);
-      }
-      fft32<false>(z);
-      split_store(z, V + i1 * S_PLANE + qq * S_PAIR);
-    }
-    __syncthreads();
-    axis_pass<2, false>(V);
-    __syncthreads();
-    {  // axis 1: forward, x r^ (scaled), inverse
+    {  // axis 1: psi^_j = u^_j r^ (r^ pre-scaled), inverse
       const int i2 = t / F_HC, k3 = t % F_HC;
       cpx<float>* base = V + srow(i2) + k3;
       const cpx<float>* rr = rh + i2 * F_HC + k3;
+      const float* uk = a.uhat + ((size_t)b * a.J + j) * U_STRIDE + fold32(i2) * U_N + k3;
       cpx<float> x[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) x[i] = base[i * S_PLANE];
-      fft32<false>(x);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) x[i] = cmul(x[i], rr[i * F_ROW]);
+      for (int i = 0; i < 32; ++i) x[i] = cscale(rr[i * F_ROW], __ldg(uk + fold32(i) * (U_N * U_N)));
       fft32<true>(x);
 #pragma unroll
       for (int i = 0; i < 32; ++i) base[i * S_PLANE] = x[i];
@@ -326,7 +387,9 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_tail(FusedArgs a) {
 
 }  // namespace
 
-size_t fused32_workspace_bytes(int B, int G) { return (size_t)B * F_H * 8 * (1 + (size_t)G); }
+size_t fused32_workspace_bytes(int B, int G, int J) {
+  return (size_t)B * F_H * 8 * (1 + (size_t)G) + (size_t)B * J * U_STRIDE * sizeof(float);
+}
 
 int fused32_default_groups(int B) {
   // enough CTAs to fill 152 SMs several times over, at most 8 groups
@@ -337,6 +400,7 @@ int fused32_default_groups(int B) {
 lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const double* g, double* out, int B,
                                   void* ws, int G, int* launches) {
   cudaError_t e = upload_twiddles();
+  if (e == cudaSuccess) e = upload_dct();
   if (e != cudaSuccess) return cuda_fail(e, "fused32 twiddles");
   const size_t sm = sizeof(cpx<float>) * S_TOTAL;
   static bool attr = false;
@@ -354,6 +418,7 @@ lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const doubl
   a.omega = p->d_omega32;
   a.rhat = (cpx<float>*)ws;
   a.part = a.rhat + (size_t)B * F_H;
+  a.uhat = (float*)(a.part + (size_t)G * B * F_H);
   a.out = out;
   a.h = 2.0 * p->L / F_N;
   a.log_inv_eps = std::log(1.0 / p->eps);
@@ -364,9 +429,10 @@ lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const doubl
   a.Q = 3 * 16 * 16 + 1;
   cudaStream_t s = p->stream;
   LBO_LAUNCH(p, "f32_head", s, k_f32_head, B, F_THREADS, sm, a);
+  LBO_LAUNCH(p, "f32_uhat", s, k_f32_uhat, dim3(a.J, B), U_THREADS, 0, a);
   LBO_LAUNCH(p, "f32_gain", s, k_f32_gain, dim3(G + 1, B), F_THREADS, sm, a);
   LBO_LAUNCH(p, "f32_tail", s, k_f32_tail, B, F_THREADS, sm, a);
-  *launches += 3;
+  *launches += 4;
   e = cudaGetLastError();
   return e == cudaSuccess ? LBO_OK : cuda_fail(e, "fused32 launch");
 }
