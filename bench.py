@@ -38,7 +38,7 @@ PEAK_TFLOPS = {"fp64": 4 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12,
                "fp32": 256 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12}
 # DRAM bytes (read + write) per launch of the dominant kernel at the benchmark
 # workload, from ncu (profiles/*.md); None when not captured for this build.
-NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456}
+NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456, ("f32_gain", 32, "fp32"): 401499648}
 
 
 def transform_axis_flops(n):
@@ -315,6 +315,8 @@ def run_ours(args, world, rank, local):
     tg = torch.from_numpy(g).to(dev)
     out = torch.empty_like(tg)
     stream = torch.cuda.current_stream(dev)
+    # radial-node groups per CTA of the fused FP32 kernel, timed on this batch
+    jgroups = plan.autotune(tp, tg, out) if not args.no_autotune else 0
     for _ in range(args.warmup):
         plan.apply_linearized(tp, tg, out)
     torch.cuda.synchronize()
@@ -368,6 +370,7 @@ def run_ours(args, world, rank, local):
                    "N": N_GRID, "box": BOX, "vhs_omega": args.omega, "radial_nodes": N_GRID,
                    "batch_per_gpu": BATCH, "precision": args.precision,
                    "eps": args.eps if args.eps is not None else 1e-9,
+                   "jgroups": jgroups if jgroups else "default",
                    "parallelism": "replicas (instances sharded, no collective)" if world > 1 else "single GPU",
                    "l2": "inputs 67 MB + outputs 67 MB + workspace 0.41 GB per step > 129 MB L2"},
         "gpu_launches": launches,
@@ -439,6 +442,7 @@ def main():
     ap.add_argument("--omega", type=float, default=0.5)
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--moment-fix", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default radial-node grouping")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
