@@ -80,11 +80,14 @@ template <typename T, int N>
 static lbo_status build_phit(lbo_plan* p, const double* d_stab, T* d_phit);
 
 static void free_tables(lbo_plan* p) {
-  void* ptrs[] = {p->d_phi64, p->d_omega64, p->d_phit64, p->d_phi32, p->d_omega32, p->d_phit32, p->d_dummy_params};
+  void* ptrs[] = {p->d_phi64, p->d_omega64, p->d_phit64, p->d_phi32, p->d_omega32, p->d_phit32, p->d_dummy_params,
+                  p->d_dct64, p->d_dct32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->d_phi64 = p->d_omega64 = p->d_phit64 = nullptr;
   p->d_phi32 = p->d_omega32 = p->d_phit32 = nullptr;
+  p->d_dct64 = nullptr;
+  p->d_dct32 = nullptr;
   p->d_dummy_params = nullptr;
 }
 
@@ -151,6 +154,22 @@ static lbo_status build_tables(lbo_plan* p) {
     for (int i = 0; i < Q; ++i) fo[i] = (float)om[i];
     TRY(cudaMemcpy(p->d_omega32, fo.data(), sizeof(float) * Q, cudaMemcpyHostToDevice));
   }
+  {
+    // c_d cos(2 pi k d / N), k = 0..N/2, d = 0..N/4-1 (c_0 = 1, c_d = 2)
+    const int HN = N / 2 + 1, Q4 = N / 4;
+    std::vector<double> dc((size_t)HN * Q4);
+    std::vector<float> df(dc.size());
+    for (int k = 0; k < HN; ++k)
+      for (int d = 0; d < Q4; ++d) {
+        long double a = 2.0L * 3.14159265358979323846264338327950288L * ((long double)k * d) / N;
+        dc[(size_t)k * Q4 + d] = (d == 0 ? 1.0 : 2.0) * (double)cosl(a);
+        df[(size_t)k * Q4 + d] = (float)dc[(size_t)k * Q4 + d];
+      }
+    TRY(cudaMalloc(&p->d_dct64, sizeof(double) * dc.size()));
+    TRY(cudaMalloc(&p->d_dct32, sizeof(float) * df.size()));
+    TRY(cudaMemcpy(p->d_dct64, dc.data(), sizeof(double) * dc.size(), cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(p->d_dct32, df.data(), sizeof(float) * df.size(), cudaMemcpyHostToDevice));
+  }
 #undef TRY
   lbo_status s2;
   switch (N) {
@@ -190,9 +209,10 @@ static lbo_status ensure_ws_bytes(lbo_plan* p, size_t bytes) {
 }
 
 static lbo_status ensure_workspace(lbo_plan* p, int batch) {
-  const size_t N = p->N, H = N * N * (N / 2 + 1), n3 = N * N * N;
-  // generic path: 3 half spectra + 3 real fields per instance, sized for FP64
-  return ensure_ws_bytes(p, (size_t)batch * (3 * H * 16 + 3 * n3 * 8));
+  const size_t N = p->N, H = N * N * (N / 2 + 1), n3 = N * N * N, HN = N / 2 + 1;
+  // generic path: 3 half spectra + 3 real fields + the u^_j DCT planes per
+  // instance, sized for FP64
+  return ensure_ws_bytes(p, (size_t)batch * (3 * H * 16 + 3 * n3 * 8 + HN * HN * HN * 8));
 }
 
 static lbo_status ensure_stage(lbo_plan* p, size_t in_doubles, size_t out_doubles, size_t par_doubles) {
@@ -279,7 +299,9 @@ static lbo_status run_linearized(lbo_plan* p, const double* params, const double
   T* R1 = (T*)(LH + (size_t)B * H);
   T* R2 = R1 + (size_t)B * n3;
   T* R3 = R2 + (size_t)B * n3;
+  T* UP = R3 + (size_t)B * n3;  // [B][HC]^3 u^_j after the axis-3 and axis-2 DCTs
   const bool f64 = sizeof(T) == 8;
+  const T* dct = (const T*)(f64 ? (void*)p->d_dct64 : (void*)p->d_dct32);
   const T* phi = (const T*)(f64 ? (void*)p->d_phi64 : (void*)p->d_phi32);
   const T* omg = (const T*)(f64 ? (void*)p->d_omega64 : (void*)p->d_omega32);
   const T* phit = (const T*)(f64 ? (void*)p->d_phit64 : (void*)p->d_phit32);
@@ -287,7 +309,6 @@ static lbo_status run_linearized(lbo_plan* p, const double* params, const double
   const size_t sm = PlaneSmem<T, N, PPC>::BYTES;
   const dim3 gp(N / PPC, B), ga((N * HC + CW - 1) / CW, B), blk(256);
   set_smem(k_plane_fwd<T, N, PPC, SRC_RATIO>, sm);
-  set_smem(k_plane_fwd<T, N, PPC, SRC_U>, sm);
   set_smem(k_plane_fwd<T, N, PPC, SRC_REAL64>, sm);
   set_smem(k_plane_fwd<T, N, PPC, SRC_MAXW>, sm);
   set_smem(k_plane_inv<T, N, PPC, INV_MH_FWD>, sm);
@@ -299,16 +320,19 @@ static lbo_status run_linearized(lbo_plan* p, const double* params, const double
   pa.log_inv_eps = std::log(1.0 / p->eps);
   pa.cutoff = p->cutoff;
   auto kf_ratio = k_plane_fwd<T, N, PPC, SRC_RATIO>;
-  auto kf_u = k_plane_fwd<T, N, PPC, SRC_U>;
   auto kf_real = k_plane_fwd<T, N, PPC, SRC_REAL64>;
   auto kf_maxw = k_plane_fwd<T, N, PPC, SRC_MAXW>;
   auto ki_mh = k_plane_inv<T, N, PPC, INV_MH_FWD>;
   auto ki_real = k_plane_inv<T, N, PPC, INV_TO_REAL>;
   auto ka_fwd = k_axis1<T, N, CW, AX_FWD_STORE>;
-  auto ka_mulc = k_axis1<T, N, CW, AX_FWD_MULC_INV>;
   auto ka_mult = k_axis1<T, N, CW, AX_FWD_MULT_INV>;
   auto ka_acc = k_axis1<T, N, CW, AX_FWD_ACC>;
   auto ka_inv = k_axis1<T, N, CW, AX_INV_STORE>;
+  auto ka_uhat = k_axis1<T, N, CW, AX_UHAT_INV>;
+  constexpr int PL = (256 / HC) < HC ? (256 / HC) : HC;  // octant planes per block
+  auto k_up = k_uhat_planes<T, N, PL>;
+  const size_t sm_up = sizeof(T) * ((size_t)PL * HC * HC + (size_t)HC * (N / 4));
+  set_smem(k_up, sm_up);
   auto k_comb = k_combine<T, N>;
   int launches = 0;
   // r^ = FFT(r), r = g/M with the cut-off (Algorithm 1, gain term)
@@ -317,14 +341,15 @@ static lbo_status run_linearized(lbo_plan* p, const double* params, const double
   LBO_LAUNCH(p, "axis1_fwd", s, ka_fwd, ga, blk, 0, ax, W1, RH);
   launches += 2;
   for (int j = 0; j < p->J; ++j) {
-    // u_j = M^g phit_j ; u^_j = FFT(u_j)
-    pa.phit = phit + (size_t)j * n3;
-    LBO_LAUNCH(p, "plane_fwd_u", s, kf_u, gp, blk, sm, pa, W1);
-    // psi_j = InvFFT(u^_j r^)
+    // u^_j = FFT(M^g phit_j), real and even: DCT-I of the octant, axes 3 and 2
+    LBO_LAUNCH(p, "uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params, phit + (size_t)j * n3,
+               dct, pa.h, UP);
+    // psi_j = InvFFT(u^_j r^), u^_j finished along axis 1 in the same kernel
     Axis1Args a1{};
-    a1.mulc = RH;
+    a1.uplanes = UP;
+    a1.dct = dct;
     a1.scale = 1.0 / (double)n3;
-    LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mulc, ga, blk, 0, a1, W1, W1);
+    LBO_LAUNCH(p, "axis1_uhat_inv", s, ka_uhat, ga, blk, 0, a1, RH, W1);
     // psi_j <- M^h psi_j ; psi^_j = FFT(psi_j)
     LBO_LAUNCH(p, "plane_inv_mh_fwd", s, ki_mh, gp, blk, sm, pa, W1, (T*)nullptr);
     // L^+ += phi_j psi^_j

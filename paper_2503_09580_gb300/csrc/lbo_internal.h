@@ -23,6 +23,8 @@ struct lbo_plan {
   float* d_phi32 = nullptr;
   float* d_omega32 = nullptr;
   float* d_phit32 = nullptr;
+  double* d_dct64 = nullptr;    // [N/2+1][N/4] DCT-I coefficients of u^_j (lin_kernels.cuh)
+  float* d_dct32 = nullptr;
   double* d_dummy_params = nullptr;
   // workspace of the generic path
   void* ws = nullptr;

@@ -300,29 +300,149 @@ enum Axis1Mode {
   AX_FWD_MULC_INV = 1,// dst = F1^-1( F1(src) * mulc * scale ), mulc per instance
   AX_FWD_MULT_INV = 2,// dst = F1^-1( F1(src) * table[|k|^2] )
   AX_FWD_ACC = 3,     // dst (+)= table[|k|^2] * F1(src)
-  AX_INV_STORE = 4    // dst = F1^-1(src)
+  AX_INV_STORE = 4,   // dst = F1^-1(src)
+  AX_UHAT_INV = 5     // dst = F1^-1( src * u^_j(|k|) * scale ), src already axis-1 transformed;
+                      // u^_j from its axes-3,2 DCT planes, finished along axis 1 here
 };
 
 struct Axis1Args {
   const void* mulc;     // [B][H] complex T (AX_FWD_MULC_INV)
   const void* table;    // [QMAX] T (AX_FWD_MULT_INV, AX_FWD_ACC)
-  double scale;         // AX_FWD_MULC_INV
+  double scale;         // AX_FWD_MULC_INV, AX_UHAT_INV
   int first;            // AX_FWD_ACC: store instead of accumulate
+  const void* uplanes;  // [B][N/2+1]^3 T (AX_UHAT_INV): u^_j after the axis-3 and axis-2 DCTs
+  const void* dct;      // [N/2+1][N/4] T (AX_UHAT_INV): DCT-I coefficients
 };
+
+// ------------------------------------------------------------ u^_j as a DCT-I
+// u_j = M^g phit_j depends on the cyclic displacement d only through |d|, so
+// it is real and even in each component of d, and its DFT u^_j is real and
+// even in each component of k.  On the N-point cyclic grid that DFT is the
+// separable DCT-I of length N/2 + 1 of the octant d in [0, N/2]^3:
+//   U(k) = sum_d c_d x_d cos(2 pi k d / N),  c_0 = c_(N/2) = 1, c_d = 2 otherwise.
+// Pairing d with N/2 - d (cos(2 pi k (N/2 - d) / N) = (-1)^k cos(2 pi k d / N))
+// leaves N/4 terms per output: even k over x_d + x_(N/2-d) plus the middle
+// term 2 x_(N/4) cos(pi k / 2), odd k over x_d - x_(N/2-d).
+// dct[k * (N/4) + d] = c_d cos(2 pi k d / N), k = 0..N/2, d = 0..N/4-1.
+template <typename T, int N>
+struct DctPencil {
+  static constexpr int HN = N / 2 + 1, Q4 = N / 4;
+  T ev[Q4], od[Q4], mid;
+  // x_d = src[d * stride], d = 0..N/2
+  __device__ __forceinline__ void load(const T* src, size_t stride) {
+#pragma unroll
+    for (int d = 0; d < Q4; ++d) {
+      const T a = src[d * stride], b = src[(N / 2 - d) * stride];
+      ev[d] = a + b;
+      od[d] = a - b;
+    }
+    mid = src[Q4 * stride];
+  }
+  __device__ __forceinline__ T out(int k, const T* dct) const {
+    T acc;
+    if (k & 1) {
+      acc = (T)0;
+#pragma unroll
+      for (int d = 0; d < Q4; ++d) acc += dct[k * Q4 + d] * od[d];
+    } else {
+      acc = (k & 2) ? (T)-2 * mid : (T)2 * mid;
+#pragma unroll
+      for (int d = 0; d < Q4; ++d) acc += dct[k * Q4 + d] * ev[d];
+    }
+    return acc;
+  }
+};
+
+// Axes 3 and 2 of u^_j for a block of PL octant planes d1 of one instance:
+// w(d) = rho (pi theta)^-3/2 exp(-|d h|^2 / theta) phit_j(d), DCT-I along d3
+// then d2, stored as up[b][d1][k2][k3].  grid = (ceil((N/2+1)/PL), B).
+template <typename T, int N, int PL>
+__global__ void __launch_bounds__(256) k_uhat_planes(const double* __restrict__ params, const T* __restrict__ phit,
+                                                     const T* __restrict__ dct, double h, T* __restrict__ up) {
+  constexpr int HN = N / 2 + 1, Q4 = N / 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* W = (T*)smem_raw;            // [PL][HN][HN]
+  T* tab = W + PL * HN * HN;      // [HN][Q4]
+  __shared__ double mg[HN + 1];   // mg[HN] = rho (pi theta)^-3/2
+  const int b = blockIdx.y, d1_0 = blockIdx.x * PL;
+  const int np = HN - d1_0 < PL ? HN - d1_0 : PL;
+  const double rho = params[5 * b], theta = params[5 * b + 4];
+  for (int t = threadIdx.x; t <= HN; t += blockDim.x) {
+    if (t < HN) {
+      const double x = t * h;
+      mg[t] = exp(-(x * x) / theta);
+    } else {
+      mg[HN] = rho * pow(3.141592653589793 * theta, -1.5);
+    }
+  }
+  for (int t = threadIdx.x; t < HN * Q4; t += blockDim.x) tab[t] = dct[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < np * HN * HN; t += blockDim.x) {
+    const int d3 = t % HN, d2 = (t / HN) % HN, p = t / (HN * HN), d1 = d1_0 + p;
+    const double w = mg[HN] * (mg[d1] * mg[d2]) * mg[d3];
+    W[t] = (T)(w * (double)phit[((size_t)d1 * N + d2) * N + d3]);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < np * HN; t += blockDim.x) {  // axis 3: pencil (p, d2)
+    T* x = W + t * HN;
+    DctPencil<T, N> pen;
+    pen.load(x, 1);
+    for (int k = 0; k < HN; ++k) x[k] = pen.out(k, tab);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < np * HN; t += blockDim.x) {  // axis 2: pencil (p, k3)
+    T* x = W + (t / HN) * HN * HN + t % HN;
+    DctPencil<T, N> pen;
+    pen.load(x, HN);
+    for (int k = 0; k < HN; ++k) x[k * HN] = pen.out(k, tab);
+  }
+  __syncthreads();
+  T* dst = up + ((size_t)b * HN + d1_0) * HN * HN;
+  for (int t = threadIdx.x; t < np * HN * HN; t += blockDim.x) dst[t] = W[t];
+}
 
 template <typename T, int N, int CW, int MODE>
 __global__ void __launch_bounds__(256) k_axis1(Axis1Args a, const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst) {
   constexpr int HC = N / 2 + 1, NC = N * HC;
   __shared__ __align__(16) cpx<T> S[N * CW];
+  __shared__ T Uc[MODE == AX_UHAT_INV ? CW * HC : 1];  // u^_j(|k1|, column)
   const int b = blockIdx.y, c0 = blockIdx.x * CW;
   const size_t inst = (size_t)b * N * NC;
   for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
     int c = t % CW, r = t / CW;
     S[t] = (c0 + c < NC) ? src[inst + (size_t)r * NC + c0 + c] : make_c((T)0, (T)0);
   }
-  __syncthreads();
-  if constexpr (MODE != AX_INV_STORE) smem_fft<T, N, false, true>(S, CW, 1, CW);
-  else smem_fft<T, N, true, true>(S, CW, 1, CW);
+  if constexpr (MODE == AX_UHAT_INV) {
+    // finish u^_j along axis 1 for this tile's columns (|k2|, k3): 8 threads
+    // per column, each forming every 8th output
+    const T* up = (const T*)a.uplanes + (size_t)b * HC * HC * HC;
+    const T* dct = (const T*)a.dct;
+    for (int t = threadIdx.x; t < CW * 8; t += blockDim.x) {
+      const int c = t % CW, gsub = t / CW, col = c0 + c;
+      if (col >= NC) continue;
+      const int p2 = col / HC, k3 = col % HC;
+      int k2 = centred<N>(freq_of_pos<N>(p2));
+      k2 = k2 < 0 ? -k2 : k2;
+      DctPencil<T, N> pen;
+      pen.load(up + (size_t)k2 * HC + k3, (size_t)HC * HC);
+      for (int k = gsub; k < HC; k += 8) Uc[c * HC + k] = pen.out(k, dct);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
+      int c = t % CW, r = t / CW;
+      if (c0 + c < NC) {
+        int k1 = centred<N>(freq_of_pos<N>(r));
+        k1 = k1 < 0 ? -k1 : k1;
+        S[t] = cscale(S[t], (T)(Uc[c * HC + k1] * (T)a.scale));
+      }
+    }
+    __syncthreads();
+    smem_fft<T, N, true, true>(S, CW, 1, CW);
+  } else {
+    __syncthreads();
+    if constexpr (MODE != AX_INV_STORE) smem_fft<T, N, false, true>(S, CW, 1, CW);
+    else smem_fft<T, N, true, true>(S, CW, 1, CW);
+  }
   if constexpr (MODE == AX_FWD_MULC_INV || MODE == AX_FWD_MULT_INV) {
     for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
       int c = t % CW, r = t / CW;

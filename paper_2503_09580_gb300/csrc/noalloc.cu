@@ -66,9 +66,9 @@ lbo_status setup_device(int dev) {
 }
 
 size_t bytes_per_instance(int N, bool f64) {
-  const size_t H = (size_t)N * N * (N / 2 + 1), n3 = (size_t)N * N * N;
+  const size_t H = (size_t)N * N * (N / 2 + 1), n3 = (size_t)N * N * N, HN = N / 2 + 1;
   const size_t re = f64 ? 8 : 4;
-  return 3 * H * 2 * re + 3 * n3 * re;
+  return 3 * H * 2 * re + 3 * n3 * re + HN * HN * HN * re;
 }
 
 bool on_device(const void* ptr) {
@@ -101,20 +101,24 @@ lbo_status run(const lbo_plan* p, const double* params, const double* g, double*
   T* R1 = (T*)(LH + (size_t)B * H);
   T* R2 = R1 + (size_t)B * n3;
   T* R3 = R2 + (size_t)B * n3;
+  T* UP = R3 + (size_t)B * n3;
   const bool f64 = sizeof(T) == 8;
+  const T* dct = (const T*)(f64 ? (const void*)p->d_dct64 : (const void*)p->d_dct32);
   const T* phi = (const T*)(f64 ? (const void*)p->d_phi64 : (const void*)p->d_phi32);
   const T* omg = (const T*)(f64 ? (const void*)p->d_omega64 : (const void*)p->d_omega32);
   const T* phit = (const T*)(f64 ? (const void*)p->d_phit64 : (const void*)p->d_phit32);
   const size_t sm = PlaneSmem<T, N, PPC>::BYTES;
   const dim3 gp(N / PPC, B), ga((N * HC + CW - 1) / CW, B), blk(256);
   auto kf_ratio = k_plane_fwd<T, N, PPC, SRC_RATIO>;
-  auto kf_u = k_plane_fwd<T, N, PPC, SRC_U>;
+  constexpr int PL = (256 / HC) < HC ? (256 / HC) : HC;
+  auto k_up = k_uhat_planes<T, N, PL>;
+  const size_t sm_up = sizeof(T) * ((size_t)PL * HC * HC + (size_t)HC * (N / 4));
   auto kf_real = k_plane_fwd<T, N, PPC, SRC_REAL64>;
   auto kf_maxw = k_plane_fwd<T, N, PPC, SRC_MAXW>;
   auto ki_mh = k_plane_inv<T, N, PPC, INV_MH_FWD>;
   auto ki_real = k_plane_inv<T, N, PPC, INV_TO_REAL>;
   smem_attr(kf_ratio, sm);
-  smem_attr(kf_u, sm);
+  smem_attr(k_up, sm_up);
   smem_attr(kf_real, sm);
   smem_attr(kf_maxw, sm);
   smem_attr(ki_mh, sm);
@@ -129,12 +133,12 @@ lbo_status run(const lbo_plan* p, const double* params, const double* g, double*
   kf_ratio<<<gp, blk, sm, s>>>(pa, W1);
   k_axis1<T, N, CW, AX_FWD_STORE><<<ga, blk, 0, s>>>(ax, W1, RH);
   for (int j = 0; j < p->J; ++j) {
-    pa.phit = phit + (size_t)j * n3;
-    kf_u<<<gp, blk, sm, s>>>(pa, W1);
+    k_up<<<dim3((HC + PL - 1) / PL, B), blk, sm_up, s>>>(params, phit + (size_t)j * n3, dct, pa.h, UP);
     Axis1Args a1{};
-    a1.mulc = RH;
+    a1.uplanes = UP;
+    a1.dct = dct;
     a1.scale = 1.0 / (double)n3;
-    k_axis1<T, N, CW, AX_FWD_MULC_INV><<<ga, blk, 0, s>>>(a1, W1, W1);
+    k_axis1<T, N, CW, AX_UHAT_INV><<<ga, blk, 0, s>>>(a1, RH, W1);
     ki_mh<<<gp, blk, sm, s>>>(pa, W1, (T*)nullptr);
     Axis1Args a2{};
     a2.table = phi + (size_t)j * Q;
