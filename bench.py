@@ -205,7 +205,7 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def newton_leg(precision, kn, nx=128, n=32, L=8.0):
+def newton_leg(precision, kn, nx=128, n=32, L=8.0, residual_precision=None):
     """One modified Newton step of the 1-D steady problem: x in [0, 1], nx
     cells, hard spheres, diffuse walls at theta 1 and 2, initial global
     Maxwellian rho = 1, u = 0, theta = 1.5, sweep-preconditioned FGMRES."""
@@ -219,6 +219,11 @@ def newton_leg(precision, kn, nx=128, n=32, L=8.0):
     solver = plan.solver(kind="slab", nx=nx, x_left=0.0, x_right=1.0, kn=kn, wall_left=(1.0, 0, 0, 0),
                          wall_right=(2.0, 0, 0, 0), total_mass=mass, krylov_rtol=1e-3, krylov_atol=1e-7,
                          krylov_restart=40, krylov_maxit=400, precond="sweep")
+    rplan = None
+    if residual_precision is not None:
+        # the residual's Q(f,f) in its own precision, the Krylov operator in `precision`
+        rplan = lbo.Plan(n, L, 0.5, n, precision=residual_precision, hemisphere_p=4)
+        solver.set_residual_plan(rplan)
     f = torch.from_numpy(f0).cuda()
     # untimed step on a copy: workspaces, tables and the Q state are set up
     # on first use; the timed step then starts from the same state
@@ -233,6 +238,8 @@ def newton_leg(precision, kn, nx=128, n=32, L=8.0):
            "linear_residual": st["linear_residual"]}
     solver.close()
     plan.close()
+    if rplan is not None:
+        rplan.close()
     return out
 
 
@@ -269,6 +276,47 @@ def bkw_leg(precision, steps=1, n=64, L=8.0, dt=0.05):
     plan.close()
     return {"newton_step_ms": float(np.median(newton_ms)), "newton_iterations": iters, "steps": steps,
             "final_residual": st["residual_norm"], "rel_err_vs_bkw": err}
+
+
+def n64_leg(with_oracle, batch=64, steps=3, L=8.0):
+    """L[g] applications/s at N = 64 (J = 64, batch 64, benchmark recipe:
+    per-instance Maxwellians, quartic polynomial + 1e-3 noise), FP32 and
+    FP64; FP32 against FP64 on the whole batch and, with the oracle, both
+    against the oracle on one instance."""
+    import torch
+    from paper_2503_09580_gb300 import lbo, workloads
+    n = 64
+    params, g = workloads.batched_instances(n, L, batch=batch, seed=7, noise=1e-3)
+    tp, tg = torch.from_numpy(params).cuda(), torch.from_numpy(g).cuda()
+    res, outs = {}, {}
+    for prec in ("fp32", "fp64"):
+        plan = lbo.Plan(n, L, 0.5, n, precision=prec)
+        out = torch.empty_like(tg)
+        for _ in range(2):
+            plan.apply_linearized(tp, tg, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.apply_linearized(tp, tg, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[prec] = {"value": batch / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms}
+        outs[prec] = out.cpu().numpy()
+        plan.close()
+    a, b = outs["fp32"], outs["fp64"]
+    res["fp32"]["rel_err_vs_fp64"] = float(max(np.abs(a[i] - b[i]).max() / np.abs(b[i]).max() for i in range(batch)))
+    res["fp32"]["speedup_vs_fp64"] = res["fp32"]["value"] / res["fp64"]["value"]
+    if with_oracle:
+        from oracle.linearized import Tables, apply_linearized
+        t0 = time.perf_counter()
+        ref = apply_linearized(Tables(n, L, 0.5, n), params[:1], g[:1])[0]
+        res["fp64"]["rel_err_vs_oracle"] = float(np.abs(b[0] - ref).max() / np.abs(ref).max())
+        res["fp32"]["rel_err_vs_oracle"] = float(np.abs(a[0] - ref).max() / np.abs(ref).max())
+        res["oracle_seconds_per_instance"] = time.perf_counter() - t0
+    res["workload"] = "batched L[g], N=64, J=64, batch 64, per-instance Maxwellians, quartic + 1e-3 noise"
+    return res
 
 
 def mixed_leg(steps=5):
@@ -422,8 +470,10 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_extra:
         line["newton_step"] = {"workload": "1-D steady slab, 128 cells, N=32, hard spheres, walls theta 1/2, "
                                            "Kn=1, first step from a global Maxwellian theta=1.5",
-                               "fp32": newton_leg("fp32", 1.0), "fp64": newton_leg("fp64", 1.0)}
+                               "fp32": newton_leg("fp32", 1.0), "fp64": newton_leg("fp64", 1.0),
+                               "fp32_operator_fp64_residual": newton_leg("fp32", 1.0, residual_precision="fp64")}
         line["mixed_n"] = mixed_leg()
+        line["n64"] = n64_leg(with_oracle=not args.no_cpu_baseline)
         line["bkw_n64"] = {"workload": "homogeneous BKW relaxation, Maxwell molecules, N=64, J=64, M=32, "
                                        "one backward-Euler step dt=0.05 (4 Newton iterations)",
                            "fp32": bkw_leg("fp32"), "fp64": bkw_leg("fp64")}

@@ -237,6 +237,17 @@ lbo_status lbo_newton_step(lbo_solver *solver, double *f, const double *f_prev, 
 lbo_status lbo_solver_residual(lbo_solver *solver, const double *f, const double *f_prev, double *out,
                                double *norm);
 
+/* Mixed precision: evaluate Q(f,f) of the nonlinear residual with `plan`
+ * (typically an FP64 plan) while the linear operator L of the Krylov solve
+ * keeps the solver's own plan (typically FP32).  The modified Newton step of
+ * Eqs. (5.4), (5.6) only needs an approximate Jacobian, so the state then
+ * converges to the residual's precision.  `plan` must have the solver's N
+ * and box; the solver launches it on its own stream (the plan's stream is
+ * set to the solver plan's stream on every residual evaluation) and does not
+ * own it: keep it alive until the solver is destroyed or the call is undone
+ * with plan = NULL.  LBO_EINVAL on mismatched N or box. */
+lbo_status lbo_solver_set_residual_plan(lbo_solver *solver, lbo_plan *plan);
+
 void lbo_solver_destroy(lbo_solver *solver);
 
 /* Learned preconditioner (SLAB only; no counterpart in the paper: a learned

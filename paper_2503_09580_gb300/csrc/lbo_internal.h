@@ -54,6 +54,7 @@ struct lbo_plan {
 struct lbo_solver {
   lbo_problem pb;
   lbo_plan* plan = nullptr;
+  lbo_plan* rplan = nullptr;  // Q of the residual, if not the solver's own plan
   int N = 0, nx = 0, m = 0;
   size_t n3 = 0, len = 0;
   double h = 0, dx = 1, wnorm = 1, kL = 0, kR = 0;

@@ -287,7 +287,9 @@ lbo_status sweep_only(lbo_solver* S, const double* v, double* z) {
 
 // Nonlinear residual into out (and its weighted norm).
 lbo_status residual(lbo_solver* S, const double* f, const double* f_prev, double* out, double* nrm) {
-  lbo_status st = lbo_apply_quadratic(S->plan, f, S->Qf, S->nx);
+  lbo_plan* qp = S->rplan ? S->rplan : S->plan;
+  qp->stream = S->plan->stream;
+  lbo_status st = lbo_apply_quadratic(qp, f, S->Qf, S->nx);
   if (st != LBO_OK) return st;
   cudaStream_t s = S->plan->stream;
   if (S->pb.kind == LBO_PROBLEM_SLAB) {
@@ -583,6 +585,13 @@ lbo_status lbo_solver_residual(lbo_solver* S, const double* f, const double* f_p
   if (!S || !f || !out) return LBO_EINVAL;
   if (S->pb.kind == LBO_PROBLEM_HOMOGENEOUS && !f_prev) return LBO_EINVAL;
   return residual(S, f, f_prev, out, nrm);
+}
+
+lbo_status lbo_solver_set_residual_plan(lbo_solver* S, lbo_plan* plan) {
+  if (!S) return LBO_EINVAL;
+  if (plan && (plan->N != S->plan->N || plan->L != S->plan->L)) return LBO_EINVAL;
+  S->rplan = plan;
+  return LBO_OK;
 }
 
 lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_newton_stats* stats) {

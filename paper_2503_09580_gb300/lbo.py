@@ -28,7 +28,7 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_status_string", "lbo_last_error", "lbo_plan_profile", "lbo_plan_profile_count",
            "lbo_plan_profile_get", "lbo_apply_linearized_noalloc", "lbo_noalloc_scratch_bytes",
            "lbo_noalloc_bytes_per_instance", "lbo_solver_create", "lbo_newton_step", "lbo_solver_residual",
-           "lbo_solver_destroy", "lbo_network_param_count", "lbo_network_loss_grad", "lbo_solver_collect",
+           "lbo_solver_set_residual_plan", "lbo_solver_destroy", "lbo_network_param_count", "lbo_network_loss_grad", "lbo_solver_collect",
            "lbo_solver_pair_count", "lbo_solver_train_network", "lbo_solver_get_network", "lbo_solver_set_network",
            "lbo_solver_network_param_count", "lbo_plan_autotune", "lbo_group_create", "lbo_group_set_stream",
            "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy")
@@ -122,6 +122,8 @@ def load():
     lib.lbo_newton_step.restype = ip
     lib.lbo_solver_residual.argtypes = [vp, dp, dp, dp, ctypes.POINTER(ctypes.c_double)]
     lib.lbo_solver_residual.restype = ip
+    lib.lbo_solver_set_residual_plan.argtypes = [vp, vp]
+    lib.lbo_solver_set_residual_plan.restype = ip
     lib.lbo_solver_destroy.argtypes = [vp]
     lib.lbo_solver_destroy.restype = None
     lib.lbo_network_param_count.argtypes = [ip]
@@ -365,6 +367,13 @@ class Solver:
         scales = np.ascontiguousarray(scales, dtype=np.float32)
         _check(load().lbo_solver_set_network(self._h, int(hidden), params.ctypes.data_as(ctypes.c_void_p),
                                              scales.ctypes.data_as(ctypes.c_void_p)), "lbo_solver_set_network")
+
+    def set_residual_plan(self, plan):
+        """Evaluate the residual's Q(f,f) with `plan` (e.g. FP64) while the
+        Krylov operator keeps the solver's plan; None undoes it."""
+        _check(load().lbo_solver_set_residual_plan(self._h, None if plan is None else plan._h),
+               "lbo_solver_set_residual_plan")
+        self._rplan = plan  # kept alive with the solver
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
