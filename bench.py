@@ -243,6 +243,53 @@ def newton_leg(precision, kn, nx=128, n=32, L=8.0, residual_precision=None):
     return out
 
 
+def newton_to_tol_leg(mode, tol=1e-10, nx=8, n=32, L=8.0):
+    """Fourier-flow slab (x in [0, 1], nx cells, hard spheres, walls at theta
+    1 and 2, Kn = 1, from a global Maxwellian theta = 1.5) solved to
+    |R| < tol: modified Newton steps while they still gain, then
+    exact-Jacobian steps.  mode 'fp64': everything FP64; 'mixed': the
+    Krylov operator (L, and Q inside the exact Jacobian) in FP32 with the
+    residual's Q in FP64."""
+    import torch
+    from paper_2503_09580_gb300 import lbo
+    a = (np.arange(n) - n // 2) * (2 * L / n)
+    v2 = a[:, None, None] ** 2 + a[None, :, None] ** 2 + a[None, None, :] ** 2
+    f0 = np.broadcast_to((2 * np.pi * 1.5) ** -1.5 * np.exp(-v2 / 3.0), (nx, n, n, n)).copy()
+    mass = (1.0 / nx) * (2 * L / n) ** 3 * f0.sum()
+    p64 = lbo.Plan(n, L, 0.5, n, hemisphere_p=2, mass_fix=1)
+    pop = p64 if mode == "fp64" else lbo.Plan(n, L, 0.5, n, hemisphere_p=2, mass_fix=1, precision="fp32")
+    kw = dict(kind="slab", nx=nx, x_left=0.0, x_right=1.0, kn=1.0, wall_left=(1.0, 0, 0, 0),
+              wall_right=(2.0, 0, 0, 0), total_mass=mass, wall_flux="discrete", krylov_rtol=1e-3,
+              krylov_atol=1e-16, krylov_restart=40, krylov_maxit=400, precond="sweep")
+    mod = pop.solver(**kw)
+    ex = pop.solver(**dict(kw, jacobian="exact", krylov_rtol=1e-6))
+    if mode == "mixed":
+        mod.set_residual_plan(p64)
+        ex.set_residual_plan(p64)
+    f = torch.from_numpy(f0).cuda()
+    steps, its, prev = [], 0, None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(20):
+        use_exact = prev is not None and (prev < 1e-4 or k >= 6)
+        st = (ex if use_exact else mod).newton_step(f)
+        r = st["residual_norm"]
+        steps.append(("exact" if use_exact else "modified", r))
+        its += st["krylov_iterations"]
+        if r < tol:
+            break
+        prev = r
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    out = torch.empty_like(f)
+    judge = p64.solver(**kw)
+    final = judge.residual(f, out)
+    for s in (mod, ex, judge):
+        s.close()
+    return {"seconds": secs, "newton_steps": len(steps), "krylov_iterations": its,
+            "final_residual_fp64": final, "history": [[k, float(r)] for k, r in steps]}
+
+
 def bkw_leg(precision, steps=1, n=64, L=8.0, dt=0.05):
     """Backward-Euler steps of the homogeneous equation with the quadratic
     operator (Maxwell molecules, BKW initial data at K = 0.6), Newton with the
@@ -472,6 +519,10 @@ def run_ours(args, world, rank, local):
                                            "Kn=1, first step from a global Maxwellian theta=1.5",
                                "fp32": newton_leg("fp32", 1.0), "fp64": newton_leg("fp64", 1.0),
                                "fp32_operator_fp64_residual": newton_leg("fp32", 1.0, residual_precision="fp64")}
+        line["newton_to_1e-10"] = {
+            "workload": "1-D steady slab, 8 cells, N=32, hard spheres, walls theta 1/2, Kn=1, from a global "
+                        "Maxwellian; modified steps, then exact-Jacobian steps, until |R| < 1e-10",
+            "fp64": newton_to_tol_leg("fp64"), "fp32_operator_fp64_residual": newton_to_tol_leg("mixed")}
         line["mixed_n"] = mixed_leg()
         line["n64"] = n64_leg(with_oracle=not args.no_cpu_baseline)
         line["bkw_n64"] = {"workload": "homogeneous BKW relaxation, Maxwell molecules, N=64, J=64, M=32, "

@@ -201,6 +201,14 @@ typedef struct {
   int coarse_moments;     /* MOMENT preconditioner: 5 (collision invariants)
                              or 13 (plus traceless stress and heat flux);
                              other values mean 5                            */
+  int jacobian;           /* 0: L about the local Maxwellian of every cell, the
+                             modified step of Eqs. (5.4), (5.6);
+                             1: the exact derivative of the residual,
+                             J v = (Q(f + s v) - Q(f - s v)) / (2 s) with
+                             s = |f| / |v| (exact for the bilinear Q of
+                             Eq. (2.14) up to rounding): two Q evaluations
+                             in the plan's precision per Krylov product,
+                             quadratic convergence near the solution      */
 } lbo_problem;
 
 typedef struct {

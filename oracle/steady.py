@@ -121,6 +121,18 @@ class Slab:
             return self.transport(g, linear=True) - Lg / self.kn
         return apply
 
+    def exact_jacobian(self, f):
+        """g -> transport(g) - (Q(f_j, g_j) + Q(g_j, f_j))/Kn: the derivative
+        of the discrete residual itself (Q(f,f) is the diagonal of the
+        symmetric bilinear form of Eq. (2.14)), in place of the
+        local-Maxwellian L_j of the modified step.  Library extension."""
+        def apply(g):
+            J = np.stack([grid.to_centred(quadratic_operator(
+                self.tab, grid.to_cyclic(f[j]), self.sig, self.wm, g=grid.to_cyclic(g[j]),
+                mass_fix=self.q_mass_fix)) for j in range(self.nx)])
+            return self.transport(g, linear=True) - J / self.kn
+        return apply
+
     def norm(self, r):
         """Discrete L2 norm sqrt(dx h^3 sum r^2), Sec. 5.3."""
         return np.sqrt(self.dx * self.h ** 3 * (r * r).sum())
@@ -151,31 +163,35 @@ class Slab:
             z[j][zero] = r[j][zero] / (nu[j] / self.kn + shift)
         return z
 
-    def bordered_operator(self, params, f):
+    def bordered_operator(self, params, f, jacobian="local_maxwellian"):
         """A'(g) = A g + e m(g) with e = f / m(f)."""
-        A = self.linear_operator(params)
+        A = self.exact_jacobian(f) if jacobian == "exact" else self.linear_operator(params)
         e = f / self.mass(f)
 
         def apply(g):
             return A(g) + e * self.mass(g)
         return apply
 
-    def newton_step(self, f, total_mass, rtol=1e-10, restart=60, maxiter=400, shift=0.0):
+    def newton_step(self, f, total_mass, rtol=1e-10, restart=60, maxiter=400, shift=0.0,
+                    jacobian="local_maxwellian"):
         """One modified Newton step: returns (f_new, g, |R(f)|).  GMRES on the
         bordered operator, preconditioned by the upwind sweep with
         nu_j = rho_j (Eq. (5.7)).  shift > 0 solves (A + shift I) g = R
         instead: one step of pseudo-transient continuation with
-        dtau = 1/shift (a library extension; the paper's step has shift 0)."""
+        dtau = 1/shift (a library extension; the paper's step has shift 0).
+        jacobian="exact" uses exact_jacobian in place of the local-Maxwellian
+        L_j (full Newton; also a library extension)."""
         from scipy.sparse.linalg import LinearOperator, gmres
         R = self.residual(f)
         params = self.local_params(f)
         if self.inL is None and self.inR is None:
-            A = self.bordered_operator(params, f)
+            A = self.bordered_operator(params, f, jacobian)
             rhs = R + (f / self.mass(f)) * (self.mass(f) - total_mass)
         else:
             # an inflow side fixes the incoming ghost values: no mass null
             # mode, and the mass in the slab is set by the boundary fluxes
-            A, rhs = self.linear_operator(params), R
+            A = self.exact_jacobian(f) if jacobian == "exact" else self.linear_operator(params)
+            rhs = R
         if shift:
             A0 = A
             A = lambda g: A0(g) + shift * g  # noqa: E731

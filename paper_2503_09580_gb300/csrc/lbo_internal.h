@@ -67,6 +67,9 @@ struct lbo_solver {
   void* coarse = nullptr;                  // moment coarse correction (coarse.cu)
   bool force_sweep = false;                // fallback from the learned preconditioner
   double shift = 0, r_first = 0;           // pseudo-transient shift 1/dtau, first residual norm
+  const double* fcur = nullptr;            // state of the current step (exact Jacobian)
+  double fnorm = 0;                        // its Euclidean norm
+  double *ja = nullptr, *jb = nullptr;     // f +- s v and their Q (exact Jacobian)
 };
 
 namespace lbo {

@@ -255,9 +255,38 @@ bool bordered(const lbo_solver* S) {
   return S->pb.kind == LBO_PROBLEM_SLAB && S->pb.bc_left == LBO_BC_WALL && S->pb.bc_right == LBO_BC_WALL;
 }
 
+// Lv = J_Q v = (Q(f + s v) - Q(f - s v)) / (2 s), s = |f| / |v|: exact for
+// the bilinear Q up to rounding, balanced so that s v is of the size of f.
+lbo_status exact_jacobian_q(lbo_solver* S, const double* v) {
+  cudaStream_t s = S->plan->stream;
+  lbo_status st = LBO_OK;
+  const double vn = norm2(S, v, &st);
+  if (st != LBO_OK) return st;
+  if (!(vn > 0)) {
+    cudaMemsetAsync(S->Lv, 0, sizeof(double) * S->len, s);
+    return LBO_OK;
+  }
+  const double sc = S->fnorm > 0 ? S->fnorm / vn : 1.0;
+  for (int side = 0; side < 2; ++side) {
+    double* x = side == 0 ? S->ja : S->jb;
+    cudaMemcpyAsync(x, S->fcur, sizeof(double) * S->len, cudaMemcpyDeviceToDevice, s);
+    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, x, v, side == 0 ? sc : -sc, 1.0,
+               S->len);
+  }
+  S->plan->stream = s;
+  st = lbo_apply_quadratic(S->plan, S->ja, S->Lv, S->nx);  // Q(f + s v)
+  if (st == LBO_OK) st = lbo_apply_quadratic(S->plan, S->jb, S->ja, S->nx);  // Q(f - s v)
+  if (st != LBO_OK) return st;
+  LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, S->Lv, S->ja, -0.5 / sc, 0.5 / sc,
+             S->len);
+  return LBO_OK;
+}
+
 // out = A' v:  SLAB: T v - L v / Kn + e m(v) + v / dtau;  HOMOGENEOUS: v - dt L v
+// (L v replaced by the exact J_Q v when the problem asks for the exact Jacobian)
 lbo_status apply_op(lbo_solver* S, const double* v, double* out, bool border = true) {
-  lbo_status st = lbo_apply_linearized(S->plan, S->params, v, S->Lv, S->nx);
+  lbo_status st = S->pb.jacobian == 1 ? exact_jacobian_q(S, v)
+                                      : lbo_apply_linearized(S->plan, S->params, v, S->Lv, S->nx);
   if (st != LBO_OK) return st;
   cudaStream_t s = S->plan->stream;
   if (S->pb.kind == LBO_PROBLEM_SLAB) {
@@ -502,6 +531,7 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
   }
   if (pb->precond < 0 || pb->precond > 3) return LBO_EINVAL;
   if (pb->line_search < 0 || pb->line_search > 60 || !(pb->pseudo_dt >= 0)) return LBO_EINVAL;
+  if (pb->jacobian < 0 || pb->jacobian > 1) return LBO_EINVAL;
   lbo_solver* S = new lbo_solver();
   S->pb = *pb;
   S->plan = plan;
@@ -525,6 +555,10 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
   alloc(&S->rhs, len);
   alloc(&S->x, len);
   alloc(&S->evec, len);
+  if (pb->jacobian == 1) {
+    alloc(&S->ja, len);
+    alloc(&S->jb, len);
+  }
   alloc(&S->Qf, len);
   alloc(&S->params, 5 * (size_t)S->nx);
   alloc(&S->nu, S->nx);
@@ -611,6 +645,10 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
   double rn = 0;
   lbo_status st = residual(S, f, f_prev, S->rhs, &rn);
   cudaEventRecord(t1, s);
+  if (st == LBO_OK && S->pb.jacobian == 1) {
+    S->fcur = f;  // f stays unchanged until the linear solve is done
+    S->fnorm = norm2(S, f, &st);
+  }
   if (st == LBO_OK) {
     ns->residual_norm = rn;
     // pseudo-transient continuation: dtau = pseudo_dt |R_first| / |R_k|
@@ -683,8 +721,8 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
 
 void lbo_solver_destroy(lbo_solver* S) {
   if (!S) return;
-  double* bufs[] = {S->V, S->Z, S->w, S->Lv, S->rhs, S->x, S->evec, S->Qf, S->params, S->nu, S->WL, S->WR,
-                    S->part, S->res};
+  double* bufs[] = {S->V,      S->Z,  S->w,  S->Lv, S->rhs, S->x,    S->evec, S->ja,
+                    S->jb,     S->Qf, S->params, S->nu, S->WL,  S->WR, S->part, S->res};
   for (double* p : bufs)
     if (p) cudaFree(p);
   free_network(S);

@@ -78,3 +78,26 @@ def test_large_shift_gives_explicit_pseudo_time_step():
         errs.append(np.abs(s * g - R).max() / np.abs(R).max())
     assert errs[1] < 1e-3
     assert errs[1] < 0.05 * errs[0]  # shrinks like 1/s
+
+
+def test_exact_jacobian_is_the_derivative_of_the_residual():
+    """R is quadratic in f (transport is linear, Q(f,f) is the diagonal of a
+    symmetric bilinear form), so its central difference is exact for any
+    step: (R(f + e g) - R(f - e g)) / (2 e) equals the exact Jacobian applied
+    to g, which the oracle forms from the bilinear form instead of Q(f,f).
+    With walls the ghost map is linear too; the check holds for both sides."""
+    for inflow in (False, True):
+        kw = dict(inflow_left=(1.0, 0.6, 0.0, 0.0, 1.0), inflow_right=(1.3, 0.4, 0.0, 0.0, 1.2)) if inflow else {}
+        S = Slab(8, 6.0, 0.5, 4, nx=3, kn=0.4, hemisphere=hemisphere_rule(1), wall_flux="discrete", **kw)
+        a = (np.arange(8) - 4) * S.h
+        f = np.stack([_maxwell(a, (1.0 + 0.1 * j, 0.2 * j, 0.0, 0.1, 1.0 + 0.2 * j)) for j in range(3)])
+        rng = np.random.default_rng(5)
+        g = rng.standard_normal(f.shape) * f
+        Jg = S.exact_jacobian(f)(g)
+        if not inflow:  # the residual's ghost cells are the linear wall map of f
+            for e in (1e-3, 0.7):
+                fd = (S.residual(f + e * g) - S.residual(f - e * g)) / (2 * e)
+                assert np.abs(fd - Jg).max() <= 1e-9 * np.abs(Jg).max()
+        else:  # inflow ghosts are constant data: they cancel in the difference
+            fd = (S.residual(f + 0.5 * g) - S.residual(f - 0.5 * g)) / 1.0
+            assert np.abs(fd - Jg).max() <= 1e-9 * np.abs(Jg).max()
