@@ -290,6 +290,48 @@ def newton_to_tol_leg(mode, tol=1e-10, nx=8, n=32, L=8.0):
             "final_residual_fp64": final, "history": [[k, float(r)] for k, r in steps]}
 
 
+def shock_leg(precond, nx=128, n=32, L=8.0, tol=1e-10):
+    """Planar Mach-2 shock: x in [-1, 1], nx cells, hard spheres, Kn = 0.1,
+    Rankine-Hugoniot inflow states (gamma = 5/3), tanh start; pseudo-
+    transient continuation (dtau from 0.3) with exact-Jacobian Newton steps,
+    Krylov operator in FP32 and residual in FP64, until |R| < tol."""
+    import torch
+    from paper_2503_09580_gb300 import lbo
+    gam, mach = 5.0 / 3.0, 2.0
+    u1 = mach * np.sqrt(gam)
+    r = (gam + 1) * mach ** 2 / ((gam - 1) * mach ** 2 + 2)
+    p2 = 1 + 2 * gam / (gam + 1) * (mach ** 2 - 1)
+    up, down = (1.0, u1, 0.0, 0.0, 1.0), (r, u1 / r, 0.0, 0.0, p2 / r)
+    x = -1.0 + (np.arange(nx) + 0.5) * (2.0 / nx)
+    a = (np.arange(n) - n // 2) * (2 * L / n)
+    f = []
+    for wj in 0.5 * (1 + np.tanh(x / 0.15)):
+        rho, uu, _, _, th = [(1 - wj) * p + wj * q for p, q in zip(up, down)]
+        f.append(rho * (2 * np.pi * th) ** -1.5 * np.exp(-((a[:, None, None] - uu) ** 2 + a[None, :, None] ** 2
+                                                           + a[None, None, :] ** 2) / (2 * th)))
+    p32 = lbo.Plan(n, L, 0.5, n, hemisphere_p=2, precision="fp32", mass_fix=1)
+    p64 = lbo.Plan(n, L, 0.5, n, hemisphere_p=2, mass_fix=1)
+    solver = p32.solver(kind="slab", nx=nx, x_left=-1.0, x_right=1.0, kn=0.1, total_mass=1.0, inflow_left=up,
+                        inflow_right=down, krylov_rtol=1e-3, krylov_atol=1e-14, krylov_restart=40,
+                        krylov_maxit=600, precond=precond, pseudo_dt=0.3, jacobian="exact")
+    solver.set_residual_plan(p64)
+    tf = torch.from_numpy(np.stack(f)).cuda()
+    steps, its = [], 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(30):
+        st = solver.newton_step(tf)
+        steps.append(float(st["residual_norm"]))
+        its += st["krylov_iterations"]
+        if st["residual_norm"] < tol:
+            break
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    solver.close()
+    return {"seconds": secs, "newton_steps": len(steps), "krylov_iterations": its,
+            "final_residual": steps[-1], "converged": steps[-1] < tol}
+
+
 def bkw_leg(precision, steps=1, n=64, L=8.0, dt=0.05):
     """Backward-Euler steps of the homogeneous equation with the quadratic
     operator (Maxwell molecules, BKW initial data at K = 0.6), Newton with the
@@ -523,6 +565,11 @@ def run_ours(args, world, rank, local):
             "workload": "1-D steady slab, 8 cells, N=32, hard spheres, walls theta 1/2, Kn=1, from a global "
                         "Maxwellian; modified steps, then exact-Jacobian steps, until |R| < 1e-10",
             "fp64": newton_to_tol_leg("fp64"), "fp32_operator_fp64_residual": newton_to_tol_leg("mixed")}
+        line["shock_to_1e-10"] = {
+            "workload": "Mach-2 planar shock, 128 cells, N=32, hard spheres, Kn=0.1, Rankine-Hugoniot inflow "
+                        "states; continuation + exact-Jacobian Newton, FP32 operator, FP64 residual; "
+                        "plain FGMRES (no preconditioner) does not converge on it",
+            "sweep": shock_leg("sweep"), "moment": shock_leg("moment")}
         line["mixed_n"] = mixed_leg()
         line["n64"] = n64_leg(with_oracle=not args.no_cpu_baseline)
         line["bkw_n64"] = {"workload": "homogeneous BKW relaxation, Maxwell molecules, N=64, J=64, M=32, "
