@@ -53,27 +53,58 @@ KERNEL_AXIS_PASSES = {
     "plane_fwd_ratio": 2, "plane_fwd_u": 2, "plane_fwd_g": 2, "plane_fwd_maxw": 2,
     "plane_inv_mh_fwd": 4, "plane_inv": 2,
     "axis1_fwd": 1, "axis1_inv": 1, "axis1_fwd_mul_inv": 2, "axis1_fwd_acc": 1,
+    "axis1_uhat_inv": 1,
+}
+
+
+def dct_pass_flops(n):
+    """One pass of the octant DCT-I of u^_j: (n/2+1)^3 outputs, each n/4
+    multiply-adds over the paired sums plus the pairing add."""
+    hn, q4 = n // 2 + 1, n // 4
+    return hn ** 3 * (2 * q4 + 1)
+
+
+# u^_j kernels: their own work (the octant DCT passes and the weight build),
+# not the FFT passes they replace
+DCT_KERNELS = {
+    "uhat_planes": lambda n, J: 2 * dct_pass_flops(n) + 4 * (n // 2 + 1) ** 3,      # one radial node
+    "axis1_uhat_inv": lambda n, J: dct_pass_flops(n),                              # plus its FFT pass
+    "f32_uhat": lambda n, J: J * (3 * dct_pass_flops(n) + 4 * (n // 2 + 1) ** 3),  # all radial nodes
 }
 KERNEL_POINTWISE = {  # flops per grid point per instance
-    "plane_inv_mh_fwd": 2, "axis1_fwd_mul_inv": 3, "axis1_fwd_acc": 4,
+    "plane_inv_mh_fwd": 2, "axis1_fwd_mul_inv": 3, "axis1_fwd_acc": 4, "axis1_uhat_inv": 3, "combine": 5,
 }
 # Fused FP32 kernels (N = 32): whole real 3-D transforms per instance.
-#   head: r^ (1);  uhat: u^_j for every radial node (J; computed as a DCT-I
-#   of one octant, counted as the transform it replaces);  gain: 2 per
+#   head: r^ (1);  uhat: u^_j for every radial node (octant DCT-I, counted
+#   by its own work in DCT_KERNELS);  gain: 2 per
 #   radial node (psi_j, psi^_j) plus the loss term's 4 (g, M forward and
 #   back);  tail: the inverse of L^+ (1).
-FUSED_TRANSFORMS = {"f32_head": lambda J: 1, "f32_uhat": lambda J: J, "f32_gain": lambda J: 2 * J + 4,
-                    "f32_tail": lambda J: 1}
-FUSED_POINTWISE = {"f32_gain": lambda J: 10 * J, "f32_uhat": lambda J: 2 * J}
+FUSED_TRANSFORMS = {"f32_head": lambda J: 1, "f32_gain": lambda J: 2 * J + 4, "f32_tail": lambda J: 1}
+FUSED_POINTWISE = {"f32_gain": lambda J: 10 * J}
 
 
 def kernel_flops_per_instance(name, n, J=None):
     J = n if J is None else J
+    extra = DCT_KERNELS[name](n, J) if name in DCT_KERNELS else 0
+    if name == "f32_uhat":
+        return extra
     if name in FUSED_TRANSFORMS:
         return (FUSED_TRANSFORMS[name](J) * 3 * transform_axis_flops(n)
                 + FUSED_POINTWISE.get(name, lambda J: 0)(J) * n ** 3)
     return (KERNEL_AXIS_PASSES.get(name, 0) * transform_axis_flops(n)
-            + KERNEL_POINTWISE.get(name, 0) * n ** 3)
+            + KERNEL_POINTWISE.get(name, 0) * n ** 3 + extra)
+
+
+def kernel_rooflines(prof, n, batch, peak):
+    """Per kernel: average launch time (live CUDA events) and its own
+    algorithmic rate against the pipe's peak (TFLOP/s)."""
+    out = {}
+    for name, (cnt, tot) in sorted(prof.items()):
+        per = tot / max(cnt, 1)
+        fl = kernel_flops_per_instance(name, n) * batch
+        ach = fl / (per * 1e-3) / 1e12 if per > 0 else 0.0
+        out[name] = {"launches": cnt, "ms_per_launch": per, "achieved_tflops": ach, "frac": ach / peak}
+    return out
 
 
 def apply_flops_per_instance(n, J):
@@ -519,6 +550,7 @@ def run_ours(args, world, rank, local):
                      "peak_source": "derived: flop/clk/SM x 152 SMs x 2070 MHz",
                      "kernel_share": share, "kernel_ms_per_launch": per_launch_ms,
                      "apply_flops_per_instance": apply_flops_per_instance(N_GRID, N_GRID)},
+        "kernel_rooflines": kernel_rooflines(prof, N_GRID, BATCH, peak),
         "e2e": {"value": world * BATCH / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(params.nbytes + g.nbytes), "d2h_bytes_per_step": int(g.nbytes)},
     }
@@ -543,14 +575,18 @@ def run_ours(args, world, rank, local):
             p64.apply_linearized(tp, tg, out64)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p64.profile(True)
         f0.record(stream)
         for _ in range(args.fp64_steps):
             p64.apply_linearized(tp, tg, out64)
         f1.record(stream)
         torch.cuda.synchronize()
+        prof64 = p64.profile_read()
+        p64.profile(False)
         ms64 = max_over_ranks(f0.elapsed_time(f1) / args.fp64_steps, world)
         line["fp64_plain"] = {"value": world * BATCH / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
-                              "speedup_of_value": value / (world * BATCH / (ms64 * 1e-3))}
+                              "speedup_of_value": value / (world * BATCH / (ms64 * 1e-3)),
+                              "kernel_rooflines": kernel_rooflines(prof64, N_GRID, BATCH, PEAK_TFLOPS["fp64"])}
         if ref is not None:
             k = ref.shape[0]
             got64 = out64.cpu().numpy()[:k]
@@ -584,8 +620,8 @@ def run_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-fp64-leg", action="store_true")

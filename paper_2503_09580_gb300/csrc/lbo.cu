@@ -329,7 +329,7 @@ static lbo_status run_linearized(lbo_plan* p, const double* params, const double
   auto ka_acc = k_axis1<T, N, CW, AX_FWD_ACC>;
   auto ka_inv = k_axis1<T, N, CW, AX_INV_STORE>;
   auto ka_uhat = k_axis1<T, N, CW, AX_UHAT_INV>;
-  constexpr int PL = (256 / HC) < HC ? (256 / HC) : HC;  // octant planes per block
+  constexpr int PL = UhatPlanes<N>::PL;  // octant planes per block
   auto k_up = k_uhat_planes<T, N, PL>;
   const size_t sm_up = sizeof(T) * ((size_t)PL * HC * HC + (size_t)HC * (N / 4));
   set_smem(k_up, sm_up);

@@ -353,6 +353,16 @@ struct DctPencil {
   }
 };
 
+// Octant planes per block of k_uhat_planes: at most 256 / (N/2+1) (one
+// pencil per thread), spread evenly over the fewest blocks.
+template <int N>
+struct UhatPlanes {
+  static constexpr int HC = N / 2 + 1;
+  static constexpr int MAXP = (256 / HC) < HC ? (256 / HC) : HC;
+  static constexpr int BLOCKS = (HC + MAXP - 1) / MAXP;
+  static constexpr int PL = (HC + BLOCKS - 1) / BLOCKS;
+};
+
 // Axes 3 and 2 of u^_j for a block of PL octant planes d1 of one instance:
 // w(d) = rho (pi theta)^-3/2 exp(-|d h|^2 / theta) phit_j(d), DCT-I along d3
 // then d2, stored as up[b][d1][k2][k3].  grid = (ceil((N/2+1)/PL), B).

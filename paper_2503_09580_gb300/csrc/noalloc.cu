@@ -110,7 +110,7 @@ lbo_status run(const lbo_plan* p, const double* params, const double* g, double*
   const size_t sm = PlaneSmem<T, N, PPC>::BYTES;
   const dim3 gp(N / PPC, B), ga((N * HC + CW - 1) / CW, B), blk(256);
   auto kf_ratio = k_plane_fwd<T, N, PPC, SRC_RATIO>;
-  constexpr int PL = (256 / HC) < HC ? (256 / HC) : HC;
+  constexpr int PL = UhatPlanes<N>::PL;
   auto k_up = k_uhat_planes<T, N, PL>;
   const size_t sm_up = sizeof(T) * ((size_t)PL * HC * HC + (size_t)HC * (N / 4));
   auto kf_real = k_plane_fwd<T, N, PPC, SRC_REAL64>;
