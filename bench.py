@@ -321,7 +321,7 @@ def newton_to_tol_leg(mode, tol=1e-10, nx=8, n=32, L=8.0):
             "final_residual_fp64": final, "history": [[k, float(r)] for k, r in steps]}
 
 
-def shock_leg(precond, nx=128, n=32, L=8.0, tol=1e-10):
+def shock_leg(precond, nx=128, n=32, L=8.0, tol=1e-10, coarse_operator="galerkin"):
     """Planar Mach-2 shock: x in [-1, 1], nx cells, hard spheres, Kn = 0.1,
     Rankine-Hugoniot inflow states (gamma = 5/3), tanh start; pseudo-
     transient continuation (dtau from 0.3) with exact-Jacobian Newton steps,
@@ -344,7 +344,8 @@ def shock_leg(precond, nx=128, n=32, L=8.0, tol=1e-10):
     p64 = lbo.Plan(n, L, 0.5, n, hemisphere_p=2, mass_fix=1)
     solver = p32.solver(kind="slab", nx=nx, x_left=-1.0, x_right=1.0, kn=0.1, total_mass=1.0, inflow_left=up,
                         inflow_right=down, krylov_rtol=1e-3, krylov_atol=1e-14, krylov_restart=40,
-                        krylov_maxit=600, precond=precond, pseudo_dt=0.3, jacobian="exact")
+                        krylov_maxit=600, precond=precond, pseudo_dt=0.3, jacobian="exact",
+                        coarse_operator=coarse_operator)
     solver.set_residual_plan(p64)
     tf = torch.from_numpy(np.stack(f)).cuda()
     steps, its = [], 0
@@ -605,7 +606,7 @@ def run_ours(args, world, rank, local):
             "workload": "Mach-2 planar shock, 128 cells, N=32, hard spheres, Kn=0.1, Rankine-Hugoniot inflow "
                         "states; continuation + exact-Jacobian Newton, FP32 operator, FP64 residual; "
                         "plain FGMRES (no preconditioner) does not converge on it",
-            "sweep": shock_leg("sweep"), "moment": shock_leg("moment")}
+            "sweep": shock_leg("sweep"), "moment_transport": shock_leg("moment", coarse_operator="transport")}
         line["mixed_n"] = mixed_leg()
         line["n64"] = n64_leg(with_oracle=not args.no_cpu_baseline)
         line["bkw_n64"] = {"workload": "homogeneous BKW relaxation, Maxwell molecules, N=64, J=64, M=32, "

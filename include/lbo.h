@@ -209,6 +209,13 @@ typedef struct {
                              Eq. (2.14) up to rounding): two Q evaluations
                              in the plan's precision per Krylov product,
                              quadratic convergence near the solution      */
+  int coarse_operator;    /* MOMENT preconditioner: 0 assembles and applies
+                             W^T A' P with the full operator A' (Galerkin);
+                             1 keeps only A''s transport, border and shift
+                             parts, exact for the 5 collision invariants up
+                             to the discrete collision operator's
+                             conservation, and needs no collision operator
+                             per Krylov iteration                         */
 } lbo_problem;
 
 typedef struct {

@@ -22,6 +22,14 @@
 // basis vectors coloured mod 3 (no two cells of one colour share a
 // neighbour), and factored on the host by banded LU with partial pivoting.
 // The rank-one border becomes one extra row and column (an arrow).
+//
+// coarse_operator = 1 replaces A' by its transport, border and shift parts
+// in both the assembly and the residual r - A' z.  For the five collision
+// invariants this drops only what the discrete collision operator fails to
+// conserve (W^T L P = 0 and W^T J_Q P = 0 in exact arithmetic), and it saves
+// the collision-operator application that the Galerkin form spends per
+// Krylov iteration: the low-order moment equation of synthetic
+// acceleration.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -285,7 +293,7 @@ lbo_status coarse_assemble(lbo_solver* S, bool border) {
         if (st != LBO_OK) return st;
         for (int j = colour; j < nx; j += 3) C->qr[nb * j + b] = S->dx * C->h_mom[nb * j];
       }
-      st = solver_apply_op(S, C->d_vec, C->d_out, false);
+      st = solver_apply_op(S, C->d_vec, C->d_out, false, S->pb.coarse_operator != 1);
       if (st != LBO_OK) return st;
       st = restrict_to_host(S, C->d_out);
       if (st != LBO_OK) return st;
@@ -316,7 +324,7 @@ lbo_status coarse_correct(lbo_solver* S, const double* v, double* z) {
   CoarseState* C = state(S);
   if (!C || !C->valid) return LBO_OK;
   cudaStream_t s = S->plan->stream;
-  lbo_status st = solver_apply_op(S, z, C->d_out, true);
+  lbo_status st = solver_apply_op(S, z, C->d_out, true, S->pb.coarse_operator != 1);
   if (st != LBO_OK) return st;
   solver_axpby(S, C->d_out, v, 1.0, -1.0);  // v - A' z
   st = restrict_to_host(S, C->d_out);

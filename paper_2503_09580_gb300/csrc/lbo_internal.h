@@ -80,7 +80,7 @@ lbo_status network_record(lbo_solver* S, const double* w, const double* zk, doub
                           lbo_status (*sweep)(lbo_solver*, const double*, double*));
 void free_network(lbo_solver* S);
 // slab operator A' (with or without the mass border) and y = a x + b y (solver.cu)
-lbo_status solver_apply_op(lbo_solver* S, const double* v, double* out, bool border);
+lbo_status solver_apply_op(lbo_solver* S, const double* v, double* out, bool border, bool collisions);
 void solver_axpby(lbo_solver* S, double* y, const double* x, double a, double b);
 // moment coarse correction (coarse.cu)
 lbo_status coarse_assemble(lbo_solver* S, bool border);

@@ -284,9 +284,13 @@ lbo_status exact_jacobian_q(lbo_solver* S, const double* v) {
 
 // out = A' v:  SLAB: T v - L v / Kn + e m(v) + v / dtau;  HOMOGENEOUS: v - dt L v
 // (L v replaced by the exact J_Q v when the problem asks for the exact Jacobian)
-lbo_status apply_op(lbo_solver* S, const double* v, double* out, bool border = true) {
-  lbo_status st = S->pb.jacobian == 1 ? exact_jacobian_q(S, v)
-                                      : lbo_apply_linearized(S->plan, S->params, v, S->Lv, S->nx);
+// collisions = false drops the collision term (SLAB only): the transport,
+// border and shift parts alone, for the transport-only coarse operator
+lbo_status apply_op(lbo_solver* S, const double* v, double* out, bool border = true, bool collisions = true) {
+  if (!collisions && S->pb.kind != LBO_PROBLEM_SLAB) return LBO_EINVAL;
+  lbo_status st = !collisions          ? LBO_OK
+                  : S->pb.jacobian == 1 ? exact_jacobian_q(S, v)
+                                        : lbo_apply_linearized(S->plan, S->params, v, S->Lv, S->nx);
   if (st != LBO_OK) return st;
   cudaStream_t s = S->plan->stream;
   if (S->pb.kind == LBO_PROBLEM_SLAB) {
@@ -294,7 +298,8 @@ lbo_status apply_op(lbo_solver* S, const double* v, double* out, bool border = t
     // the mass border e m(v) only where both sides are walls: an inflow side
     // fixes the incoming ghost values, so the operator has no mass null mode
     const double* ev = border && bordered(S) ? S->evec : nullptr;
-    LBO_LAUNCH(S->plan, "solver_transport", s, k_transport, grid_for(S->len), 256, 0, v, S->Lv, ev, S->res,
+    const double* lv = collisions ? S->Lv : nullptr;
+    LBO_LAUNCH(S->plan, "solver_transport", s, k_transport, grid_for(S->len), 256, 0, v, lv, ev, S->res,
                S->WL, S->WR, out, S->N, S->nx, S->h, S->dx, 1.0, -1.0 / S->pb.kn, 1.0,
                S->pb.bc_left == LBO_BC_INFLOW ? 0.0 : -1.0, S->pb.bc_right == LBO_BC_INFLOW ? 0.0 : -1.0, S->shift);
   } else {
@@ -468,8 +473,8 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
 
 }  // namespace
 
-lbo_status solver_apply_op(lbo_solver* S, const double* v, double* out, bool border) {
-  return apply_op(S, v, out, border);
+lbo_status solver_apply_op(lbo_solver* S, const double* v, double* out, bool border, bool collisions) {
+  return apply_op(S, v, out, border, collisions);
 }
 
 void solver_axpby(lbo_solver* S, double* y, const double* x, double a, double b) {
@@ -532,6 +537,7 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
   if (pb->precond < 0 || pb->precond > 3) return LBO_EINVAL;
   if (pb->line_search < 0 || pb->line_search > 60 || !(pb->pseudo_dt >= 0)) return LBO_EINVAL;
   if (pb->jacobian < 0 || pb->jacobian > 1) return LBO_EINVAL;
+  if (pb->coarse_operator < 0 || pb->coarse_operator > 1) return LBO_EINVAL;
   lbo_solver* S = new lbo_solver();
   S->pb = *pb;
   S->plan = plan;

@@ -46,7 +46,7 @@ class Problem(ctypes.Structure):
                 ("bc_left", ctypes.c_int), ("bc_right", ctypes.c_int), ("inflow_left", ctypes.c_double * 5),
                 ("inflow_right", ctypes.c_double * 5), ("line_search", ctypes.c_int),
                 ("pseudo_dt", ctypes.c_double), ("coarse_moments", ctypes.c_int),
-                ("jacobian", ctypes.c_int)]
+                ("jacobian", ctypes.c_int), ("coarse_operator", ctypes.c_int)]
 
 
 class NewtonStats(ctypes.Structure):
@@ -291,7 +291,8 @@ class Solver:
                  wall_left=(1.0, 0.0, 0.0, 0.0), wall_right=(1.0, 0.0, 0.0, 0.0), total_mass=1.0,
                  wall_flux="analytic", dt=0.0, krylov_rtol=1e-3, krylov_atol=1e-7, krylov_restart=30,
                  krylov_maxit=300, precond="sweep", inflow_left=None, inflow_right=None, line_search=0,
-                 pseudo_dt=0.0, coarse_moments=5, jacobian="local_maxwellian"):
+                 pseudo_dt=0.0, coarse_moments=5, jacobian="local_maxwellian",
+                 coarse_operator="galerkin"):
         lib = load()
         pb = Problem()
         pb.kind = PROBLEM[kind]
@@ -316,6 +317,7 @@ class Solver:
         pb.pseudo_dt = float(pseudo_dt)
         pb.coarse_moments = int(coarse_moments)
         pb.jacobian = {"local_maxwellian": 0, "exact": 1}[jacobian]
+        pb.coarse_operator = {"galerkin": 0, "transport": 1}[coarse_operator]
         h = ctypes.c_void_p()
         _check(lib.lbo_solver_create(ctypes.byref(pb), plan._h, ctypes.byref(h)), "lbo_solver_create")
         self._h, self.plan, self.problem = h, plan, pb

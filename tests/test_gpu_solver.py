@@ -262,7 +262,7 @@ def test_line_search_keeps_full_steps_when_newton_converges():
     assert out[0][0][-1] < 0.05 * out[0][0][0]
 
 
-def _shock_slab(nx, precond, n=32, L=8.0):
+def _shock_slab(nx, precond, n=32, L=8.0, coarse_operator="galerkin"):
     up, down = _rh_states(2.0)
     x = -1.0 + (np.arange(nx) + 0.5) * (2.0 / nx)
     a = (np.arange(n) - n // 2) * (2 * L / n)
@@ -276,7 +276,7 @@ def _shock_slab(nx, precond, n=32, L=8.0):
     p64 = lbo.Plan(n, L, 0.5, n, hemisphere_p=2, mass_fix=1)
     kw = dict(kind="slab", nx=nx, x_left=-1.0, x_right=1.0, kn=0.1, total_mass=1.0, inflow_left=up,
               inflow_right=down, krylov_rtol=1e-3, krylov_atol=1e-14, krylov_restart=40, krylov_maxit=600)
-    solver = p32.solver(precond=precond, pseudo_dt=0.3, jacobian="exact", **kw)
+    solver = p32.solver(precond=precond, pseudo_dt=0.3, jacobian="exact", coarse_operator=coarse_operator, **kw)
     solver.set_residual_plan(p64)
     judge = p64.solver(precond="sweep", **kw)
     return np.stack(f), solver, judge, (p32, p64), down
@@ -287,11 +287,13 @@ def test_mach2_shock_converges():
     inflow states, tanh start): pseudo-transient continuation (dtau from
     0.3) with exact-Jacobian Newton steps (Jacobian's Q in FP32, residual in
     FP64) converges to |R| < 1e-10 judged in FP64; the coarse moment
-    correction needs well under the sweep's Krylov iterations for it.
-    (Modified Newton does not converge here, and plain FGMRES stalls.)"""
+    correction needs well under the sweep's Krylov iterations for it, in
+    its Galerkin form and in its transport-only form (which spends no extra
+    collision operator per iteration).  (Modified Newton does not converge
+    here, and plain FGMRES stalls.)"""
     its = {}
-    for pc in ("sweep", "moment"):
-        f, solver, judge, plans, down = _shock_slab(32, pc)
+    for pc, co in (("sweep", "galerkin"), ("moment", "galerkin"), ("moment", "transport")):
+        f, solver, judge, plans, down = _shock_slab(32, pc, coarse_operator=co)
         tf = torch.from_numpy(f).to(DEV)
         hist, total = [], 0
         for _ in range(18):
@@ -302,14 +304,15 @@ def test_mach2_shock_converges():
                 break
         out = torch.empty_like(tf)
         final = judge.residual(tf, out)
-        print(pc, "steps", len(hist), "krylov", total, "final", final)
+        print(pc, co, "steps", len(hist), "krylov", total, "final", final)
         assert final < 1e-10
         fg = tf.cpu().numpy()
         assert np.isfinite(fg).all()
         rho = (16.0 / 32) ** 3 * fg.reshape(32, -1).sum(axis=1)
         assert 0.95 < rho.min() and rho.max() < down[0] + 0.05
-        its[pc] = total
-    assert its["moment"] <= 0.7 * its["sweep"]
+        its[pc + "/" + co] = total
+    assert its["moment/galerkin"] <= 0.7 * its["sweep/galerkin"]
+    assert its["moment/transport"] <= 0.6 * its["sweep/galerkin"]
 
 
 def test_mixed_precision_residual_plan():
