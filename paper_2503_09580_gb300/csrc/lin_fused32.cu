@@ -14,8 +14,9 @@
 // Kernels per application of a batch: k_f32_head (r^ = FFT(r) / N^3),
 // k_f32_uhat (u^_j = FFT(M^g phit_j) of every instance and radial node, as
 // a DCT-I of one octant), k_f32_gain (grid = (j-groups + 1) x batch: partial
-// L^+ per group, and the loss term written into out by the extra block),
-// k_f32_tail (sum of the partials, inverse transform, added to out in FP64).
+// L^+ per group, and the loss term written to an FP32 buffer by the extra
+// block), k_f32_tail (sum of the partials, inverse transform, plus the loss
+// term, written to out in FP64).
 #include <cmath>
 
 #include "fused32.cuh"
@@ -34,6 +35,7 @@ struct FusedArgs {
   cpx<float>* rhat;    // [B][F_H], pre-scaled by N^-3
   cpx<float>* part;    // [G][B][F_H] partial L^+ per j-group
   float* uhat;         // [B][J][U_STRIDE] u^_j = FFT(M^g phit_j) on the octant k in [0,16]^3
+  float* lossf;        // [B][N^3] loss term -u M - w g in FP32 (loss block -> tail)
   double* out;         // [B][N^3]
   double h, log_inv_eps;
   int cutoff, J, G, B, Q;
@@ -95,6 +97,8 @@ __device__ __forceinline__ void dct17(const float (&x)[U_N], float* dst, int str
 // |v-u|^2 >= dstar, dstar the smallest double that passes the test.
 struct PrepTables {
   double a[3 * 32], em[3 * 32], ei[3 * 32];
+  float eif[3 * 32];  // ei in FP32, for the ratio of the head kernel
+  float emf[3 * 32];  // em in FP32, for the loss term
   double dstar;
 };
 
@@ -114,6 +118,8 @@ __device__ __forceinline__ void fill_prep(PrepTables& T, const InstanceParams& q
     }
     T.em[t] = em;
     T.ei[t] = ei;
+    T.eif[t] = (float)ei;
+    T.emf[t] = (float)em;
   } else if (t == 96) {
     const double twoth = __dmul_rn(2.0, q.theta);
     const double thr = __dsub_rn(log_inv_eps, __dmul_rn(1.5, log(__dmul_rn(__dmul_rn(2.0, 3.141592653589793), q.theta))));
@@ -153,14 +159,20 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_head(FusedArgs a) {
   fill_prep(T, q, a.h, a.log_inv_eps);
   const double* gb = a.g + (size_t)b * 32768;
   const bool cut = a.cutoff != 0;
+  // The cut-off decision stays in FP64 exactly as the oracle forms it,
+  // ((a_1 + a_2) + a_3) >= d*, with the row sum a_1 + a_2 hoisted; the ratio
+  // itself is formed in FP32 (it is rounded to FP32 for the transform
+  // anyway).  A point that passes the cut has (a_1 + a_2) / (2 theta) below
+  // the threshold, so its partial product stays finite; a cut point is
+  // selected, never multiplied.
   rows_forward(V, [&](int i1, int qq, int i3) {
     float v[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int i2 = 2 * qq + r;
       const double d2 = __dadd_rn(__dadd_rn(T.a[i1], T.a[32 + i2]), T.a[64 + i3]);
-      const double val = gb[(i1 * 32 + i2) * 32 + i3] * ((T.ei[i1] * T.ei[32 + i2]) * T.ei[64 + i3]);
-      v[r] = (cut && d2 >= T.dstar) ? 0.f : (float)val;
+      const float val = (float)gb[(i1 * 32 + i2) * 32 + i3] * ((T.eif[i1] * T.eif[32 + i2]) * T.eif[64 + i3]);
+      v[r] = (cut && d2 >= T.dstar) ? 0.f : val;
     }
     return make_c(v[0], v[1]);
   });
@@ -217,17 +229,17 @@ __global__ void __launch_bounds__(U_THREADS, 4) k_f32_uhat(FusedArgs a) {
   for (int e = t; e < U_SZ; e += U_THREADS) dst[e] = W[e];
 }
 
-// Loss term of one instance: out = -InvFFT(FFT(g) omega) M - InvFFT(FFT(M) omega) g.
+// Loss term of one instance, lossf = -InvFFT(FFT(g) omega) M - InvFFT(FFT(M) omega) g (FP32).
 __device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T, int b) {
   const int t = threadIdx.x;
   const double* gb = a.g + (size_t)b * 32768;
-  double* ob = a.out + (size_t)b * 32768;
+  float* ob = a.lossf + (size_t)b * 32768;
   for (int pass = 0; pass < 2; ++pass) {
     rows_forward(V, [&](int i1, int qq, int i3) {
       if (pass == 0)
         return make_c((float)gb[(i1 * 32 + 2 * qq) * 32 + i3], (float)gb[(i1 * 32 + 2 * qq + 1) * 32 + i3]);
-      const double m13 = T.em[i1] * T.em[64 + i3];
-      return make_c((float)(m13 * T.em[32 + 2 * qq]), (float)(m13 * T.em[32 + 2 * qq + 1]));
+      const float m13 = T.emf[i1] * T.emf[64 + i3];
+      return make_c(m13 * T.emf[32 + 2 * qq], m13 * T.emf[32 + 2 * qq + 1]);
     });
     {
       const int i2 = t / F_HC, k3 = t % F_HC;
@@ -250,17 +262,18 @@ __device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T
       cpx<float> z[32];
       load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
       fft32<true>(z);
-      double* o0 = ob + (i1 * 32 + 2 * qq) * 32;
+      // FP32: every term carries the rounding of an FP32 transform
+      float* o0 = ob + (i1 * 32 + 2 * qq) * 32;
       const double* g0 = gb + (i1 * 32 + 2 * qq) * 32;
+      const float ma = T.emf[i1] * T.emf[32 + 2 * qq], mb = T.emf[i1] * T.emf[32 + 2 * qq + 1];
 #pragma unroll 4
       for (int i3 = 0; i3 < 32; ++i3) {
         if (pass == 0) {  // -u M
-          const double m13 = T.em[i1] * T.em[64 + i3];
-          o0[i3] = -(double)z[i3].x * (m13 * T.em[32 + 2 * qq]);
-          o0[32 + i3] = -(double)z[i3].y * (m13 * T.em[32 + 2 * qq + 1]);
+          o0[i3] = -z[i3].x * (ma * T.emf[64 + i3]);
+          o0[32 + i3] = -z[i3].y * (mb * T.emf[64 + i3]);
         } else {  // -w g
-          o0[i3] -= (double)z[i3].x * g0[i3];
-          o0[32 + i3] -= (double)z[i3].y * g0[32 + i3];
+          o0[i3] -= z[i3].x * (float)g0[i3];
+          o0[32 + i3] -= z[i3].y * (float)g0[32 + i3];
         }
       }
     }
@@ -348,7 +361,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
   }
 }
 
-// out += InvFFT(sum over groups of the partial L^+).
+// out = InvFFT(sum over groups of the partial L^+) + the loss term, in FP64.
 __global__ void __launch_bounds__(F_THREADS, 1) k_f32_tail(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   cpx<float>* V = (cpx<float>*)smem;
@@ -377,10 +390,11 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_tail(FusedArgs a) {
     load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
     fft32<true>(z);
     double* o0 = a.out + (size_t)b * 32768 + (i1 * 32 + 2 * qq) * 32;
+    const float* l0 = a.lossf + (size_t)b * 32768 + (i1 * 32 + 2 * qq) * 32;
 #pragma unroll 4
-    for (int i3 = 0; i3 < 32; ++i3) {
-      o0[i3] += (double)z[i3].x;
-      o0[32 + i3] += (double)z[i3].y;
+    for (int i3 = 0; i3 < 32; ++i3) {  // out = L+ + loss, summed in FP32
+      o0[i3] = (double)(z[i3].x + l0[i3]);
+      o0[32 + i3] = (double)(z[i3].y + l0[32 + i3]);
     }
   }
 }
@@ -388,7 +402,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_tail(FusedArgs a) {
 }  // namespace
 
 size_t fused32_workspace_bytes(int B, int G, int J) {
-  return (size_t)B * F_H * 8 * (1 + (size_t)G) + (size_t)B * J * U_STRIDE * sizeof(float);
+  return (size_t)B * F_H * 8 * (1 + (size_t)G) + (size_t)B * J * U_STRIDE * sizeof(float) +
+         (size_t)B * 32768 * sizeof(float);
 }
 
 int fused32_default_groups(int B) {
@@ -419,6 +434,7 @@ lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const doubl
   a.rhat = (cpx<float>*)ws;
   a.part = a.rhat + (size_t)B * F_H;
   a.uhat = (float*)(a.part + (size_t)G * B * F_H);
+  a.lossf = a.uhat + (size_t)B * p->J * U_STRIDE;
   a.out = out;
   a.h = 2.0 * p->L / F_N;
   a.log_inv_eps = std::log(1.0 / p->eps);
