@@ -14,7 +14,7 @@
 // the target c_j solves G_j c_j = m(z_j) - m(s_j), G_j the 5x5 moment matrix
 // of phi_a phi_b M_j.  Training: full-batch Adam on the mean squared error,
 // FP32 weights, hand-written forward/backward kernels.  FGMRES keeps the
-// exact operator as the judge, so a poor network costs iterations only.
+// exact operator as the measure of convergence, so a poor network costs iterations only.
 #include <cmath>
 #include <cstring>
 #include <vector>

@@ -372,7 +372,7 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
   bool done = false;
   // the learned preconditioner gets half the iteration budget; if it has not
   // converged by then, the solve continues from the current iterate with the
-  // plain sweep (the exact operator stays the judge)
+  // plain sweep (the exact operator still measures convergence)
   S->force_sweep = false;
   const bool learned = S->pb.precond == LBO_PRECOND_LEARNED;
   const int learned_budget = S->pb.krylov_maxit / 2;

@@ -1,6 +1,6 @@
 """Learned preconditioner: hand-written GPU backward pass against the CPU
 oracle of the network, training on solver-generated pairs, and the safety
-property (the exact operator judges; a poor network costs iterations only).
+property (the exact operator measures convergence; a poor network costs iterations only).
 The measured gain over the plain sweep is printed (on this slab problem the
 trained network does not beat the sweep; the fallback keeps the solve exact)."""
 import numpy as np

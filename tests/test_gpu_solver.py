@@ -278,22 +278,22 @@ def _shock_slab(nx, precond, n=32, L=8.0, coarse_operator="galerkin"):
               inflow_right=down, krylov_rtol=1e-3, krylov_atol=1e-14, krylov_restart=40, krylov_maxit=600)
     solver = p32.solver(precond=precond, pseudo_dt=0.3, jacobian="exact", coarse_operator=coarse_operator, **kw)
     solver.set_residual_plan(p64)
-    judge = p64.solver(precond="sweep", **kw)
-    return np.stack(f), solver, judge, (p32, p64), down
+    fp64_res = p64.solver(precond="sweep", **kw)
+    return np.stack(f), solver, fp64_res, (p32, p64), down
 
 
 def test_mach2_shock_converges():
     """Planar Mach-2 shock (hard spheres, Kn = 0.1, 32 cells, Rankine-Hugoniot
     inflow states, tanh start): pseudo-transient continuation (dtau from
     0.3) with exact-Jacobian Newton steps (Jacobian's Q in FP32, residual in
-    FP64) converges to |R| < 1e-10 judged in FP64; the coarse moment
+    FP64) converges to |R| < 1e-10 measured in FP64; the coarse moment
     correction needs well under the sweep's Krylov iterations for it, in
     its Galerkin form and in its transport-only form (which spends no extra
     collision operator per iteration).  (Modified Newton does not converge
     here, and plain FGMRES stalls.)"""
     its = {}
     for pc, co in (("sweep", "galerkin"), ("moment", "galerkin"), ("moment", "transport")):
-        f, solver, judge, plans, down = _shock_slab(32, pc, coarse_operator=co)
+        f, solver, fp64_res, plans, down = _shock_slab(32, pc, coarse_operator=co)
         tf = torch.from_numpy(f).to(DEV)
         hist, total = [], 0
         for _ in range(18):
@@ -303,7 +303,7 @@ def test_mach2_shock_converges():
             if st["residual_norm"] < 1e-10:
                 break
         out = torch.empty_like(tf)
-        final = judge.residual(tf, out)
+        final = fp64_res.residual(tf, out)
         print(pc, co, "steps", len(hist), "krylov", total, "final", final)
         assert final < 1e-10
         fg = tf.cpu().numpy()
@@ -374,7 +374,7 @@ def test_exact_newton_with_fp32_jacobian_reaches_fp64_residual():
     """Fourier-flow slab: four modified steps bring |R| to ~1e-5 (the floor of
     the modified iteration is ~1e-6); exact-Jacobian steps then converge
     quadratically.  With the Jacobian's Q in FP32 and the residual in FP64
-    the state reaches |R| < 1e-12 judged in FP64, while the all-FP32 solver
+    the state reaches |R| < 1e-12 measured in FP64, while the all-FP32 solver
     stops at the accuracy of its FP32 residual (above 1e-9)."""
     n, L, nx = 32, 8.0, 8
     oracle = Slab(n, L, 1.0, n, nx=nx, kn=1.0, hemisphere=hemisphere_rule(2), wall_flux="discrete")
@@ -385,7 +385,7 @@ def test_exact_newton_with_fp32_jacobian_reaches_fp64_residual():
     kw = dict(kind="slab", nx=nx, kn=1.0, wall_left=(1.0, 0, 0, 0), wall_right=(2.0, 0, 0, 0), total_mass=C,
               wall_flux="discrete", krylov_rtol=1e-3, krylov_atol=1e-16, krylov_restart=40, krylov_maxit=400,
               precond="sweep")
-    judge = p64.solver(**kw)
+    fp64_res = p64.solver(**kw)
     out = torch.empty((nx, n, n, n), dtype=torch.float64, device=DEV)
     final = {}
     for mode in ("mixed", "fp32"):
@@ -401,7 +401,7 @@ def test_exact_newton_with_fp32_jacobian_reaches_fp64_residual():
             hist.append(st["residual_norm"])
             if st["residual_norm"] < 1e-13:
                 break
-        final[mode] = judge.residual(tf, out)
+        final[mode] = fp64_res.residual(tf, out)
         print(mode, hist, final[mode])
         assert abs(oracle.mass(tf.cpu().numpy()) - C) <= 1e-9 * C
         mod.close()
