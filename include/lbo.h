@@ -252,6 +252,23 @@ lbo_status lbo_newton_step(lbo_solver *solver, double *f, const double *f_prev, 
 lbo_status lbo_solver_residual(lbo_solver *solver, const double *f, const double *f_prev, double *out,
                                double *norm);
 
+/* A slab whose cells carry different velocity grids (the shock workload with
+ * N chosen per cell; not in the paper, which uses one N).  plans[p] is the
+ * plan of one N (one plan per N, the same box); cell j uses
+ * plans[cell_plan[j]].  The state vector holds the cells one after the
+ * other, cell j as N_j^3 doubles in the usual centred order;
+ * lbo_solver_state_length gives its total length.  Collisions are applied
+ * per cell with the cell's plan; the upwind difference of a cell uses its
+ * neighbours spectrally resampled to its grid (zero padding to a finer grid,
+ * truncation to a coarser one, the Nyquist term of the coarser grid a
+ * cosine).  Supported: SLAB with inflow sides at both ends (LBO_EUNSUPPORTED
+ * otherwise), preconditioner NONE or SWEEP (the sweep runs on the finest
+ * grid), both Jacobians, continuation and line search; per-N residual plans
+ * through lbo_solver_set_residual_plan (one call per N). */
+lbo_status lbo_solver_create_mixed(const lbo_problem *problem, lbo_plan *const *plans, int nplans,
+                                   const int *cell_plan, lbo_solver **out);
+size_t lbo_solver_state_length(const lbo_solver *solver);
+
 /* Mixed precision: evaluate Q(f,f) of the nonlinear residual with `plan`
  * (typically an FP64 plan) while the linear operator L of the Krylov solve
  * keeps the solver's own plan (typically FP32).  The modified Newton step of
@@ -260,7 +277,9 @@ lbo_status lbo_solver_residual(lbo_solver *solver, const double *f, const double
  * and box; the solver launches it on its own stream (the plan's stream is
  * set to the solver plan's stream on every residual evaluation) and does not
  * own it: keep it alive until the solver is destroyed or the call is undone
- * with plan = NULL.  LBO_EINVAL on mismatched N or box. */
+ * with plan = NULL.  LBO_EINVAL on mismatched N or box.  A mixed-N solver
+ * takes one residual plan per N (the call sets the one of plan's N; NULL
+ * clears all). */
 lbo_status lbo_solver_set_residual_plan(lbo_solver *solver, lbo_plan *plan);
 
 void lbo_solver_destroy(lbo_solver *solver);

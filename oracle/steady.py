@@ -217,3 +217,108 @@ def initial_state(slab, total_mass=1.0, theta_left=1.0, theta_right=2.0):
         th = (1 - w) * theta_left + w * theta_right
         out.append(total_mass / width * (2 * np.pi * th) ** -1.5 * np.exp(-v2 / (2 * th)))
     return np.stack(out)
+
+
+class MixedSlab:
+    """Slab whose cells carry different velocity grids n_j on the same box
+    (the mixed-n shock workload; library extension).  Reading: the upwind
+    difference of cell j uses its neighbours resampled to cell j's grid
+    (resample.py: zero padding or truncation), so every cell's transport
+    term lives on its own grid; collisions are cell-local with the tables
+    of the cell's n.  Inflow sides only (the ghost of a Newton correction is
+    zero, and there is no mass border).  States are lists of centred-order
+    arrays, one per cell.
+    """
+
+    def __init__(self, ns, L, omega, x_left=-0.5, x_right=0.5, kn=1.0, hemisphere=None, q_mass_fix=None,
+                 inflow_left=None, inflow_right=None):
+        from .resample import resample_centred
+        self.resample = resample_centred
+        self.ns = [int(n) for n in ns]
+        self.nx, self.L, self.kn = len(ns), L, kn
+        self.dx = (x_right - x_left) / self.nx
+        self.tabs = {n: Tables(n, L, omega, n) for n in sorted(set(self.ns))}
+        self.sig, self.wm = hemisphere
+        self.q_mass_fix = q_mass_fix
+
+        def axes(n):
+            a = (np.arange(n) - n // 2) * grid.spacing(n, L)
+            return a
+
+        def maxwell(st, n):
+            rho, u1, u2, u3, th = st
+            a = axes(n)
+            return rho * (2 * np.pi * th) ** -1.5 * np.exp(
+                -((a[:, None, None] - u1) ** 2 + (a[None, :, None] - u2) ** 2 + (a[None, None, :] - u3) ** 2)
+                / (2 * th))
+        self.v1 = {n: np.broadcast_to(axes(n)[:, None, None], (n, n, n)) for n in self.tabs}
+        self.inL = maxwell(inflow_left, self.ns[0])
+        self.inR = maxwell(inflow_right, self.ns[-1])
+
+    def _on(self, x, n):
+        return x if x.shape[0] == n else self.resample(x, n)
+
+    def transport(self, f, linear=False):
+        out = []
+        for j, n in enumerate(self.ns):
+            v1 = self.v1[n]
+            left = (0.0 * f[j] if linear else self.inL) if j == 0 else self._on(f[j - 1], n)
+            right = (0.0 * f[j] if linear else self.inR) if j == self.nx - 1 else self._on(f[j + 1], n)
+            out.append((np.maximum(v1, 0.0) * (f[j] - left) + np.minimum(v1, 0.0) * (right - f[j])) / self.dx)
+        return out
+
+    def collision_q(self, f):
+        return [grid.to_centred(quadratic_operator(self.tabs[n], grid.to_cyclic(f[j]), self.sig, self.wm,
+                                                   mass_fix=self.q_mass_fix)) for j, n in enumerate(self.ns)]
+
+    def residual(self, f):
+        return [t - q / self.kn for t, q in zip(self.transport(f), self.collision_q(f))]
+
+    def local_params(self, f):
+        out = np.empty((self.nx, 5))
+        for j, n in enumerate(self.ns):
+            rho, u, th, _, _ = moments(grid.to_cyclic(f[j]), n, self.L)
+            out[j] = (rho, u[0], u[1], u[2], th)
+        return out
+
+    def norm(self, r):
+        """sqrt(dx sum_j h_j^3 sum r_j^2), the discrete L2 norm cell by cell."""
+        return np.sqrt(self.dx * sum(grid.spacing(n, self.L) ** 3 * (x * x).sum() for n, x in zip(self.ns, r)))
+
+    def operator(self, f, jacobian="local_maxwellian", shift=0.0):
+        params = self.local_params(f)
+
+        def coll(g):
+            if jacobian == "exact":
+                return [grid.to_centred(quadratic_operator(self.tabs[n], grid.to_cyclic(f[j]), self.sig, self.wm,
+                                                           g=grid.to_cyclic(g[j]), mass_fix=self.q_mass_fix))
+                        for j, n in enumerate(self.ns)]
+            return [grid.to_centred(collision_operator(self.tabs[n], p[0], p[1:4], p[4], grid.to_cyclic(g[j])))
+                    for j, (n, p) in enumerate(zip(self.ns, params))]
+
+        def apply(g):
+            return [t - c / self.kn + shift * x for t, c, x in zip(self.transport(g, linear=True), coll(g), g)]
+        return apply
+
+    def flatten(self, f):
+        return np.concatenate([x.ravel() for x in f])
+
+    def unflatten(self, x):
+        out, o = [], 0
+        for n in self.ns:
+            out.append(x[o:o + n ** 3].reshape(n, n, n))
+            o += n ** 3
+        return out
+
+    def newton_step(self, f, rtol=1e-10, restart=80, maxiter=400, shift=0.0, jacobian="local_maxwellian"):
+        """One Newton step (modified or exact Jacobian, optional shift),
+        unpreconditioned GMRES (scipy) on the flattened cells; returns
+        (f_new, g, |R(f)|)."""
+        from scipy.sparse.linalg import LinearOperator, gmres
+        R = self.residual(f)
+        A = self.operator(f, jacobian, shift)
+        n = sum(x.size for x in f)
+        op = LinearOperator((n, n), matvec=lambda x: self.flatten(A(self.unflatten(x))), dtype=np.float64)
+        x, info = gmres(op, self.flatten(R), rtol=rtol, atol=0.0, restart=restart, maxiter=maxiter)
+        g = self.unflatten(x)
+        return [a - b for a, b in zip(f, g)], g, self.norm(R)

@@ -65,6 +65,7 @@ struct lbo_solver {
   double* host = nullptr;                  // pinned small results
   void* netstate = nullptr;                // learned preconditioner (network.cu)
   void* coarse = nullptr;                  // moment coarse correction (coarse.cu)
+  void* mixed = nullptr;                   // cells of different N (mixed.cu)
   bool force_sweep = false;                // fallback from the learned preconditioner
   double shift = 0, r_first = 0;           // pseudo-transient shift 1/dtau, first residual norm
   const double* fcur = nullptr;            // state of the current step (exact Jacobian)
@@ -82,6 +83,17 @@ void free_network(lbo_solver* S);
 // slab operator A' (with or without the mass border) and y = a x + b y (solver.cu)
 lbo_status solver_apply_op(lbo_solver* S, const double* v, double* out, bool border, bool collisions);
 void solver_axpby(lbo_solver* S, double* y, const double* x, double a, double b);
+double solver_norm2(lbo_solver* S, const double* y, lbo_status* st);
+lbo_status solver_sweep_uniform(lbo_solver* S, const double* r, double* z, int N, double h);
+// cells of different N (mixed.cu)
+lbo_status mixed_setup(lbo_solver* S, lbo_plan* const* plans, int nplans, const int* cell_plan);
+size_t mixed_state_length(const lbo_plan* const* plans, int nx, const int* cell_plan);
+void mixed_moments(lbo_solver* S, const double* f, double* params, double* nu);
+lbo_status mixed_residual(lbo_solver* S, const double* f, double* out, double* nrm);
+lbo_status mixed_apply_op(lbo_solver* S, const double* v, double* out);
+lbo_status mixed_sweep(lbo_solver* S, const double* v, double* z);
+lbo_status mixed_set_residual_plan(lbo_solver* S, lbo_plan* plan);
+void free_mixed(lbo_solver* S);
 // moment coarse correction (coarse.cu)
 lbo_status coarse_assemble(lbo_solver* S, bool border);
 bool coarse_valid(const lbo_solver* S);

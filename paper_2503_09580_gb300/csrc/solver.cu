@@ -1,6 +1,7 @@
 // Modified Newton / flexible GMRES solver (Sec. 5 and the supplement's fully
 // discrete scheme) on top of a plan's L[g] and Q(f,f).  Host-side Arnoldi on
 // small matrices; every long-vector operation is an FP64 kernel here.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -287,6 +288,7 @@ lbo_status exact_jacobian_q(lbo_solver* S, const double* v) {
 // collisions = false drops the collision term (SLAB only): the transport,
 // border and shift parts alone, for the transport-only coarse operator
 lbo_status apply_op(lbo_solver* S, const double* v, double* out, bool border = true, bool collisions = true) {
+  if (S->mixed) return collisions ? mixed_apply_op(S, v, out) : LBO_EUNSUPPORTED;
   if (!collisions && S->pb.kind != LBO_PROBLEM_SLAB) return LBO_EINVAL;
   lbo_status st = !collisions          ? LBO_OK
                   : S->pb.jacobian == 1 ? exact_jacobian_q(S, v)
@@ -321,6 +323,7 @@ lbo_status sweep_only(lbo_solver* S, const double* v, double* z) {
 
 // Nonlinear residual into out (and its weighted norm).
 lbo_status residual(lbo_solver* S, const double* f, const double* f_prev, double* out, double* nrm) {
+  if (S->mixed) return mixed_residual(S, f, out, nrm);
   lbo_plan* qp = S->rplan ? S->rplan : S->plan;
   qp->stream = S->plan->stream;
   lbo_status st = lbo_apply_quadratic(qp, f, S->Qf, S->nx);
@@ -473,6 +476,15 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
 
 }  // namespace
 
+double solver_norm2(lbo_solver* S, const double* y, lbo_status* st) { return norm2(S, y, st); }
+
+lbo_status solver_sweep_uniform(lbo_solver* S, const double* r, double* z, int N, double h) {
+  LBO_LAUNCH(S->plan, "solver_sweep", S->plan->stream, k_sweep, grid_for((size_t)N * N * N), 256, 0, r, z, S->nu, N,
+             S->nx, h, S->dx, S->pb.kn, S->shift);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "sweep");
+}
+
 lbo_status solver_apply_op(lbo_solver* S, const double* v, double* out, bool border, bool collisions) {
   return apply_op(S, v, out, border, collisions);
 }
@@ -489,8 +501,13 @@ lbo_status apply_precond(lbo_solver* S, const double* v, double* z) {
   if (pc == LBO_PRECOND_NONE || S->pb.kind != LBO_PROBLEM_SLAB) {
     cudaMemcpyAsync(z, v, sizeof(double) * S->len, cudaMemcpyDeviceToDevice, s);
   } else {
-    LBO_LAUNCH(S->plan, "solver_sweep", s, k_sweep, grid_for(S->n3), 256, 0, v, z, S->nu, S->N, S->nx, S->h, S->dx,
-               S->pb.kn, S->shift);
+    if (S->mixed) {
+      lbo_status st = mixed_sweep(S, v, z);
+      if (st != LBO_OK) return st;
+    } else {
+      LBO_LAUNCH(S->plan, "solver_sweep", s, k_sweep, grid_for(S->n3), 256, 0, v, z, S->nu, S->N, S->nx, S->h,
+                 S->dx, S->pb.kn, S->shift);
+    }
     if (pc == LBO_PRECOND_LEARNED && !S->force_sweep) {
       lbo_status st = network_correction(S, v, z);
       if (st != LBO_OK) return st;
@@ -508,6 +525,42 @@ lbo_status apply_precond(lbo_solver* S, const double* v, double* z) {
 }  // namespace lbo
 
 using namespace lbo;
+
+// Krylov basis and work vectors of S->len doubles, small reduction buffers.
+static lbo_status solver_alloc(lbo_solver* S) {
+  const lbo_problem* pb = &S->pb;
+  const size_t len = S->len;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](double** p, size_t n) {
+    if (e == cudaSuccess) e = cudaMalloc(p, sizeof(double) * n);
+  };
+  alloc(&S->V, (size_t)(S->m + 1) * len);
+  alloc(&S->Z, (size_t)S->m * len);
+  alloc(&S->w, len);
+  alloc(&S->Lv, len);
+  alloc(&S->rhs, len);
+  alloc(&S->x, len);
+  alloc(&S->evec, len);
+  if (pb->jacobian == 1) {
+    alloc(&S->ja, len);
+    alloc(&S->jb, len);
+  }
+  alloc(&S->Qf, len);
+  alloc(&S->params, 5 * (size_t)S->nx);
+  alloc(&S->nu, S->nx);
+  alloc(&S->WL, S->n3);
+  alloc(&S->WR, S->n3);
+  alloc(&S->part, (size_t)RED_BLOCKS * 256);
+  alloc(&S->res, 8 + 256);
+  if (e == cudaSuccess) e = cudaMallocHost(&S->host, sizeof(double) * 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    lbo_solver_destroy(S);
+    set_error_text("solver allocation");
+    return LBO_ENOMEM;
+  }
+  return LBO_OK;
+}
 
 extern "C" {
 
@@ -549,36 +602,8 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
   S->h = 2.0 * plan->L / S->N;
   S->dx = pb->kind == LBO_PROBLEM_SLAB ? (pb->x_right - pb->x_left) / pb->nx : 1.0;
   S->wnorm = S->dx * S->h * S->h * S->h;
-  const size_t len = S->len;
-  cudaError_t e = cudaSuccess;
-  auto alloc = [&](double** p, size_t n) {
-    if (e == cudaSuccess) e = cudaMalloc(p, sizeof(double) * n);
-  };
-  alloc(&S->V, (size_t)(S->m + 1) * len);
-  alloc(&S->Z, (size_t)S->m * len);
-  alloc(&S->w, len);
-  alloc(&S->Lv, len);
-  alloc(&S->rhs, len);
-  alloc(&S->x, len);
-  alloc(&S->evec, len);
-  if (pb->jacobian == 1) {
-    alloc(&S->ja, len);
-    alloc(&S->jb, len);
-  }
-  alloc(&S->Qf, len);
-  alloc(&S->params, 5 * (size_t)S->nx);
-  alloc(&S->nu, S->nx);
-  alloc(&S->WL, S->n3);
-  alloc(&S->WR, S->n3);
-  alloc(&S->part, (size_t)RED_BLOCKS * 256);
-  alloc(&S->res, 8 + 256);
-  if (e == cudaSuccess) e = cudaMallocHost(&S->host, sizeof(double) * 256);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    lbo_solver_destroy(S);
-    set_error_text("solver allocation");
-    return LBO_ENOMEM;
-  }
+  lbo_status ast = solver_alloc(S);
+  if (ast != LBO_OK) return ast;
   if (pb->kind == LBO_PROBLEM_SLAB) {
     // wall Maxwellian shapes W(v) = (2 pi theta)^{-3/2} exp(-|v-u_w|^2 / (2 theta))
     std::vector<double> wl(S->n3), wr(S->n3);
@@ -610,7 +635,7 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
       S->kL = pb->bc_left == LBO_BC_WALL ? std::sqrt(2.0 * 3.141592653589793 / pb->wall_left[0]) : 0.0;
       S->kR = pb->bc_right == LBO_BC_WALL ? std::sqrt(2.0 * 3.141592653589793 / pb->wall_right[0]) : 0.0;
     }
-    e = cudaMemcpy(S->WL, wl.data(), sizeof(double) * S->n3, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(S->WL, wl.data(), sizeof(double) * S->n3, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(S->WR, wr.data(), sizeof(double) * S->n3, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       lbo_solver_destroy(S);
@@ -621,6 +646,53 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
   return LBO_OK;
 }
 
+lbo_status lbo_solver_create_mixed(const lbo_problem* pb, lbo_plan* const* plans, int nplans, const int* cell_plan,
+                                   lbo_solver** out) {
+  if (!pb || !plans || nplans < 1 || !cell_plan || !out) return LBO_EINVAL;
+  *out = nullptr;
+  if (pb->kind != LBO_PROBLEM_SLAB || pb->nx < 1 || pb->krylov_restart < 1 || pb->krylov_restart > 200 ||
+      pb->krylov_maxit < 1 || !(pb->x_right > pb->x_left) || !(pb->kn > 0))
+    return LBO_EINVAL;
+  if (pb->bc_left != LBO_BC_INFLOW || pb->bc_right != LBO_BC_INFLOW) return LBO_EUNSUPPORTED;
+  if (!(pb->inflow_left[0] > 0) || !(pb->inflow_left[4] > 0) || !(pb->inflow_right[0] > 0) ||
+      !(pb->inflow_right[4] > 0))
+    return LBO_EINVAL;
+  if (pb->precond != LBO_PRECOND_NONE && pb->precond != LBO_PRECOND_SWEEP) return LBO_EUNSUPPORTED;
+  if (pb->line_search < 0 || pb->line_search > 60 || !(pb->pseudo_dt >= 0)) return LBO_EINVAL;
+  if (pb->jacobian < 0 || pb->jacobian > 1) return LBO_EINVAL;
+  int nmax = 0;
+  for (int p = 0; p < nplans; ++p) {
+    if (!plans[p] || plans[p]->L != plans[0]->L || plans[p]->N > 64) return LBO_EINVAL;
+    for (int q = 0; q < p; ++q)
+      if (plans[q]->N == plans[p]->N) return LBO_EINVAL;  // one plan per N
+    nmax = std::max(nmax, plans[p]->N);
+  }
+  for (int j = 0; j < pb->nx; ++j)
+    if (cell_plan[j] < 0 || cell_plan[j] >= nplans) return LBO_EINVAL;
+  lbo_solver* S = new lbo_solver();
+  S->pb = *pb;
+  S->plan = plans[0];  // the stream and profiling scope of the solver's own launches
+  S->N = nmax;
+  S->nx = pb->nx;
+  S->m = pb->krylov_restart;
+  S->n3 = (size_t)nmax * nmax * nmax;
+  S->len = mixed_state_length(plans, pb->nx, cell_plan);
+  S->h = 2.0 * plans[0]->L / nmax;
+  S->dx = (pb->x_right - pb->x_left) / pb->nx;
+  S->wnorm = S->dx * S->h * S->h * S->h;  // finest cell's weight, for the absolute tolerance only
+  lbo_status st = solver_alloc(S);
+  if (st != LBO_OK) return st;
+  st = mixed_setup(S, plans, nplans, cell_plan);
+  if (st != LBO_OK) {
+    lbo_solver_destroy(S);
+    return st;
+  }
+  *out = S;
+  return LBO_OK;
+}
+
+size_t lbo_solver_state_length(const lbo_solver* S) { return S ? S->len : 0; }
+
 lbo_status lbo_solver_residual(lbo_solver* S, const double* f, const double* f_prev, double* out, double* nrm) {
   if (!S || !f || !out) return LBO_EINVAL;
   if (S->pb.kind == LBO_PROBLEM_HOMOGENEOUS && !f_prev) return LBO_EINVAL;
@@ -629,6 +701,7 @@ lbo_status lbo_solver_residual(lbo_solver* S, const double* f, const double* f_p
 
 lbo_status lbo_solver_set_residual_plan(lbo_solver* S, lbo_plan* plan) {
   if (!S) return LBO_EINVAL;
+  if (S->mixed) return mixed_set_residual_plan(S, plan);
   if (plan && (plan->N != S->plan->N || plan->L != S->plan->L)) return LBO_EINVAL;
   S->rplan = plan;
   return LBO_OK;
@@ -647,7 +720,8 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
   cudaEventCreate(&t2);
   cudaEventRecord(t0, s);
   // local Maxwellians (FP64 moments) and the nonlinear residual
-  LBO_LAUNCH(S->plan, "solver_moments", s, k_cell_moments, S->nx, 512, 0, f, S->params, S->nu, S->N, S->h);
+  if (S->mixed) mixed_moments(S, f, S->params, S->nu);
+  else LBO_LAUNCH(S->plan, "solver_moments", s, k_cell_moments, S->nx, 512, 0, f, S->params, S->nu, S->N, S->h);
   double rn = 0;
   lbo_status st = residual(S, f, f_prev, S->rhs, &rn);
   cudaEventRecord(t1, s);
@@ -694,8 +768,9 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
       LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, f, S->x, -1.0, 1.0, S->len);
       double lambda = 1.0;
       for (int ls = 0; st2 == LBO_OK && ls < S->pb.line_search; ++ls) {
-        LBO_LAUNCH(S->plan, "solver_moments", s, k_cell_moments, S->nx, 512, 0, f, S->params, (double*)nullptr,
-                   S->N, S->h);
+        if (S->mixed) mixed_moments(S, f, S->params, nullptr);
+        else LBO_LAUNCH(S->plan, "solver_moments", s, k_cell_moments, S->nx, 512, 0, f, S->params,
+                        (double*)nullptr, S->N, S->h);
         double rt = 0;
         st2 = residual(S, f, f_prev, S->w, &rt);
         if (st2 != LBO_OK) break;
@@ -733,6 +808,7 @@ void lbo_solver_destroy(lbo_solver* S) {
     if (p) cudaFree(p);
   free_network(S);
   free_coarse(S);
+  free_mixed(S);
   if (S->host) cudaFreeHost(S->host);
   delete S;
 }

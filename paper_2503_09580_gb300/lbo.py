@@ -28,7 +28,8 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_status_string", "lbo_last_error", "lbo_plan_profile", "lbo_plan_profile_count",
            "lbo_plan_profile_get", "lbo_apply_linearized_noalloc", "lbo_noalloc_scratch_bytes",
            "lbo_noalloc_bytes_per_instance", "lbo_solver_create", "lbo_newton_step", "lbo_solver_residual",
-           "lbo_solver_set_residual_plan", "lbo_solver_destroy", "lbo_network_param_count", "lbo_network_loss_grad", "lbo_solver_collect",
+           "lbo_solver_set_residual_plan", "lbo_solver_create_mixed", "lbo_solver_state_length",
+           "lbo_solver_destroy", "lbo_network_param_count", "lbo_network_loss_grad", "lbo_solver_collect",
            "lbo_solver_pair_count", "lbo_solver_train_network", "lbo_solver_get_network", "lbo_solver_set_network",
            "lbo_solver_network_param_count", "lbo_plan_autotune", "lbo_group_create", "lbo_group_set_stream",
            "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy")
@@ -125,6 +126,10 @@ def load():
     lib.lbo_solver_residual.restype = ip
     lib.lbo_solver_set_residual_plan.argtypes = [vp, vp]
     lib.lbo_solver_set_residual_plan.restype = ip
+    lib.lbo_solver_create_mixed.argtypes = [vp, vp, ip, vp, vp]
+    lib.lbo_solver_create_mixed.restype = ip
+    lib.lbo_solver_state_length.argtypes = [vp]
+    lib.lbo_solver_state_length.restype = ctypes.c_size_t
     lib.lbo_solver_destroy.argtypes = [vp]
     lib.lbo_solver_destroy.restype = None
     lib.lbo_network_param_count.argtypes = [ip]
@@ -292,7 +297,7 @@ class Solver:
                  wall_flux="analytic", dt=0.0, krylov_rtol=1e-3, krylov_atol=1e-7, krylov_restart=30,
                  krylov_maxit=300, precond="sweep", inflow_left=None, inflow_right=None, line_search=0,
                  pseudo_dt=0.0, coarse_moments=5, jacobian="local_maxwellian",
-                 coarse_operator="galerkin"):
+                 coarse_operator="galerkin", _mixed=None):
         lib = load()
         pb = Problem()
         pb.kind = PROBLEM[kind]
@@ -319,8 +324,20 @@ class Solver:
         pb.jacobian = {"local_maxwellian": 0, "exact": 1}[jacobian]
         pb.coarse_operator = {"galerkin": 0, "transport": 1}[coarse_operator]
         h = ctypes.c_void_p()
-        _check(lib.lbo_solver_create(ctypes.byref(pb), plan._h, ctypes.byref(h)), "lbo_solver_create")
+        if _mixed is None:
+            _check(lib.lbo_solver_create(ctypes.byref(pb), plan._h, ctypes.byref(h)), "lbo_solver_create")
+        else:
+            plans, cell_plan = _mixed
+            arr = (ctypes.c_void_p * len(plans))(*[q._h.value for q in plans])
+            cp = (ctypes.c_int * len(cell_plan))(*[int(c) for c in cell_plan])
+            _check(lib.lbo_solver_create_mixed(ctypes.byref(pb), arr, len(plans), cp, ctypes.byref(h)),
+                   "lbo_solver_create_mixed")
+            self._plans = list(plans)  # kept alive with the solver
         self._h, self.plan, self.problem = h, plan, pb
+
+    def state_length(self):
+        """Doubles in the state vector (sum of the cells' N^3)."""
+        return int(load().lbo_solver_state_length(self._h))
 
     def newton_step(self, f, f_prev=None):
         """One modified Newton step in place on the device tensor f; returns the stats dict."""
@@ -437,3 +454,13 @@ class Group:
             self.close()
         except Exception:
             pass
+
+
+def mixed_solver(plans, cell_plan, **problem):
+    """lbo_solver_create_mixed: a slab whose cell j uses plans[cell_plan[j]]
+    (one plan per N, the same box); `problem` as for Plan.solver (kind
+    'slab', inflow sides).  The state is the cells' fields concatenated, cell
+    j as N_j^3 doubles in centred order."""
+    problem = dict(problem)
+    problem["nx"] = len(cell_plan)
+    return Solver(plans[0], _mixed=(plans, cell_plan), **problem)
