@@ -364,6 +364,56 @@ def shock_leg(precond, nx=128, n=32, L=8.0, tol=1e-10, coarse_operator="galerkin
             "final_residual": steps[-1], "converged": steps[-1] < tol}
 
 
+def shock_mixed_leg(nx=64, L=8.0, tol=1e-10, seed=5):
+    """Mach-2 shock with a velocity grid per cell: N drawn from {24, 32, 48}
+    with probabilities 0.5 / 0.35 / 0.15 (seeded), x in [-1, 1], Kn = 0.1,
+    continuation + exact-Jacobian Newton, FP32 operator, FP64 residual per
+    N, sweep on the finest grid, until |R| < tol."""
+    import torch
+    from paper_2503_09580_gb300 import lbo
+    gam, mach = 5.0 / 3.0, 2.0
+    u1 = mach * np.sqrt(gam)
+    r = (gam + 1) * mach ** 2 / ((gam - 1) * mach ** 2 + 2)
+    p2 = 1 + 2 * gam / (gam + 1) * (mach ** 2 - 1)
+    up, down = (1.0, u1, 0.0, 0.0, 1.0), (r, u1 / r, 0.0, 0.0, p2 / r)
+    Ns = (24, 32, 48)
+    choice = np.random.default_rng(seed).choice(3, size=nx, p=[0.5, 0.35, 0.15])
+    plans = [lbo.Plan(n, L, 0.5, n, hemisphere_p=2, precision="fp32", mass_fix=1) for n in Ns]
+    rplans = [lbo.Plan(n, L, 0.5, n, hemisphere_p=2, mass_fix=1) for n in Ns]
+    solver = lbo.mixed_solver(plans, list(choice), kind="slab", x_left=-1.0, x_right=1.0, kn=0.1,
+                              inflow_left=up, inflow_right=down, krylov_rtol=1e-3, krylov_atol=1e-14,
+                              krylov_restart=40, krylov_maxit=600, precond="sweep", pseudo_dt=0.3,
+                              jacobian="exact")
+    for p in rplans:
+        solver.set_residual_plan(p)
+    x = -1.0 + (np.arange(nx) + 0.5) * (2.0 / nx)
+    cells = []
+    for c, wj in zip(choice, 0.5 * (1 + np.tanh(x / 0.15))):
+        n = Ns[c]
+        rho, uu, _, _, th = [(1 - wj) * a + wj * b for a, b in zip(up, down)]
+        a = (np.arange(n) - n // 2) * (2 * L / n)
+        cells.append((rho * (2 * np.pi * th) ** -1.5 * np.exp(-((a[:, None, None] - uu) ** 2 + a[None, :, None] ** 2
+                                                               + a[None, None, :] ** 2) / (2 * th))).ravel())
+    tf = torch.from_numpy(np.concatenate(cells)).cuda()
+    steps, its = [], 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(30):
+        st = solver.newton_step(tf)
+        steps.append(float(st["residual_norm"]))
+        its += st["krylov_iterations"]
+        if st["residual_norm"] < tol:
+            break
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    solver.close()
+    return {"workload": "Mach-2 planar shock, %d cells, N per cell from {24, 32, 48} (seeded 0.5/0.35/0.15: "
+                        "%d/%d/%d), hard spheres, Kn=0.1; continuation + exact-Jacobian Newton, FP32 operator, "
+                        "FP64 residual, sweep preconditioner" % ((nx,) + tuple(int((choice == k).sum()) for k in range(3))),
+            "seconds": secs, "newton_steps": len(steps), "krylov_iterations": its, "final_residual": steps[-1],
+            "converged": steps[-1] < tol}
+
+
 def bkw_leg(precision, steps=1, n=64, L=8.0, dt=0.05):
     """Backward-Euler steps of the homogeneous equation with the quadratic
     operator (Maxwell molecules, BKW initial data at K = 0.6), Newton with the
@@ -607,6 +657,8 @@ def run_ours(args, world, rank, local):
                         "states; continuation + exact-Jacobian Newton, FP32 operator, FP64 residual; "
                         "plain FGMRES (no preconditioner) does not converge on it",
             "sweep": shock_leg("sweep"), "moment_transport": shock_leg("moment", coarse_operator="transport")}
+        if args.shock_cells > 0:
+            line["shock_mixed_n_to_1e-10"] = shock_mixed_leg(nx=args.shock_cells)
         line["mixed_n"] = mixed_leg()
         line["n64"] = n64_leg(with_oracle=not args.no_cpu_baseline)
         line["bkw_n64"] = {"workload": "homogeneous BKW relaxation, Maxwell molecules, N=64, J=64, M=32, "
@@ -631,6 +683,8 @@ def main():
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--moment-fix", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default radial-node grouping")
+    ap.add_argument("--shock-cells", type=int, default=0,
+                    help="run the mixed-N shock leg with this many cells (64 cells: about 2.5 minutes)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
