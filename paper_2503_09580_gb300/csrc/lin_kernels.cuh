@@ -36,14 +36,12 @@ enum PlaneSrc {
   SRC_RATIO = 0,   // r = g / M, 0 where the cut-off of Eq. (3.9) applies
   SRC_REAL64 = 1,  // a double field (the ABI input g)
   SRC_MAXW = 2,    // the Maxwellian M
-  SRC_U = 3,       // u_j = M^g phit_j, cyclic displacement order
   SRC_REALT = 4    // a field of the transform precision T (a.src)
 };
 
 struct PlaneArgs {
   const double* params;  // [B][5]
   const double* g;       // [B][N^3] (SRC_RATIO / SRC_REAL64)
-  const void* phit;      // [N^3] of T (SRC_U): phit_j, cyclic order
   const void* src;       // [B][N^3] of T (SRC_REALT)
   double h;              // grid spacing
   double log_inv_eps;    // ln(1/eps)
@@ -95,29 +93,22 @@ __device__ __forceinline__ void fill_maxwellian_tables(double* em, double* thr, 
 
 template <typename T, int N, int SRC>
 __device__ __forceinline__ T plane_source(const PlaneArgs& a, const InstanceParams& q, int b, int i1, int i2, int i3,
-                                          const double* ex1, const double* em, double thr) {
-  if constexpr (SRC == SRC_U) {
-    // M^g(d) phit_j(d), d = cyclic displacement; ex1[i] = exp(-d_i^2/theta)
-    const T* ph = (const T*)a.phit;
-    double mg = ex1[N + i1] * ex1[i2] * ex1[i3];  // ex1[N..2N) carries the prefactor
-    return (T)(mg * (double)ph[(i1 * N + i2) * N + i3]);
+                                          const double* em, double thr) {
+  size_t idx = (((size_t)b * N + i1) * N + i2) * N + i3;
+  if constexpr (SRC == SRC_REALT) {
+    return ((const T*)a.src)[idx];
+  } else if constexpr (SRC == SRC_REAL64) {
+    return (T)a.g[idx];
   } else {
-    size_t idx = (((size_t)b * N + i1) * N + i2) * N + i3;
-    if constexpr (SRC == SRC_REALT) {
-      return ((const T*)a.src)[idx];
-    } else if constexpr (SRC == SRC_REAL64) {
-      return (T)a.g[idx];
-    } else {
-      double M = em[i1] * em[N + i2] * em[2 * N + i3];
-      if constexpr (SRC == SRC_MAXW) {
-        return (T)M;
-      } else {  // SRC_RATIO
-        if (a.cutoff) {
-          double d2 = dist2(i1, i2, i3, N, a.h, q);
-          if (__ddiv_rn(d2, __dmul_rn(2.0, q.theta)) > thr) return (T)0;
-        }
-        return (T)(a.g[idx] / M);
+    double M = em[i1] * em[N + i2] * em[2 * N + i3];
+    if constexpr (SRC == SRC_MAXW) {
+      return (T)M;
+    } else {  // SRC_RATIO
+      if (a.cutoff) {
+        double d2 = dist2(i1, i2, i3, N, a.h, q);
+        if (__ddiv_rn(d2, __dmul_rn(2.0, q.theta)) > thr) return (T)0;
       }
+      return (T)(a.g[idx] / M);
     }
   }
 }
@@ -201,19 +192,6 @@ __device__ __forceinline__ void plane_load_B(cpx<T>* B, const cpx<T>* src, int b
   __syncthreads();
 }
 
-// Per-instance separable Gaussian tables for M^g (SRC_U): ex[i] for axes 2,3
-// = exp(-d_i^2/theta); ex[N + i] = rho (pi theta)^{-3/2} exp(-d_i^2/theta).
-template <int N>
-__device__ __forceinline__ void fill_mg_tables(double* ex, const InstanceParams& q, double h) {
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    double d = (double)centred<N>(i) * h;
-    double e = exp(-(d * d) / q.theta);
-    ex[i] = e;
-    ex[N + i] = q.rho * pow(3.141592653589793 * q.theta, -1.5) * e;
-  }
-  __syncthreads();
-}
-
 // Per-instance separable tables for M^h = rho (pi theta)^{-3/2} prod_d exp(-(v_d-u_d)^2/theta):
 // eh[d*N + i] = exp(-(v_i-u_d)^2/theta), axis 1 carries the prefactor.
 template <int N>
@@ -236,18 +214,16 @@ __global__ void __launch_bounds__(256) k_plane_fwd(PlaneArgs a, cpx<T>* __restri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* A = (cpx<T>*)smem_raw;
   cpx<T>* B = A + PlaneSmem<T, N, PPC>::A_ELEMS;
-  __shared__ double ex[2 * N];
   __shared__ double em[3 * N];
   __shared__ double thr;
   const int b = blockIdx.y, i1_0 = blockIdx.x * PPC;
   const InstanceParams q = load_params(a.params, b);
-  if constexpr (SRC == SRC_U) fill_mg_tables<N>(ex, q, a.h);
   if constexpr (SRC == SRC_RATIO || SRC == SRC_MAXW) fill_maxwellian_tables<N>(em, &thr, q, a.h, a.log_inv_eps);
   for (int t = threadIdx.x; t < PPC * (N / 2) * N; t += blockDim.x) {
     int i3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
     int i1 = i1_0 + pp;
-    T x0 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq, i3, ex, em, thr);
-    T x1 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq + 1, i3, ex, em, thr);
+    T x0 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq, i3, em, thr);
+    T x1 = plane_source<T, N, SRC>(a, q, b, i1, 2 * qq + 1, i3, em, thr);
     A[(pp * (N / 2) + qq) * N + i3] = make_c(x0, x1);
   }
   __syncthreads();
@@ -297,7 +273,6 @@ __global__ void __launch_bounds__(256) k_plane_inv(PlaneArgs a, cpx<T>* __restri
 // ------------------------------------------------------------ axis 1
 enum Axis1Mode {
   AX_FWD_STORE = 0,   // dst = F1(src)
-  AX_FWD_MULC_INV = 1,// dst = F1^-1( F1(src) * mulc * scale ), mulc per instance
   AX_FWD_MULT_INV = 2,// dst = F1^-1( F1(src) * table[|k|^2] )
   AX_FWD_ACC = 3,     // dst (+)= table[|k|^2] * F1(src)
   AX_INV_STORE = 4,   // dst = F1^-1(src)
@@ -306,9 +281,8 @@ enum Axis1Mode {
 };
 
 struct Axis1Args {
-  const void* mulc;     // [B][H] complex T (AX_FWD_MULC_INV)
   const void* table;    // [QMAX] T (AX_FWD_MULT_INV, AX_FWD_ACC)
-  double scale;         // AX_FWD_MULC_INV, AX_UHAT_INV
+  double scale;         // AX_UHAT_INV
   int first;            // AX_FWD_ACC: store instead of accumulate
   const void* uplanes;  // [B][N/2+1]^3 T (AX_UHAT_INV): u^_j after the axis-3 and axis-2 DCTs
   const void* dct;      // [N/2+1][N/4] T (AX_UHAT_INV): DCT-I coefficients
@@ -453,18 +427,13 @@ __global__ void __launch_bounds__(256) k_axis1(Axis1Args a, const cpx<T>* __rest
     if constexpr (MODE != AX_INV_STORE) smem_fft<T, N, false, true>(S, CW, 1, CW);
     else smem_fft<T, N, true, true>(S, CW, 1, CW);
   }
-  if constexpr (MODE == AX_FWD_MULC_INV || MODE == AX_FWD_MULT_INV) {
+  if constexpr (MODE == AX_FWD_MULT_INV) {
     for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
       int c = t % CW, r = t / CW;
       if (c0 + c < NC) {
-        if constexpr (MODE == AX_FWD_MULC_INV) {
-          cpx<T> m = ((const cpx<T>*)a.mulc)[inst + (size_t)r * NC + c0 + c];
-          S[t] = cscale(cmul(S[t], m), (T)a.scale);
-        } else {
-          int col = c0 + c, p2 = col / HC, k3 = col % HC;
-          int k1 = centred<N>(freq_of_pos<N>(r)), k2 = centred<N>(freq_of_pos<N>(p2));
-          S[t] = cscale(S[t], ((const T*)a.table)[k1 * k1 + k2 * k2 + k3 * k3]);
-        }
+        int col = c0 + c, p2 = col / HC, k3 = col % HC;
+        int k1 = centred<N>(freq_of_pos<N>(r)), k2 = centred<N>(freq_of_pos<N>(p2));
+        S[t] = cscale(S[t], ((const T*)a.table)[k1 * k1 + k2 * k2 + k3 * k3]);
       }
     }
     __syncthreads();
