@@ -219,3 +219,20 @@ def test_radix3_sizes_fp64(n):
     plan32 = lbo.Plan(n, L, 0.5, n, precision="fp32")
     got32 = run(plan32, params, g)
     assert relerr(got32, ref) <= 2.0 ** -24 * ratio_max(params, g, n, L)
+
+
+def test_gpu_within_u_max_r_of_the_extended_reference():
+    """The noisy N = 16 instance of tests/golden/noisy_n16_extended.txt
+    (extended-precision direct sums): the FP64 and FP32 GPU paths are within
+    u max|r| of it at the stored points (u the unit roundoff of the
+    transform precision)."""
+    from test_oracle_extended import load_extended_golden
+    max_abs, max_ratio, vals = load_extended_golden()
+    params, g = workloads.batched_instances(16, 8.0, batch=1, seed=31, noise=1e-3)
+    idx = np.array([i for i, _ in vals])
+    ref = np.array([v for _, v in vals])
+    for prec, u in (("fp64", 2.0 ** -53), ("fp32", 2.0 ** -24)):
+        out = run(lbo.Plan(16, 8.0, 0.5, 16, precision=prec), params, g)[0].ravel()
+        err = np.abs(out[idx] - ref).max() / max_abs
+        print(prec, "error against the extended reference %.3e, bound %.3e" % (err, u * max_ratio))
+        assert err <= u * max_ratio
