@@ -55,15 +55,21 @@ void hemisphere_rule(int p, std::vector<double>& sig, std::vector<double>& wm) {
   }
 }
 
-// F (after all three forward passes) -> x E and x conj(E), inverse axis 1 of both.
+// F (after all three forward passes) -> x E and x conj(E), inverse axis 1 of
+// both, for hemisphere node m0 + blockIdx.z: alpha_d = c sigma_(m,d), results
+// at W1, W2 + blockIdx.z * mstride.
 template <typename T, int N, int CW>
-__global__ void __launch_bounds__(256) k_axis1_phase(const cpx<T>* __restrict__ FH, cpx<T>* __restrict__ W1,
-                                                     cpx<T>* __restrict__ W2, double al1, double al2, double al3) {
+__global__ void __launch_bounds__(256) k_axis1_phase(const cpx<T>* __restrict__ FH, cpx<T>* __restrict__ W1b,
+                                                     cpx<T>* __restrict__ W2b, const double* __restrict__ sig,
+                                                     int m0, double cj, size_t mstride) {
   constexpr int HC = N / 2 + 1, NC = N * HC;
   __shared__ __align__(16) cpx<T> S1[N * CW];
   __shared__ __align__(16) cpx<T> S2[N * CW];
   __shared__ cpx<double> mf[3 * N];  // per-axis factors, indexed by cyclic frequency
-  const int b = blockIdx.y, c0 = blockIdx.x * CW;
+  const int b = blockIdx.y, c0 = blockIdx.x * CW, m = m0 + blockIdx.z;
+  const double al1 = cj * sig[3 * m], al2 = cj * sig[3 * m + 1], al3 = cj * sig[3 * m + 2];
+  cpx<T>* W1 = W1b + blockIdx.z * mstride;
+  cpx<T>* W2 = W2b + blockIdx.z * mstride;
   const size_t inst = (size_t)b * N * NC;
   for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) {
     const int d = t / N, k = t % N;
@@ -106,10 +112,17 @@ __global__ void __launch_bounds__(256) k_axis1_phase(const cpx<T>* __restrict__ 
   }
 }
 
-// Inverse planes of W1, W2 -> T+, T-; P (+)= scale * T+ T- (real field, T).
+// Inverse planes of W1, W2 -> T+, T-; P = 4 w_m T+ T- (real field, T) for
+// hemisphere node m0 + blockIdx.z (inputs and output offset by blockIdx.z).
 template <typename T, int N, int PPC>
-__global__ void __launch_bounds__(256) k_plane_inv_prod(const cpx<T>* __restrict__ W1, const cpx<T>* __restrict__ W2,
-                                                        T* __restrict__ P, double scale, int first) {
+__global__ void __launch_bounds__(256) k_plane_inv_prod(const cpx<T>* __restrict__ W1b, const cpx<T>* __restrict__ W2b,
+                                                        T* __restrict__ Pb, const double* __restrict__ wm, int m0,
+                                                        size_t mstride, size_t pstride) {
+  const cpx<T>* W1 = W1b + blockIdx.z * mstride;
+  const cpx<T>* W2 = W2b + blockIdx.z * mstride;
+  T* P = Pb + blockIdx.z * pstride;
+  // 4 w_m: phi_j carries 4 pi^2 w_j B_j s_j / N^3, Eq. (2.14) needs 16 pi^2
+  const double scale = 4.0 * wm[m0 + blockIdx.z];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int E = PlaneSmem<T, N, PPC>::A_ELEMS + PlaneSmem<T, N, PPC>::B_ELEMS;
   cpx<T>* A1 = (cpx<T>*)smem_raw;
@@ -126,15 +139,36 @@ __global__ void __launch_bounds__(256) k_plane_inv_prod(const cpx<T>* __restrict
     const int i3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
     const cpx<T> zp = A1[(pp * (N / 2) + qq) * N + i3], zm = A2[(pp * (N / 2) + qq) * N + i3];
     const size_t o = (((size_t)b * N + i1_0 + pp) * N + 2 * qq) * N + i3;
-    const T v0 = sc * zp.x * zm.x, v1 = sc * zp.y * zm.y;
-    if (first) {
-      P[o] = v0;
-      P[o + N] = v1;
-    } else {
-      P[o] += v0;
-      P[o + N] += v1;
-    }
+    P[o] = sc * zp.x * zm.x;
+    P[o + N] = sc * zp.y * zm.y;
   }
+}
+
+// Ps (+)= sum over the chunk's hemisphere nodes of P_m, in the order of m
+__global__ void k_sum_m_f(const float* __restrict__ Pm, float* __restrict__ Ps, int mb, size_t pstride, size_t total,
+                          int first) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    float acc = first ? Pm[t] : Ps[t] + Pm[t];
+    for (int z = 1; z < mb; ++z) acc += Pm[z * pstride + t];
+    Ps[t] = acc;
+  }
+}
+__global__ void k_sum_m_d(const double* __restrict__ Pm, double* __restrict__ Ps, int mb, size_t pstride,
+                          size_t total, int first) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    double acc = first ? Pm[t] : Ps[t] + Pm[t];
+    for (int z = 1; z < mb; ++z) acc += Pm[z * pstride + t];
+    Ps[t] = acc;
+  }
+}
+
+// hemisphere nodes per launch: all M, unless their buffers would pass 1 GiB
+int q_chunk(int B, int M, int N) {
+  const size_t H = (size_t)N * N * (N / 2 + 1), n3 = (size_t)N * N * N;
+  const size_t per_m = (size_t)B * (2 * H * 16 + n3 * 8);
+  const size_t cap = (size_t)1 << 30;
+  int mb = (int)std::max<size_t>(1, cap / std::max<size_t>(per_m, 1));
+  return std::min(mb, std::max(M, 1));
 }
 
 // out = Q+ - f u  (FP64)
@@ -194,14 +228,29 @@ lbo_status run_quadratic(lbo_plan* p, QuadState* qs, const double* f, double* ou
   launches += 2;
   const int M = (int)qs->wm.size();
   const double pi = 3.141592653589793238462643383279502884;
+  // hemisphere nodes in chunks of MB per launch (grid z): their inverse
+  // transforms and products land in separate slots, summed in the order of m
+  const int MB = q_chunk(B, M, N);
+  cpx<T>* Wm1 = (cpx<T>*)(R2 + (size_t)B * n3);
+  cpx<T>* Wm2 = Wm1 + (size_t)MB * B * H;
+  T* Pm = (T*)(Wm2 + (size_t)MB * B * H);
+  const double* dsig = qs->d_gsw + p->J;
+  const double* dwm = dsig + 3 * M;
+  const size_t total = (size_t)B * n3;
+  const int cb = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
   for (int j = 0; j < p->J; ++j) {
-    for (int m = 0; m < M; ++m) {
-      const double c = pi * p->gj[j] / (2.0 * p->L);
-      LBO_LAUNCH(p, "q_axis1_phase", s, ka_ph, ga, blk, 0, FH, W1, W2, c * qs->sig[3 * m], c * qs->sig[3 * m + 1],
-                 c * qs->sig[3 * m + 2]);
-      // 4 w_m: phi_j carries 4 pi^2 w_j B_j s_j / N^3, Eq. (2.14) needs 16 pi^2
-      LBO_LAUNCH(p, "q_plane_inv_prod", s, kp_prod, gp, blk, 2 * sm, W1, W2, Ps, 4.0 * qs->wm[m], m == 0 ? 1 : 0);
-      launches += 2;
+    const double c = pi * p->gj[j] / (2.0 * p->L);
+    for (int m0 = 0; m0 < M; m0 += MB) {
+      const int mb = std::min(MB, M - m0);
+      LBO_LAUNCH(p, "q_axis1_phase", s, ka_ph, dim3(ga.x, B, mb), blk, 0, FH, Wm1, Wm2, dsig, m0, c,
+                 (size_t)B * H);
+      LBO_LAUNCH(p, "q_plane_inv_prod", s, kp_prod, dim3(gp.x, B, mb), blk, 2 * sm, Wm1, Wm2, Pm, dwm, m0,
+                 (size_t)B * H, total);
+      if constexpr (sizeof(T) == 8)
+        LBO_LAUNCH(p, "q_sum_m", s, k_sum_m_d, cb, 256, 0, Pm, Ps, mb, total, total, m0 == 0 ? 1 : 0);
+      else
+        LBO_LAUNCH(p, "q_sum_m", s, k_sum_m_f, cb, 256, 0, Pm, Ps, mb, total, total, m0 == 0 ? 1 : 0);
+      launches += 3;
     }
     pa.src = Ps;
     LBO_LAUNCH(p, "q_plane_fwd_p", s, kf_t, gp, blk, sm, pa, W1);
@@ -219,8 +268,6 @@ lbo_status run_quadratic(lbo_plan* p, QuadState* qs, const double* f, double* ou
   LBO_LAUNCH(p, "q_plane_fwd_f", s, kf_real, gp, blk, sm, pa, W1);
   LBO_LAUNCH(p, "q_axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
   LBO_LAUNCH(p, "q_plane_inv", s, ki_real, gp, blk, sm, pa, W1, R2);
-  const size_t total = (size_t)B * n3;
-  const int cb = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
   LBO_LAUNCH(p, "q_combine", s, k_comb, cb, 256, 0, f, R1, R2, out, total);
   launches += 6;
   if (p->mass_fix || p->moment_fix) {
@@ -270,7 +317,10 @@ lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int
   const bool fused = p->precision == LBO_PREC_FP32 && p->N == 32 && p->kernel_choice == 0;
   const int G = fused ? (p->jgroups > 0 ? std::min(p->jgroups, p->J) : std::min(fused32_default_groups(B), p->J)) : 0;
   const size_t N = p->N, H = N * N * (N / 2 + 1), n3 = N * N * N;
-  const size_t need = fused ? quad_fused32_workspace_bytes(B, G) : (size_t)B * (4 * H * 16 + 3 * n3 * 8);
+  const int M = (int)qs->wm.size();
+  const size_t MB = fused ? 0 : (size_t)q_chunk(B, M, (int)N);
+  const size_t need = fused ? quad_fused32_workspace_bytes(B, G)
+                            : (size_t)B * (4 * H * 16 + 3 * n3 * 8) + MB * (size_t)B * (2 * H * 16 + n3 * 8);
   if (need > qs->ws_bytes) {
     if (qs->ws) cudaFree(qs->ws);
     qs->ws = nullptr;
@@ -283,7 +333,7 @@ lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int
     }
     qs->ws_bytes = need;
   }
-  if (fused) {
+  {
     // radial nodes, hemisphere nodes and weights on the device
     if (qs->gsw_p != qs->p || qs->gsw_plan_tables != (const void*)p->d_phi32) {
       if (qs->d_gsw) cudaFree(qs->d_gsw);
@@ -297,6 +347,8 @@ lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int
       qs->gsw_p = qs->p;
       qs->gsw_plan_tables = p->d_phi32;
     }
+  }
+  if (fused) {
     int launches = 0;
     lbo_status st = run_quadratic_fused32(p, f, out, B, qs->ws, qs->d_gsw, (int)qs->wm.size(), G, &launches);
     if (st == LBO_OK && (p->mass_fix || p->moment_fix))
