@@ -101,3 +101,39 @@ def test_exact_jacobian_is_the_derivative_of_the_residual():
         else:  # inflow ghosts are constant data: they cancel in the difference
             fd = (S.residual(f + 0.5 * g) - S.residual(f - 0.5 * g)) / 1.0
             assert np.abs(fd - Jg).max() <= 1e-9 * np.abs(Jg).max()
+
+
+def test_bordered_newton_step_lands_on_the_total_mass():
+    """Walls with the grid-sum wall flux and a mass-conserving Q (zero mode
+    removed): every residual has zero total mass, and with the exact
+    Jacobian (whose Q carries the same fix) so does every operator image, so
+    the bordered system of the Newton step gives m(f - g) = C exactly
+    (Eq. (5.3)), from a state of another mass."""
+    S = Slab(8, 5.0, 1.0, 8, nx=3, kn=1.0, hemisphere=hemisphere_rule(1), wall_flux="discrete",
+             q_mass_fix="zero_mode")
+    a = (np.arange(8) - 4) * S.h
+    f = np.stack([_maxwell(a, (1.0 + 0.1 * j, 0.0, 0.0, 0.0, 1.0 + 0.3 * j)) for j in range(3)])
+    R = S.residual(f)
+    assert abs(S.mass(R)) <= 1e-13 * S.mass(np.abs(R))
+    C = 1.1 * S.mass(f)
+    f_new, g, _ = S.newton_step(f, C, rtol=1e-12, restart=80, maxiter=200, jacobian="exact")
+    assert abs(S.mass(f_new) - C) <= 1e-11 * C
+
+
+def test_exact_jacobian_at_a_maxwellian_approaches_the_linearized_operator():
+    """At a global Maxwellian the exact Jacobian's collision part is the
+    M-point bilinear form Q(M, g) + Q(g, M), the form Sec. 4.1 compares with
+    the M-free L[g]: at N = 16 they differ by the truncation (the paper's
+    Table 1 gives 3.2e-3 at this resolution), a difference that no longer
+    changes with the hemisphere order."""
+    a = (np.arange(16) - 8) * (2 * 6.0 / 16)
+    M = _maxwell(a, (1.0, 0.0, 0.0, 0.0, 1.0))
+    g = M * (1.0 + 0.3 * a[:, None, None] - 0.2 * a[None, :, None] ** 2 + 0.1 * a[None, None, :])
+    errs = []
+    for p in (4, 8):
+        S = Slab(16, 6.0, 1.0, 16, nx=1, kn=1.0, hemisphere=hemisphere_rule(p), wall_flux="discrete")
+        lin = S.linear_operator(np.array([[1.0, 0.0, 0.0, 0.0, 1.0]]))(g[None])
+        ex = S.exact_jacobian(M[None])(g[None])
+        errs.append(np.abs(ex - lin).max() / np.abs(lin).max())
+    assert 1e-4 < errs[0] < 5e-3
+    assert abs(errs[0] - errs[1]) < 0.05 * errs[0]
