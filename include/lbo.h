@@ -165,8 +165,10 @@ typedef enum {
 typedef enum { LBO_WALL_FLUX_ANALYTIC = 0, LBO_WALL_FLUX_DISCRETE = 1 } lbo_wall_flux;
 /* Inflow boundary (not in the paper, which treats walls only): the ghost
  * cell holds the given Maxwellian for the residual and zero for the Newton
- * correction; with inflow on both sides the total mass C fixes the position
- * of a steady shock (same bordered constraint as for walls). */
+ * correction.  An inflow side removes the mass null mode of the operator, so
+ * the bordered mass constraint applies only between two walls and
+ * total_mass is then ignored; nothing pins the position of a steady shock
+ * between two inflow sides. */
 typedef enum { LBO_BC_WALL = 0, LBO_BC_INFLOW = 1 } lbo_boundary;
 
 typedef struct {
@@ -242,9 +244,14 @@ typedef struct {
  * preconditioned vectors).  LBO_EINVAL for inconsistent problem data. */
 lbo_status lbo_solver_create(const lbo_problem *problem, lbo_plan *plan, lbo_solver **out);
 
-/* One modified Newton step in place on the device state f (nx*N^3).
+/* One Newton step in place on the device state f (nx*N^3): the modified
+ * step of Eqs. (5.4), (5.6) or the exact-Jacobian step (problem.jacobian),
+ * with continuation and line search as the problem sets them.
  * f_prev: the previous time level (HOMOGENEOUS; ignored for SLAB).
- * stats may be NULL. */
+ * stats may be NULL.  An inner solve that stops at its cap still applies
+ * the step and returns LBO_ENOTCONV (also in stats->status); LBO_ENAN for a
+ * non-finite residual (state unchanged), LBO_EINVAL / LBO_ECUDA for
+ * argument and CUDA errors. */
 lbo_status lbo_newton_step(lbo_solver *solver, double *f, const double *f_prev, lbo_newton_stats *stats);
 
 /* Evaluate the nonlinear residual R(f) (SLAB) or F(f) (HOMOGENEOUS) into

@@ -340,7 +340,9 @@ class Solver:
         return int(load().lbo_solver_state_length(self._h))
 
     def newton_step(self, f, f_prev=None):
-        """One modified Newton step in place on the device tensor f; returns the stats dict."""
+        """One Newton step (modified or exact Jacobian, as the problem sets it) in place on the
+        device tensor f; returns the stats dict (converged_inner False when the inner solve hit
+        its cap: the step is applied all the same)."""
         st = NewtonStats()
         self.plan._stream(f)
         rc = load().lbo_newton_step(self._h, _ptr(f), None if f_prev is None else _ptr(f_prev), ctypes.byref(st))
