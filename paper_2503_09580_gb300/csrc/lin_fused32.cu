@@ -21,6 +21,7 @@
 
 #include "fused32.cuh"
 #include "lbo_internal.h"
+#include "tmem.cuh"
 
 namespace lbo {
 namespace {
@@ -281,6 +282,17 @@ __device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T
   }
 }
 
+// The gain blocks hold the running partial L^+ in tensor memory: thread t
+// owns the same pencil (i2, k3) = (t / 17, t % 17) in the first and the last
+// pass of every j, so its 32 complex sums stay in 64 TMEM columns of its
+// lane (warp w: lanes 32 (w % 4) + lane, columns 64 (w / 4) .. + 63; 17
+// warps use 320 of the 512 columns) instead of a read-modify-write of the
+// global partial per j.  The last j adds and writes the partial to global
+// memory.  The dynamic shared memory keeps one such block per SM (two would
+// need more than the SM's 228 KB), so the 512-column allocation never waits.
+static_assert(2 * sizeof(cpx<float>) * S_TOTAL > 228 * 1024, "gain blocks must not share an SM");
+static_assert(64 * ((F_THREADS / 32 + 3) / 4) <= tmem::kColumns, "partial sums exceed TMEM");
+
 // grid (G + 1, B): blocks x < G run the gain term for their group of radial
 // nodes (partial L^+ = sum_j phi_j FFT(M^h InvFFT(u^_j r^))); block x = G
 // writes the loss term of the instance into out.
@@ -289,6 +301,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
   cpx<float>* V = (cpx<float>*)smem;
   __shared__ float mh[3 * F_N];
   __shared__ PrepTables T;
+  __shared__ uint32_t tmem_slot;
   const int grp = blockIdx.x, b = blockIdx.y, t = threadIdx.x;
   const InstanceParams q = load_params(a.params, b);
   if (grp == a.G) {
@@ -297,6 +310,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
     return;
   }
   const int j0 = (a.J * grp) / a.G, j1 = (a.J * (grp + 1)) / a.G;
+  if (t < 32) tmem::alloc(&tmem_slot, tmem::kColumns);
   if (t < 3 * F_N) {
     int dd = t / F_N, i = t % F_N;
     double ud = dd == 0 ? q.u1 : (dd == 1 ? q.u2 : q.u3);
@@ -305,7 +319,11 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
     if (dd == 0) e *= q.rho * pow(3.141592653589793 * q.theta, -1.5);
     mh[t] = (float)e;
   }
+  tmem::fence_before_sync();
   __syncthreads();
+  tmem::fence_after_sync();
+  const uint32_t tbase = tmem_slot;
+  const uint32_t tacc = tmem::addr(tbase, 32u * ((t >> 5) & 3), 64u * (t >> 7));
   const cpx<float>* rh = a.rhat + (size_t)b * F_H;
   cpx<float>* acc = a.part + ((size_t)grp * a.B + b) * F_H;
   for (int j = j0; j < j1; ++j) {
@@ -342,23 +360,44 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
     __syncthreads();
     axis_pass<2, false>(V);
     __syncthreads();
-    {  // axis 1 forward, accumulate phi_j(|k|^2) psi^_j
+    {  // axis 1 forward, accumulate phi_j(|k|^2) psi^_j (TMEM; global at the last j)
       const int i2 = t / F_HC, k3 = t % F_HC;
       cpx<float>* base = V + srow(i2) + k3;
       cpx<float>* ac = acc + i2 * F_HC + k3;
       const float* ph = a.phi + (size_t)j * a.Q;
+      const bool first = j == j0, last = j + 1 == j1;
       cpx<float> x[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i) x[i] = base[i * S_PLANE];
       fft32<false>(x);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        cpx<float> v = cscale(x[i], __ldg(ph + ksq(i, i2, k3)));
-        ac[i * F_ROW] = j == j0 ? v : ac[i * F_ROW] + v;
+      for (int c = 0; c < 8; ++c) {  // 4 complex sums = 8 columns per chunk
+        uint32_t r[8];
+        if (!first) {
+          tmem::ld8(tacc + 8 * c, r);
+          tmem::wait_ld(r);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int i = 4 * c + e;
+          cpx<float> v = cscale(x[i], __ldg(ph + ksq(i, i2, k3)));
+          if (!first) v = make_c(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1])) + v;
+          if (last) {
+            ac[i * F_ROW] = v;
+          } else {
+            r[2 * e] = __float_as_uint(v.x);
+            r[2 * e + 1] = __float_as_uint(v.y);
+          }
+        }
+        if (!last) tmem::st8(tacc + 8 * c, r);
       }
+      if (!last) tmem::wait_st();
     }
+    tmem::fence_before_sync();
     __syncthreads();
+    tmem::fence_after_sync();
   }
+  if (t < 32) tmem::dealloc(tbase, tmem::kColumns);
 }
 
 // out = InvFFT(sum over groups of the partial L^+) + the loss term, in FP64.
