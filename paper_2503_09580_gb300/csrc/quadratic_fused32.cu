@@ -6,19 +6,24 @@
 //   k_q32_gain:  grid (G + 1) x batch.  Blocks x < G take a group of radial
 //                nodes j; for each hemisphere node m they invert F E and
 //                F conj(E) on chip (E the Nyquist-averaged phase multiplier
-//                of alpha = pi g_j sigma_m / (2L)), park T+ in a per-block
-//                scratch and accumulate 4 w_m T+ T- in real space (scratch);
+//                of alpha = pi g_j sigma_m / (2L)), park T+ in tensor memory
+//                and accumulate 4 w_m T+ T- in real space (tensor memory);
 //                after the m loop one forward transform and the
 //                phi_j(|k|^2)-weighted accumulation into a per-group partial
 //                spectrum.  Block x = G writes the loss term -f InvFFT(F omega).
 //   k_q32_tail:  out += InvFFT(sum of the partial spectra).
-// The scratch rows of a block are written and read by the thread that owns
-// them (row pair (i1, q)), so they need no synchronisation; the working set
-// of the resident blocks (2 x 128 KB each) stays in L2.
+// T+ and the m-sum (128 KB each per block) are written and read only by the
+// thread that owns their row pair (i1, q) (t < 512), so they live in that
+// thread's TMEM lane: warp w (< 16) holds lanes 32 (w % 4) + lane, T+ in
+// columns 128 (w / 4) + (0..63) and the m-sum in 128 (w / 4) + (64..127),
+// column 2 i3 + r for element (i3, r) of the pair -- all 512 columns of the
+// SM.  The dynamic shared memory keeps one gain block per SM, so the
+// allocation never waits.
 #include <cmath>
 
 #include "fused32.cuh"
 #include "lbo_internal.h"
+#include "tmem.cuh"
 
 namespace lbo {
 namespace {
@@ -30,7 +35,6 @@ struct QArgs {
   const float* phi;    // [J][QMAX]: 4 pi^2 w_j B_j s_j / N^3
   const float* omega;  // [QMAX] / N^3
   const double* gsw;   // [J] radial nodes, then [M][3] sigma, then [M] w_m
-  float* scratch;      // [(G+1) B][2][N^3]: T+ and the m-sum of w_m T+ T-
   cpx<float>* part;    // [G][B][F_H]
   double* out;         // [B][N^3]
   double L;
@@ -85,40 +89,62 @@ __device__ __forceinline__ void phase_axis1(cpx<float>* V, const cpx<float>* Fb,
   for (int i = 0; i < 32; ++i) base[i * S_PLANE] = x[i];
 }
 
-// Scratch layout of a block: element (i3, r) of the row pair owned by thread
-// t (< 512) at [(2 i3 + r) * 512 + t], so that a warp touches 128 contiguous
-// bytes per access.
-__device__ __forceinline__ void rows_store_tplus(const cpx<float>* V, float* Tp, int t) {
+static_assert(2 * sizeof(cpx<float>) * S_TOTAL > 228 * 1024, "gain blocks must not share an SM");
+static_assert(128 * (512 / 32 / 4) == tmem::kColumns, "T+ and the m-sum fill TMEM exactly");
+
+// T+ (TMEM columns tp .. tp + 63) <- inverse row transform of the row pair of thread t
+__device__ __forceinline__ void rows_store_tplus(const cpx<float>* V, uint32_t tp, int t) {
   const int i1 = t >> 4, qq = t & 15;
   cpx<float> z[32];
   load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
   fft32<true>(z);
 #pragma unroll
-  for (int i3 = 0; i3 < 32; ++i3) {
-    Tp[(2 * i3) * 512 + t] = z[i3].x;
-    Tp[(2 * i3 + 1) * 512 + t] = z[i3].y;
+  for (int c = 0; c < 8; ++c) {  // i3 = 4c .. 4c + 3
+    uint32_t r[8];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      r[2 * e] = __float_as_uint(z[4 * c + e].x);
+      r[2 * e + 1] = __float_as_uint(z[4 * c + e].y);
+    }
+    tmem::st8(tp + 8 * c, r);
   }
+  tmem::wait_st();
 }
 
-__device__ __forceinline__ void rows_accumulate(const cpx<float>* V, const float* Tp, float* Pm, int t, float wq,
-                                                bool first) {
+// m-sum (columns pm .. pm + 63) (+)= w T+ T-, T- the inverse row transform
+template <bool FIRST>
+__device__ __forceinline__ void rows_accumulate(const cpx<float>* V, uint32_t tp, uint32_t pm, int t, float wq) {
   const int i1 = t >> 4, qq = t & 15;
   cpx<float> z[32];
   load_merge(V + i1 * S_PLANE + qq * S_PAIR, z);
   fft32<true>(z);
 #pragma unroll
-  for (int i3 = 0; i3 < 32; ++i3) {
-    const int o0 = (2 * i3) * 512 + t, o1 = o0 + 512;
-    const float v0 = wq * Tp[o0] * z[i3].x, v1 = wq * Tp[o1] * z[i3].y;
-    Pm[o0] = first ? v0 : Pm[o0] + v0;
-    Pm[o1] = first ? v1 : Pm[o1] + v1;
+  for (int c = 0; c < 8; ++c) {  // i3 = 4c .. 4c + 3
+    uint32_t a[8];
+    tmem::ld8(tp + 8 * c, a);
+    tmem::wait_ld(a);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {  // a <- w T+ T-
+      a[2 * e] = __float_as_uint(wq * __uint_as_float(a[2 * e]) * z[4 * c + e].x);
+      a[2 * e + 1] = __float_as_uint(wq * __uint_as_float(a[2 * e + 1]) * z[4 * c + e].y);
+    }
+    if (!FIRST) {
+      uint32_t s[8];
+      tmem::ld8(pm + 8 * c, s);
+      tmem::wait_ld(s);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = __float_as_uint(__uint_as_float(s[k]) + __uint_as_float(a[k]));
+    }
+    tmem::st8(pm + 8 * c, a);
   }
+  tmem::wait_st();
 }
 
 __global__ void __launch_bounds__(F_THREADS, 1) k_q32_gain(QArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   cpx<float>* V = (cpx<float>*)smem;
   __shared__ cpx<float> e[96];
+  __shared__ uint32_t tmem_slot;
   const int grp = blockIdx.x, b = blockIdx.y, t = threadIdx.x;
   const cpx<float>* Fb = a.F + (size_t)b * F_H;
   const double* fb = a.f + (size_t)b * 32768;
@@ -153,8 +179,12 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_gain(QArgs a) {
     return;
   }
   const int j0 = (a.J * grp) / a.G, j1 = (a.J * (grp + 1)) / a.G;
-  float* Tp = a.scratch + ((size_t)grp * a.B + b) * 2 * 32768;
-  float* Pm = Tp + 32768;
+  if (t < 32) tmem::alloc(&tmem_slot, tmem::kColumns);
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  const uint32_t tbase = tmem_slot;
+  const uint32_t tp = tmem::addr(tbase, 32u * ((t >> 5) & 3), 128u * (t >> 7)), pm = tp + 64;
   const double* sig = a.gsw + a.J;
   const double* wm = sig + 3 * a.M;
   cpx<float>* acc = a.part + ((size_t)grp * a.B + b) * F_H;
@@ -173,19 +203,22 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_gain(QArgs a) {
       }
       __syncthreads();
       const float wq = (float)(4.0 * wm[m]);
-      // T+ : inverse of F E, parked in the scratch
+      // T+ : inverse of F E, parked in tensor memory
       phase_axis1<false>(V, Fb, e);
       __syncthreads();
       axis_pass<2, true>(V);
       __syncthreads();
-      if (t < 512) rows_store_tplus(V, Tp, t);
+      if (t < 512) rows_store_tplus(V, tp, t);
       __syncthreads();
       // T- : inverse of F conj(E); accumulate w_m T+ T-
       phase_axis1<true>(V, Fb, e);
       __syncthreads();
       axis_pass<2, true>(V);
       __syncthreads();
-      if (t < 512) rows_accumulate(V, Tp, Pm, t, wq, m == 0);
+      if (t < 512) {
+        if (m == 0) rows_accumulate<true>(V, tp, pm, t, wq);
+        else rows_accumulate<false>(V, tp, pm, t, wq);
+      }
     }
     // forward transform of the m-sum, phi_j-weighted accumulation
     __syncthreads();
@@ -193,7 +226,13 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_gain(QArgs a) {
       const int i1 = t >> 4, qq = t & 15;
       cpx<float> z[32];
 #pragma unroll
-      for (int i3 = 0; i3 < 32; ++i3) z[i3] = make_c(Pm[(2 * i3) * 512 + t], Pm[(2 * i3 + 1) * 512 + t]);
+      for (int c = 0; c < 8; ++c) {
+        uint32_t s[8];
+        tmem::ld8(pm + 8 * c, s);
+        tmem::wait_ld(s);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) z[4 * c + e] = make_c(__uint_as_float(s[2 * e]), __uint_as_float(s[2 * e + 1]));
+      }
       fft32<false>(z);
       split_store(z, V + i1 * S_PLANE + qq * S_PAIR);
     }
@@ -216,6 +255,10 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_gain(QArgs a) {
       }
     }
   }
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
+  if (t < 32) tmem::dealloc(tbase, tmem::kColumns);
 }
 
 // out += InvFFT(sum of the partial gain spectra)
@@ -257,9 +300,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_q32_tail(QArgs a) {
 
 }  // namespace
 
-size_t quad_fused32_workspace_bytes(int B, int G) {
-  return (size_t)B * F_H * 8 * (1 + (size_t)G) + (size_t)(G + 1) * B * 2 * 32768 * 4;
-}
+size_t quad_fused32_workspace_bytes(int B, int G) { return (size_t)B * F_H * 8 * (1 + (size_t)G); }
 
 lbo_status run_quadratic_fused32(lbo_plan* p, const double* f, double* out, int B, void* ws, const double* d_gsw,
                                  int M, int G, int* launches) {
@@ -277,7 +318,6 @@ lbo_status run_quadratic_fused32(lbo_plan* p, const double* f, double* out, int 
   a.f = f;
   a.F = (cpx<float>*)ws;
   a.part = a.F + (size_t)B * F_H;
-  a.scratch = (float*)(a.part + (size_t)G * B * F_H);
   a.phi = p->d_phi32;
   a.omega = p->d_omega32;
   a.gsw = d_gsw;
