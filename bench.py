@@ -38,7 +38,7 @@ PEAK_TFLOPS = {"fp64": 4 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12,
                "fp32": 256 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12}
 # DRAM bytes (read + write) per launch of the dominant kernel at the benchmark
 # workload, from ncu (profiles/*.md); None when not captured for this build.
-NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456, ("f32_gain", 32, "fp32"): None}
+NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456, ("f32_gain", 32, "fp32"): 370405376}
 
 
 def transform_axis_flops(n):
