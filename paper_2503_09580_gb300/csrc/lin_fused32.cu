@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_tail(FusedArgs a) {
     fft32<true>(z);
     double* o0 = a.out + (size_t)b * 32768 + (i1 * 32 + 2 * qq) * 32;
     const float* l0 = a.lossf + (size_t)b * 32768 + (i1 * 32 + 2 * qq) * 32;
-#pragma unroll 4
+#pragma unroll
     for (int i3 = 0; i3 < 32; ++i3) {  // out = L+ + loss, summed in FP32
       o0[i3] = (double)(z[i3].x + l0[i3]);
       o0[32 + i3] = (double)(z[i3].y + l0[32 + i3]);
