@@ -218,6 +218,24 @@ typedef struct {
                              to the discrete collision operator's
                              conservation, and needs no collision operator
                              per Krylov iteration                         */
+  int inner_solver;       /* SLAB, preconditioner not NONE.  0: restarted
+                             flexible GMRES (default); 1: the source
+                             iteration of Sec. 5.2 (the paper's inner
+                             solver): S g_{l+1} = (nu_j/Kn + L_j/Kn) g_l + r
+                             with S the upwind transport plus nu_j/Kn,
+                             i.e. g += P(rhs - A g) with P the sweep of
+                             Eq. (5.7) (plus the coarse or learned
+                             correction when selected), from g = 0 until
+                             |rhs - A g| <= max(rtol |rhs|, atol) or
+                             krylov_maxit iterations; krylov_iterations
+                             counts them.  It converges only when
+                             nu_j + L_j is positive (see nu_scale)         */
+  double nu_scale;        /* nu_j = nu_scale * rho_j in the sweep, Eq. (5.7);
+                             0 means 1, the paper's choice.  The positivity
+                             condition on nu_j + L_j asks for nu_j at least
+                             the largest loss frequency of the cell, which
+                             for hard spheres exceeds rho_j (source
+                             iteration then needs nu_scale ~ 2)            */
 } lbo_problem;
 
 typedef struct {

@@ -24,8 +24,14 @@ condition dx h^3 sum f = C, Eq. (5.3), is imposed inside the solve
 is solved with right-hand side R + e (m(f) - C), which gives A g = R and
 m(f - g) = C whenever R has zero mass.
 The inner solve uses scipy's GMRES (a library routine) on the exact
-operator; the paper's own inner solver is the source iteration, Eq. (5.7),
-whose upwind sweep is ``sweep`` below.
+operator, or the paper's own inner solver, the source iteration (Eq. (5.7)
+and the supplement's fully discrete form): with S the operator the upwind
+sweep inverts (transport with zero incoming ghost values plus nu_j/Kn),
+  S g^{l+1} = (S - A) g^l + rhs,  g^0 = 0,
+which for A = transport - L/Kn is the printed update
+S g^{l+1} = (nu_j g^l + L_j[g^l])/Kn + r.  (Reading: the wall's and the
+border's couplings of g, which S leaves out, enter through (S - A) g^l,
+one iteration behind; the fixed point is the solution of A g = rhs.)
 """
 import numpy as np
 
@@ -163,6 +169,27 @@ class Slab:
             z[j][zero] = r[j][zero] / (nu[j] / self.kn + shift)
         return z
 
+    def sweep_operator(self, z, nu, shift=0.0):
+        """The operator ``sweep`` inverts: (v1^+ D^- + v1^- D^+ + nu_j/Kn + shift) z
+        with zero ghost values."""
+        zero = np.zeros((1,) + z.shape[1:])
+        ext = np.concatenate([zero, z, zero], axis=0)
+        tr = (self.vp * (ext[1:-1] - ext[:-2]) + self.vm * (ext[2:] - ext[1:-1])) / self.dx
+        return tr + (np.asarray(nu)[:, None, None, None] / self.kn + shift) * z
+
+    def source_iteration(self, A, rhs, nu, shift=0.0, rtol=1e-10, atol=0.0, maxiter=5000):
+        """Solve A g = rhs by the source iteration S g^{l+1} = (S - A) g^l + rhs
+        from g^0 = 0, S = sweep_operator (shift included in both S and A by
+        the caller's A).  Stops at |rhs - A g| <= max(rtol |rhs|, atol).
+        Returns (g, iterations, converged)."""
+        g = np.zeros_like(rhs)
+        target = max(rtol * self.norm(rhs), atol)
+        for it in range(1, maxiter + 1):
+            g = self.sweep(self.sweep_operator(g, nu, shift) - A(g) + rhs, nu, shift)
+            if self.norm(rhs - A(g)) <= target:
+                return g, it, True
+        return g, maxiter, False
+
     def bordered_operator(self, params, f, jacobian="local_maxwellian"):
         """A'(g) = A g + e m(g) with e = f / m(f)."""
         A = self.exact_jacobian(f) if jacobian == "exact" else self.linear_operator(params)
@@ -173,14 +200,17 @@ class Slab:
         return apply
 
     def newton_step(self, f, total_mass, rtol=1e-10, restart=60, maxiter=400, shift=0.0,
-                    jacobian="local_maxwellian"):
+                    jacobian="local_maxwellian", inner="gmres", nu_scale=1.0):
         """One modified Newton step: returns (f_new, g, |R(f)|).  GMRES on the
         bordered operator, preconditioned by the upwind sweep with
         nu_j = rho_j (Eq. (5.7)).  shift > 0 solves (A + shift I) g = R
         instead: one step of pseudo-transient continuation with
         dtau = 1/shift (a library extension; the paper's step has shift 0).
         jacobian="exact" uses exact_jacobian in place of the local-Maxwellian
-        L_j (full Newton; also a library extension)."""
+        L_j (full Newton; also a library extension).  inner="source_iteration"
+        solves the same system with the paper's source iteration instead
+        (maxiter then caps its iterations); the sweep takes
+        nu_j = nu_scale rho_j."""
         from scipy.sparse.linalg import LinearOperator, gmres
         R = self.residual(f)
         params = self.local_params(f)
@@ -195,10 +225,14 @@ class Slab:
         if shift:
             A0 = A
             A = lambda g: A0(g) + shift * g  # noqa: E731
+        if inner == "source_iteration":
+            g, _, _ = self.source_iteration(A, rhs, nu_scale * params[:, 0], shift, rtol=rtol, maxiter=maxiter)
+            return f - g, g, self.norm(R)
         shape = f.shape
         n = R.size
         op = LinearOperator((n, n), matvec=lambda x: A(x.reshape(shape)).ravel(), dtype=np.float64)
-        pre = LinearOperator((n, n), matvec=lambda x: self.sweep(x.reshape(shape), params[:, 0], shift).ravel(),
+        pre = LinearOperator((n, n), matvec=lambda x: self.sweep(x.reshape(shape), nu_scale * params[:, 0],
+                                                                 shift).ravel(),
                              dtype=np.float64)
         x, info = gmres(op, rhs.ravel(), rtol=rtol, atol=0.0, restart=restart, maxiter=maxiter, M=pre)
         g = x.reshape(shape)

@@ -72,6 +72,11 @@ __global__ void k_sub_combination(double* __restrict__ y, const double* __restri
 }
 
 // y = a x + b y  (a, b on the host)
+__global__ void k_scale(double* y, double a, size_t len) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+    y[e] *= a;
+}
+
 __global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b, size_t len) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
     y[e] = a * x[e] + b * y[e];
@@ -474,6 +479,55 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
   return LBO_OK;
 }
 
+// Source iteration (Sec. 5.2 and the supplement's discrete form): with S the
+// operator of the upwind sweep, S g_{l+1} = (S - A) g_l + rhs from g_0 = 0,
+// i.e. the Richardson iteration g += P(rhs - A g) with P the preconditioner
+// (the sweep; with MOMENT or LEARNED also their corrections).  One operator
+// and one preconditioner application per iteration, like an FGMRES step
+// without the orthogonalisation; the FP64 residual decides convergence.
+lbo_status source_iteration(lbo_solver* S, lbo_newton_stats* ns) {
+  const size_t len = S->len;
+  cudaStream_t s = S->plan->stream;
+  lbo_status st;
+  cudaMemsetAsync(S->x, 0, sizeof(double) * len, s);
+  const double rhs_norm = norm2(S, S->rhs, &st);
+  if (st != LBO_OK) return st;
+  ns->rhs_norm = rhs_norm * std::sqrt(S->wnorm);
+  const double tol = std::fmax(S->pb.krylov_rtol * rhs_norm, S->pb.krylov_atol / std::sqrt(S->wnorm));
+  ns->krylov_iterations = 0;
+  ns->restarts = 0;
+  ns->status = LBO_OK;
+  S->force_sweep = false;
+  if (rhs_norm == 0.0) return LBO_OK;
+  if (!std::isfinite(rhs_norm)) {
+    ns->status = LBO_ENAN;
+    return LBO_ENAN;
+  }
+  double* r = S->V;  // the residual rhs - A g, first rhs itself
+  cudaMemcpyAsync(r, S->rhs, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+  for (;;) {
+    st = apply_precond(S, r, S->Z);
+    if (st != LBO_OK) return st;
+    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(len), 256, 0, S->x, S->Z, 1.0, 1.0, len);
+    ns->krylov_iterations++;
+    st = apply_op(S, S->x, S->w);
+    if (st != LBO_OK) return st;
+    cudaMemcpyAsync(r, S->rhs, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(len), 256, 0, r, S->w, -1.0, 1.0, len);
+    const double rn = norm2(S, r, &st);
+    if (st != LBO_OK) return st;
+    if (!std::isfinite(rn)) {
+      ns->status = LBO_ENAN;
+      return LBO_ENAN;
+    }
+    if (rn <= tol) return LBO_OK;
+    if (ns->krylov_iterations >= S->pb.krylov_maxit) {
+      ns->status = LBO_ENOTCONV;
+      return LBO_OK;
+    }
+  }
+}
+
 }  // namespace
 
 double solver_norm2(lbo_solver* S, const double* y, lbo_status* st) { return norm2(S, y, st); }
@@ -591,6 +645,9 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
   if (pb->line_search < 0 || pb->line_search > 60 || !(pb->pseudo_dt >= 0)) return LBO_EINVAL;
   if (pb->jacobian < 0 || pb->jacobian > 1) return LBO_EINVAL;
   if (pb->coarse_operator < 0 || pb->coarse_operator > 1) return LBO_EINVAL;
+  if (pb->inner_solver < 0 || pb->inner_solver > 1 || !(pb->nu_scale >= 0) || !std::isfinite(pb->nu_scale))
+    return LBO_EINVAL;
+  if (pb->inner_solver == 1 && (pb->kind != LBO_PROBLEM_SLAB || pb->precond == LBO_PRECOND_NONE)) return LBO_EINVAL;
   lbo_solver* S = new lbo_solver();
   S->pb = *pb;
   S->plan = plan;
@@ -660,6 +717,9 @@ lbo_status lbo_solver_create_mixed(const lbo_problem* pb, lbo_plan* const* plans
   if (pb->precond != LBO_PRECOND_NONE && pb->precond != LBO_PRECOND_SWEEP) return LBO_EUNSUPPORTED;
   if (pb->line_search < 0 || pb->line_search > 60 || !(pb->pseudo_dt >= 0)) return LBO_EINVAL;
   if (pb->jacobian < 0 || pb->jacobian > 1) return LBO_EINVAL;
+  if (pb->inner_solver < 0 || pb->inner_solver > 1 || !(pb->nu_scale >= 0) || !std::isfinite(pb->nu_scale))
+    return LBO_EINVAL;
+  if (pb->inner_solver == 1 && pb->precond == LBO_PRECOND_NONE) return LBO_EINVAL;
   int nmax = 0;
   for (int p = 0; p < nplans; ++p) {
     if (!plans[p] || plans[p]->L != plans[0]->L || plans[p]->N > 64) return LBO_EINVAL;
@@ -722,6 +782,8 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
   // local Maxwellians (FP64 moments) and the nonlinear residual
   if (S->mixed) mixed_moments(S, f, S->params, S->nu);
   else LBO_LAUNCH(S->plan, "solver_moments", s, k_cell_moments, S->nx, 512, 0, f, S->params, S->nu, S->N, S->h);
+  if (S->pb.nu_scale > 0 && S->pb.nu_scale != 1.0)  // nu_j = nu_scale rho_j in the sweep
+    LBO_LAUNCH(S->plan, "solver_scale", s, k_scale, grid_for(S->nx), 256, 0, S->nu, S->pb.nu_scale, (size_t)S->nx);
   double rn = 0;
   lbo_status st = residual(S, f, f_prev, S->rhs, &rn);
   cudaEventRecord(t1, s);
@@ -754,7 +816,7 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
       st = coarse_assemble(S, bordered(S));
       if (st == LBO_OK && !coarse_valid(S)) ns->fallbacks++;  // singular: sweep alone
     }
-    if (st == LBO_OK) st = fgmres(S, ns);
+    if (st == LBO_OK) st = S->pb.inner_solver == 1 ? source_iteration(S, ns) : fgmres(S, ns);
     if (st == LBO_OK || st == LBO_ENOTCONV) {
       // FP64 true residual of the linear system
       lbo_status st2 = apply_op(S, S->x, S->w);

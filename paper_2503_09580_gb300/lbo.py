@@ -47,7 +47,8 @@ class Problem(ctypes.Structure):
                 ("bc_left", ctypes.c_int), ("bc_right", ctypes.c_int), ("inflow_left", ctypes.c_double * 5),
                 ("inflow_right", ctypes.c_double * 5), ("line_search", ctypes.c_int),
                 ("pseudo_dt", ctypes.c_double), ("coarse_moments", ctypes.c_int),
-                ("jacobian", ctypes.c_int), ("coarse_operator", ctypes.c_int)]
+                ("jacobian", ctypes.c_int), ("coarse_operator", ctypes.c_int), ("inner_solver", ctypes.c_int),
+                ("nu_scale", ctypes.c_double)]
 
 
 class NewtonStats(ctypes.Structure):
@@ -290,14 +291,17 @@ class Plan:
 
 
 class Solver:
-    """lbo_solver: modified Newton with flexible GMRES on a plan."""
+    """lbo_solver: Newton steps whose linear systems are solved by flexible
+    GMRES (inner="fgmres") or the paper's source iteration
+    (inner="source_iteration"); nu_scale sets nu_j = nu_scale rho_j in the
+    sweep of Eq. (5.7)."""
 
     def __init__(self, plan, kind="slab", nx=1, x_left=-0.5, x_right=0.5, kn=1.0,
                  wall_left=(1.0, 0.0, 0.0, 0.0), wall_right=(1.0, 0.0, 0.0, 0.0), total_mass=1.0,
                  wall_flux="analytic", dt=0.0, krylov_rtol=1e-3, krylov_atol=1e-7, krylov_restart=30,
                  krylov_maxit=300, precond="sweep", inflow_left=None, inflow_right=None, line_search=0,
                  pseudo_dt=0.0, coarse_moments=5, jacobian="local_maxwellian",
-                 coarse_operator="galerkin", _mixed=None):
+                 coarse_operator="galerkin", inner="fgmres", nu_scale=1.0, _mixed=None):
         lib = load()
         pb = Problem()
         pb.kind = PROBLEM[kind]
@@ -323,6 +327,8 @@ class Solver:
         pb.coarse_moments = int(coarse_moments)
         pb.jacobian = {"local_maxwellian": 0, "exact": 1}[jacobian]
         pb.coarse_operator = {"galerkin": 0, "transport": 1}[coarse_operator]
+        pb.inner_solver = {"fgmres": 0, "source_iteration": 1}[inner]
+        pb.nu_scale = float(nu_scale)
         h = ctypes.c_void_p()
         if _mixed is None:
             _check(lib.lbo_solver_create(ctypes.byref(pb), plan._h, ctypes.byref(h)), "lbo_solver_create")

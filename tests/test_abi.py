@@ -64,3 +64,24 @@ def test_binding_marshals_profile_and_noalloc_calls(lib):
     assert lib.lbo_apply_linearized_noalloc(None, None, None, None, 1) == 1
     assert lib.lbo_noalloc_scratch_bytes() == 64 << 20
     plan._h = None
+
+
+@pytest.mark.parametrize("cname,pystruct", [("lbo_problem", lbo.Problem), ("lbo_newton_stats", lbo.NewtonStats)])
+def test_binding_structs_match_the_header_layout(cname, pystruct, tmp_path):
+    """Every field of the ctypes mirrors sits at the offset the C compiler
+    gives it in include/lbo.h, and the sizes agree."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = [n for n, _ in pystruct._fields_]
+    body = "".join('  printf("%%zu\\n", offsetof(%s, %s));\n' % (cname, n) for n in names)
+    src = ("#include <stdio.h>\n#include <stddef.h>\n#include \"lbo.h\"\nint main(void) {\n"
+           '  printf("%%zu\\n", sizeof(%s));\n%s  return 0;\n}\n' % (cname, body))
+    (tmp_path / "layout.c").write_text(src)
+    exe = str(tmp_path / "layout")
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(tmp_path / "layout.c"), "-o", exe])
+    got = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert got[0] == ctypes.sizeof(pystruct)
+    assert got[1:] == [getattr(pystruct, n).offset for n in names]

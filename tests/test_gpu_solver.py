@@ -408,3 +408,29 @@ def test_exact_newton_with_fp32_jacobian_reaches_fp64_residual():
         ex.close()
     assert final["mixed"] < 1e-12
     assert final["fp32"] > 1e-9
+
+
+@pytest.mark.parametrize("omega,nu_scale", [(1.0, 1.0), (0.5, 2.0)])
+def test_source_iteration_step_matches_oracle(omega, nu_scale):
+    """The paper's inner solver on the GPU: one Newton step whose system is
+    solved by the source iteration (sweep of Eq. (5.7) with
+    nu_j = nu_scale rho_j; hard spheres need nu_scale ~ 2 for the positivity
+    of nu_j + L_j) equals the oracle's step, solved by GMRES on the same
+    bordered system, to the solver tolerance."""
+    n, L, nx, kn = 16, 5.5, 4, 2.0
+    oracle = Slab(n, L, omega, n, nx=nx, kn=kn, hemisphere=hemisphere_rule(2))
+    plan = lbo.Plan(n, L, omega, n, hemisphere_p=2)
+    f0 = initial_state(oracle)
+    C = oracle.mass(f0)
+    solver = plan.solver(kind="slab", nx=nx, kn=kn, wall_left=(1.0, 0, 0, 0), wall_right=(2.0, 0, 0, 0),
+                         total_mass=C, krylov_rtol=1e-10, krylov_atol=0.0, krylov_maxit=2000, precond="sweep",
+                         inner="source_iteration", nu_scale=nu_scale)
+    f_ref, g_ref, rn_ref = oracle.newton_step(f0.copy(), C, rtol=1e-11)
+    tf = torch.from_numpy(f0.copy()).to(DEV)
+    st = solver.newton_step(tf)
+    g = f0 - tf.cpu().numpy()
+    print("source iteration:", omega, nu_scale, st["krylov_iterations"], st["linear_residual"] / st["rhs_norm"])
+    assert st["converged_inner"]
+    assert abs(st["residual_norm"] - rn_ref) <= 1e-12 * rn_ref
+    assert st["linear_residual"] <= 1e-9 * st["rhs_norm"]
+    assert np.abs(g - g_ref).max() <= 1e-7 * np.abs(g_ref).max()

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle.quadrature import hemisphere_rule
-from oracle.steady import Slab
+from oracle.steady import Slab, initial_state
 
 pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
 
@@ -137,3 +137,81 @@ def test_exact_jacobian_at_a_maxwellian_approaches_the_linearized_operator():
         errs.append(np.abs(ex - lin).max() / np.abs(lin).max())
     assert 1e-4 < errs[0] < 5e-3
     assert abs(errs[0] - errs[1]) < 0.05 * errs[0]
+
+
+def _wall_slab(kn):
+    S = Slab(8, 5.0, 1.0, 4, nx=4, kn=kn, hemisphere=hemisphere_rule(1), wall_flux="discrete",
+             wall_left=(1.0, 0.0, 0.0, 0.0), wall_right=(1.6, 0.0, 0.0, 0.0))
+    a = (np.arange(8) - 4) * S.h
+    f = np.stack([_maxwell(a, (1.0, 0.05 * j, 0.0, 0.0, 1.0 + 0.15 * j)) for j in range(4)])
+    return S, f
+
+
+def test_source_iteration_is_the_printed_update():
+    """The supplement's update S g^{l+1} = (nu_j g^l + L_j[g^l])/Kn + r, with
+    the wall and border couplings of g^l added to the right-hand side, equals
+    the oracle's S g^{l+1} = (S - A) g^l + rhs and the sweep-preconditioned
+    Richardson step g^l + sweep(rhs - A g^l), iterate by iterate."""
+    S, f = _wall_slab(0.5)
+    params = S.local_params(f)
+    nu = params[:, 0]
+    A = S.bordered_operator(params, f)
+    L = S.linear_operator(params)
+    e = f / S.mass(f)
+    rng = np.random.default_rng(11)
+    rhs = rng.standard_normal(f.shape) * f
+    g = np.zeros_like(f)
+    for _ in range(4):
+        # printed form: collision part from L_j itself, transport part from
+        # the ghost cells that S (zero ghosts) leaves out
+        # L_j[g]/Kn = transport(g) - L(g) for the oracle's L(g) = transport(g) - L_j[g]/Kn
+        coll = nu[:, None, None, None] * g / S.kn + (S.transport(g, linear=True) - L(g))
+        ghost = S.transport(g, linear=True) - (S.sweep_operator(g, nu) - (nu[:, None, None, None] / S.kn) * g)
+        printed = S.sweep(coll - ghost - e * S.mass(g) + rhs, nu)
+        oracle_form = S.sweep(S.sweep_operator(g, nu) - A(g) + rhs, nu)
+        richardson = g + S.sweep(rhs - A(g), nu)
+        scale = np.abs(printed).max()
+        assert np.abs(oracle_form - printed).max() <= 1e-12 * scale
+        assert np.abs(richardson - printed).max() <= 1e-12 * scale
+        g = printed
+
+
+def _newton_system(kn, omega):
+    """The bordered Newton system of the first step on a 4-cell wall slab at
+    N = 16 (walls theta 1 and 2, the oracle's initial state)."""
+    S = Slab(16, 5.5, omega, 16, nx=4, kn=kn, hemisphere=hemisphere_rule(1))
+    f = initial_state(S)
+    params = S.local_params(f)
+    A = S.bordered_operator(params, f)
+    rhs = S.residual(f)  # the initial state has the target mass: no border source
+    return S, A, rhs, params[:, 0]
+
+
+def test_source_iteration_converges_faster_at_large_kn():
+    """Maxwell molecules: the source iteration reaches the solution of the
+    bordered system (|rhs - A g| <= 1e-8 |rhs| with the oracle's own A), and
+    it needs more iterations at the smaller Knudsen number, as Sec. 5.3
+    reports for the Couette flow."""
+    its = {}
+    for kn in (0.2, 2.0):
+        S, A, rhs, rho = _newton_system(kn, 1.0)
+        g, it, ok = S.source_iteration(A, rhs, rho, rtol=1e-8, maxiter=400)
+        assert ok, (kn, it)
+        assert S.norm(rhs - A(g)) <= 1e-8 * S.norm(rhs)
+        its[kn] = it
+    assert its[0.2] > 1.5 * its[2.0], its
+
+
+def test_hard_sphere_source_iteration_needs_the_positivity_condition():
+    """Sec. 5.2 asks nu_j + L_j to be positive.  For hard spheres the loss
+    frequency grows with |v| beyond rho_j, so nu_j = rho_j (the paper's
+    practical choice) lets the iteration grow, while nu_j = 2 rho_j
+    converges."""
+    S, A, rhs, rho = _newton_system(2.0, 0.5)
+    r0 = S.norm(rhs)
+    g = np.zeros_like(rhs)
+    for _ in range(20):
+        g = g + S.sweep(rhs - A(g), rho)
+    assert S.norm(rhs - A(g)) > r0
+    g2, it, ok = S.source_iteration(A, rhs, 2.0 * rho, rtol=1e-6, maxiter=200)
+    assert ok, it
