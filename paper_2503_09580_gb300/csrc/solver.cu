@@ -805,13 +805,18 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
       // bordered system: e = f / m(f), rhs = R + e (m(f) - C)
       wall_mass(S, f);
       double mf = 0;
-      cudaMemcpyAsync(&mf, S->res + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
-      cudaStreamSynchronize(s);
-      LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, S->evec, f, 1.0 / mf, 0.0, S->len);
-      LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, S->rhs, S->evec,
-                 mf - S->pb.total_mass, 1.0, S->len);
+      cudaError_t e = cudaMemcpyAsync(&mf, S->res + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "newton step: mass of the state");
+      } else {
+        LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, S->evec, f, 1.0 / mf, 0.0,
+                   S->len);
+        LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, S->rhs, S->evec,
+                   mf - S->pb.total_mass, 1.0, S->len);
+      }
     }
-    if (S->pb.kind == LBO_PROBLEM_SLAB && S->pb.precond == LBO_PRECOND_MOMENT) {
+    if (st == LBO_OK && S->pb.kind == LBO_PROBLEM_SLAB && S->pb.precond == LBO_PRECOND_MOMENT) {
       // coarse operator about this step's cell parameters (and shift)
       st = coarse_assemble(S, bordered(S));
       if (st == LBO_OK && !coarse_valid(S)) ns->fallbacks++;  // singular: sweep alone
