@@ -40,7 +40,6 @@ namespace lbo {
 namespace {
 
 constexpr int CT = 256;   // threads per cell block
-constexpr int NBMAX = 13;
 
 struct CoarseState {
   int nx = 0, nb = 5, nc = 0;
@@ -277,7 +276,6 @@ lbo_status coarse_assemble(lbo_solver* S, bool border) {
   lbo_status st = ensure(S);
   if (st != LBO_OK) return st;
   CoarseState* C = state(S);
-  cudaStream_t s = S->plan->stream;
   const int nx = S->nx, nc = C->nc, nb = C->nb;
   C->ab.assign((size_t)nc * C->bw, 0.0);
   C->pc.assign(nc, 0.0);

@@ -82,14 +82,6 @@ __global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, do
     y[e] = a * x[e] + b * y[e];
 }
 
-// y = x * (num / *den)  (scalar on the device)
-__global__ void k_scale_by(double* __restrict__ y, const double* __restrict__ x, double num,
-                           const double* __restrict__ den, size_t len) {
-  const double s = num / *den;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
-    y[e] = x[e] * s;
-}
-
 // local Maxwellian parameters of each cell: rho, u, theta (Sec. 2.1), FP64
 __global__ void __launch_bounds__(512) k_cell_moments(const double* __restrict__ f, double* __restrict__ params,
                                                      double* __restrict__ nu, int N, double h) {
@@ -385,7 +377,7 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
   const bool learned = S->pb.precond == LBO_PRECOND_LEARNED;
   const int learned_budget = S->pb.krylov_maxit / 2;
   while (!done) {
-    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(len), 256, 0, S->V, S->V, 1.0 / beta, 0.0, len);
+    LBO_LAUNCH(S->plan, "solver_scale", s, k_scale, grid_for(len), 256, 0, S->V, 1.0 / beta, len);
     std::fill(gam.begin(), gam.end(), 0.0);
     gam[0] = beta;
     int k = 0;
