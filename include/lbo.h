@@ -242,7 +242,7 @@ typedef struct {
   double residual_norm;    /* |R(f)| (or |F(f)|) at the input state             */
   double rhs_norm;         /* |right-hand side of the linear system|            */
   double linear_residual;  /* FP64 true |rhs - A g| after the solve             */
-  int krylov_iterations;
+  int krylov_iterations;   /* inner iterations: FGMRES steps or source iterations */
   int restarts;
   int fallbacks;           /* 1 if the learned preconditioner was replaced by the
                               plain sweep after half of krylov_maxit iterations,
@@ -288,8 +288,9 @@ lbo_status lbo_solver_residual(lbo_solver *solver, const double *f, const double
  * truncation to a coarser one, the Nyquist term of the coarser grid a
  * cosine).  Supported: SLAB with inflow sides at both ends (LBO_EUNSUPPORTED
  * otherwise), preconditioner NONE or SWEEP (the sweep runs on the finest
- * grid), both Jacobians, continuation and line search; per-N residual plans
- * through lbo_solver_set_residual_plan (one call per N). */
+ * grid), both inner solvers (source iteration with SWEEP), both Jacobians,
+ * continuation and line search; per-N residual plans through
+ * lbo_solver_set_residual_plan (one call per N). */
 lbo_status lbo_solver_create_mixed(const lbo_problem *problem, lbo_plan *const *plans, int nplans,
                                    const int *cell_plan, lbo_solver **out);
 size_t lbo_solver_state_length(const lbo_solver *solver);
