@@ -356,9 +356,13 @@ int lbo_solver_network_param_count(lbo_solver *solver, int hidden);
  * instead of plan-owned memory, and it calls no allocating routine.
  * - Rejects (LBO_EINVAL, nothing launched) a batch needing more than
  *   lbo_noalloc_scratch_bytes(), i.e. batch * lbo_noalloc_bytes_per_instance
- *   (1.62 MB per instance at N = 32 in FP64, 0.81 MB in FP32), host
- *   pointers, and a plan whose tables are out of date; LBO_EUNSUPPORTED with
- *   the mass or moment fix options on.
+ *   (1,661,320 bytes = 1.66 MB per instance at N = 32 in FP64, half that in
+ *   FP32: at most 40 and 80 instances), host pointers, a call made while
+ *   another device than the plan's is current, and a plan whose tables are
+ *   out of date; LBO_EUNSUPPORTED with the mass or moment fix options on or
+ *   a precision other than FP64 and FP32.
+ * - It always runs the generic kernel set (LBO_OPT_KERNEL = 1), also where
+ *   lbo_apply_linearized would pick the fused FP32 kernels.
  * - All calls share the array: calls that overlap on the GPU race and must
  *   be serialised.  Nothing in it needs to start at zero.
  * - The first call on a device (with that device current) looks up the

@@ -165,18 +165,33 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_head(FusedArgs a) {
   // itself is formed in FP32 (it is rounded to FP32 for the transform
   // anyway).  A point that passes the cut has (a_1 + a_2) / (2 theta) below
   // the threshold, so its partial product stays finite; a cut point is
-  // selected, never multiplied.
-  rows_forward(V, [&](int i1, int qq, int i3) {
-    float v[2];
+  // selected, never multiplied.  Without the cut-off the factors 1/M of the
+  // outer points exceed the FP32 range (exp(|v-u|^2/(2 theta)) reaches
+  // 1e94 on the box), so the ratio is then formed in FP64 and only r is
+  // rounded to FP32.
+  if (cut) {
+    rows_forward(V, [&](int i1, int qq, int i3) {
+      float v[2];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int i2 = 2 * qq + r;
-      const double d2 = __dadd_rn(__dadd_rn(T.a[i1], T.a[32 + i2]), T.a[64 + i3]);
-      const float val = (float)gb[(i1 * 32 + i2) * 32 + i3] * ((T.eif[i1] * T.eif[32 + i2]) * T.eif[64 + i3]);
-      v[r] = (cut && d2 >= T.dstar) ? 0.f : val;
-    }
-    return make_c(v[0], v[1]);
-  });
+      for (int r = 0; r < 2; ++r) {
+        const int i2 = 2 * qq + r;
+        const double d2 = __dadd_rn(__dadd_rn(T.a[i1], T.a[32 + i2]), T.a[64 + i3]);
+        const float val = (float)gb[(i1 * 32 + i2) * 32 + i3] * ((T.eif[i1] * T.eif[32 + i2]) * T.eif[64 + i3]);
+        v[r] = d2 >= T.dstar ? 0.f : val;
+      }
+      return make_c(v[0], v[1]);
+    });
+  } else {
+    rows_forward(V, [&](int i1, int qq, int i3) {
+      float v[2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int i2 = 2 * qq + r;
+        v[r] = (float)(gb[(i1 * 32 + i2) * 32 + i3] * ((T.ei[i1] * T.ei[32 + i2]) * T.ei[64 + i3]));
+      }
+      return make_c(v[0], v[1]);
+    });
+  }
   const int i2 = t / F_HC, k3 = t % F_HC;
   cpx<float>* base = V + srow(i2) + k3;
   cpx<float> x[32];

@@ -27,11 +27,11 @@ struct NetState {
   int hidden = 0;
   int max_pairs = 0, pairs = 0;
   bool collecting = false;
-  float* store_x = nullptr;  // [max_pairs][nx][10] raw features
+  float* store_x = nullptr;  // [max_pairs][nx][26] raw features (13 moments of v and of its sweep)
   float* store_t = nullptr;  // [max_pairs][nx][5] raw targets
   float* theta = nullptr;    // device parameters
   float scales[31] = {};  // cs_in[26], cs_out[5]
-  float* feat = nullptr;     // [nx][10] features of the vector being preconditioned
+  float* feat = nullptr;     // [nx][26] features of the vector being preconditioned
   float* corr = nullptr;     // [nx][5]
   bool trained = false;
 };

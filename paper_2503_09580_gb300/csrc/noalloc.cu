@@ -25,6 +25,12 @@
 //  * The first call on a device, with that device current, looks up the
 //    array's device address (cudaGetSymbolAddress) and uploads this file's
 //    FFT twiddle table; make that first call before any stream capture.
+//  * It always runs the generic plane/axis kernel set (the one
+//    LBO_OPT_KERNEL = 1 selects), also where the regular entry point would
+//    pick the fused FP32 kernels (N = 32), and only the FP64 and FP32
+//    precisions.
+//  * The device current at the call must be the plan's device (the plan's
+//    tables live there); other devices are rejected.
 //  * Arrays must be device pointers; the plan's tables must be current
 //    (a plan whose R, C or hemisphere option changed since its last
 //    lbo_apply_linearized call is rejected, since rebuilding the tables
@@ -32,6 +38,7 @@
 //    library routine.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "lbo_internal.h"
 #include "lin_kernels.cuh"
@@ -47,6 +54,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 void* g_scratch_ptr[kMaxDevices] = {};  // device address of the array, per device
 bool g_ready[kMaxDevices] = {};
+std::mutex g_setup_mutex;  // two host threads making their first call at once
 
 // Per-device set-up: the array's address and this file's twiddle table.
 lbo_status setup_device(int dev) {
@@ -54,6 +62,7 @@ lbo_status setup_device(int dev) {
     set_error_text("noalloc: device index out of range");
     return LBO_EINVAL;
   }
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (g_ready[dev]) return LBO_OK;
   void* ptr = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -188,10 +197,17 @@ size_t lbo_noalloc_bytes_per_instance(const lbo_plan* p) {
 lbo_status lbo_apply_linearized_noalloc(lbo_plan* p, const double* params, const double* g, double* out,
                                         int batch) {
   if (!p || batch < 0) return LBO_EINVAL;
-  if (batch == 0) return LBO_OK;
+  if (batch == 0) {
+    p->last_launches = 0;
+    return LBO_OK;
+  }
   if (!params || !g || !out || out == g) return LBO_EINVAL;
   if (p->mass_fix || p->moment_fix) {
     lbo::set_error_text("noalloc: mass/moment fix options are not supported by this entry point");
+    return LBO_EUNSUPPORTED;
+  }
+  if (p->precision != LBO_PREC_FP64 && p->precision != LBO_PREC_FP32) {
+    lbo::set_error_text("noalloc: only the FP64 and FP32 precisions are supported by this entry point");
     return LBO_EUNSUPPORTED;
   }
   if (p->tables_dirty) {
@@ -213,11 +229,18 @@ lbo_status lbo_apply_linearized_noalloc(lbo_plan* p, const double* params, const
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return lbo::cuda_fail(e, "noalloc: cudaGetDevice");
+  if (dev != p->device) {
+    lbo::set_error_text("noalloc: the current device is not the plan's device");
+    return LBO_EINVAL;
+  }
   lbo_status st = lbo::setup_device(dev);
   if (st != LBO_OK) return st;
   unsigned char* ws = (unsigned char*)lbo::g_scratch_ptr[dev];
-  return p->precision == LBO_PREC_FP64 ? lbo::dispatch<double>(p, params, g, out, batch, ws)
-                                       : lbo::dispatch<float>(p, params, g, out, batch, ws);
+  st = p->precision == LBO_PREC_FP64 ? lbo::dispatch<double>(p, params, g, out, batch, ws)
+                                     : lbo::dispatch<float>(p, params, g, out, batch, ws);
+  // same count as the regular generic path: 2 + 4 per radial node + 9
+  p->last_launches = st == LBO_OK ? 4 * p->J + 11 : 0;
+  return st;
 }
 
 }  // extern "C"

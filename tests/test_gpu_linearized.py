@@ -155,6 +155,27 @@ def test_cutoff_off_and_eps_option():
         assert relerr(got, ref) <= 1e-12
 
 
+def test_fused_fp32_without_cutoff_stays_finite():
+    """Fused FP32 kernels with the cut-off off (noise-free g = M p, so r = p is
+    bounded although 1/M of the outer points exceeds the FP32 range): the
+    ratio is formed in FP64, the result is finite and within u32 max|r| of
+    the oracle without the cut-off."""
+    n, L = 32, 8.0
+    params, g = workloads.batched_instances(n, L, batch=2, seed=12, noise=0.0)
+    plan = lbo.Plan(n, L, 0.5, n, precision="fp32", cutoff=0)
+    got = run(plan, params, g)
+    assert np.all(np.isfinite(got))
+    ref = apply_linearized(tables(n, L, 0.5, n), params, g, cutoff=False)
+    rmax = 0.0
+    a = workloads.velocity_axis(n, L)
+    for b in range(2):
+        rho, u1, u2, u3, th = params[b]
+        d2 = (a[:, None, None] - u1) ** 2 + (a[None, :, None] - u2) ** 2 + (a[None, None, :] - u3) ** 2
+        M = rho * (2 * np.pi * th) ** -1.5 * np.exp(-d2 / (2 * th))
+        rmax = max(rmax, np.abs(g[b] / M).max())
+    assert relerr(got, ref) <= 2.0 ** -24 * rmax
+
+
 def test_fp32_rounding_bound_noise_free():
     """FP32 transforms against the FP64 oracle with the same cut-off.  The
     FFT convolution of r loses accuracy in proportion to max|r| (Sec. 3.3):

@@ -123,3 +123,44 @@ def test_fused_fp32_quadratic_n32(jgroups):
     print("fused Q fp32 vs oracle %.2e, vs generic fp32 %.2e" % (relerr(a[:1], ref), relerr(a, b)))
     assert relerr(a[:1], ref) <= 2.0 ** -24 * 64
     assert relerr(a, b) <= 2.0 ** -24 * 64
+
+
+def test_quadratic_fp64_n32_p4_matches_oracle():
+    """The hemisphere order the Newton and BKW workloads use (p = 4, M = 32
+    points) at N = 32, generic FP64 kernels, one radial node per grid point."""
+    n, L, p = 32, 8.0, 4
+    params, g = workloads.batched_instances(n, L, batch=2, seed=33, noise=0.0)
+    f = maxwell_batch(n, L, params) + 0.3 * g
+    plan = lbo.Plan(n, L, 0.5, n, hemisphere_p=p)
+    got = run_q(plan, f)
+    sig, w = hemisphere_rule(p)
+    ref = apply_quadratic(Tables(n, L, 0.5, n), f, sig, w)
+    assert relerr(got, ref) <= 1e-12
+
+
+def test_quadratic_fused_fp32_n32_p4_matches_oracle():
+    """Fused FP32 Q (the default kernels for FP32 at N = 32) at p = 4 against
+    the FP64 oracle.  Bound: 64 u32 normwise (transform rounding of the
+    2 J M + J transforms, observed ~1e-6)."""
+    n, L, p = 32, 8.0, 4
+    params, g = workloads.batched_instances(n, L, batch=2, seed=34, noise=0.0)
+    f = maxwell_batch(n, L, params) + 0.3 * g
+    plan = lbo.Plan(n, L, 0.74, n, hemisphere_p=p, precision="fp32")
+    got = run_q(plan, f)
+    sig, w = hemisphere_rule(p)
+    ref = apply_quadratic(Tables(n, L, 0.74, n), f, sig, w)
+    assert relerr(got, ref) <= 64 * 2.0 ** -24
+
+
+def test_quadratic_fp64_n64_bkw_configuration_matches_oracle():
+    """The BKW workload's operator: N = 64, J = 64, Maxwell molecules,
+    M = 32 hemisphere points, generic FP64 kernels, one instance (the numpy
+    oracle takes about a minute here)."""
+    n, L, p = 64, 8.0, 4
+    params, g = workloads.batched_instances(n, L, batch=1, seed=35, noise=0.0)
+    f = maxwell_batch(n, L, params) + 0.3 * g
+    plan = lbo.Plan(n, L, 1.0, n, hemisphere_p=p)
+    got = run_q(plan, f)
+    sig, w = hemisphere_rule(p)
+    ref = apply_quadratic(Tables(n, L, 1.0, n), f, sig, w)
+    assert relerr(got, ref) <= 1e-12

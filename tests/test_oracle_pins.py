@@ -10,7 +10,7 @@ import pytest
 
 from oracle import grid
 from oracle.direct import direct_linearized, direct_quadratic
-from oracle.linearized import Tables, collision_operator, maxwellians, sinc, default_R
+from oracle.linearized import Tables, collision_operator, cutoff_mask, maxwellians, sinc, default_R
 from oracle.moments import conservation_projection, invariant_moments, moments
 from oracle.quadratic import quadratic_operator
 from oracle.quadrature import hemisphere_rule, radial_rule, radial_rule_jgr, vhs_kernel
@@ -81,7 +81,7 @@ def test_tables_closed_forms():
 
 
 # ------------------------------------------------- FFT form vs direct sums
-@pytest.mark.parametrize("n", [8, 12])
+@pytest.mark.parametrize("n", [8, 12, 16])
 def test_algorithm1_matches_direct_sums(n):
     rng = np.random.default_rng(n)
     L = 8.0
@@ -94,10 +94,13 @@ def test_algorithm1_matches_direct_sums(n):
     assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
     # With grid noise r = f/M reaches ~noise/(eps rho) in the tails and the FFT
     # convolution loses digits in proportion (Sec. 3.3); direct sums do not.
+    # (max|r| over the points where the cut-off of Eq. (3.9) keeps r)
     f = f + 1e-4 * rng.standard_normal((n, n, n))
     a = collision_operator(tab, rho, u, th, f)
     b = direct_linearized(tab, rho, u, th, f)
-    rmax = np.abs(f / M).max()
+    _, _, _, d2 = maxwellians(n, L, rho, np.array(u), th)
+    rmax = np.abs(f / M)[~cutoff_mask(d2, th, 1e-9)].max()
+    assert 1e4 < rmax < 1e7
     assert np.abs(a - b).max() <= 1e-15 * rmax * np.abs(b).max()
 
 
