@@ -5,10 +5,16 @@ background Maxwellians rho ~ U[0.5,2], u_i ~ U[-0.5,0.5], theta ~ U[0.5,2],
 g = M * (quartic polynomial, N(0,1) coefficients) + 1e-3 N(0,1) grid noise.
 
 One step = one lbo_apply_linearized call over the whole batch (every kernel
-of the path).  Prints one JSON line (rank 0).
+of the path).  The headline value is the plain FP64 path (the paper's
+arithmetic); the FP32 form, the VHS exponents 0.5 / 0.74 / 1.0 and the
+solver and N = 64 workloads are reported beside it, each precision form
+with its measured error against the oracle and its stated bound.  The ALU
+peaks of the roofline fractions are measured in the run
+(lbo_measure_alu_peaks); the HBM peak is the machine's measured copy bandwidth.
+Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
-  python bench.py --impl reference   # the CPU oracle on the host cores
+  python bench.py --impl reference   # the CPU oracle on all host cores
 
 Multi-GPU (torchrun): each rank applies L to its own batch (instances are
 independent; no data-path collective), value = all ranks' applications /
@@ -27,18 +33,54 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "L[g] applications/sec at N=32 (batch 256, per-instance Maxwellians)"
+METRIC = "L[g] applications/sec at N=32,64 vs plain FP64 GPU path at stated rel. error"
 UNIT = "applications/s"
 N_GRID, BOX, BATCH = 32, 8.0, 256
-SM_COUNT, SM_MAX_MHZ = 152, 2070.0
-# ALU peaks derived from unit counts and the maximum SM clock:
-#   FP64: 4 flop/clk/SM (2 DFMA/clk/SM, measured by an FMA probe) x 152 SMs x 2070 MHz
-#   FP32: 256 flop/clk/SM (128 FFMA lanes) x 152 SMs x 2070 MHz
-PEAK_TFLOPS = {"fp64": 4 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12,
-               "fp32": 256 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12}
-# DRAM bytes (read + write) per launch of the dominant kernel at the benchmark
-# workload, from ncu (profiles/*.md); None when not captured for this build.
-NCU_TRAFFIC = {("plane_inv_mh_fwd", 32, "fp64"): 82483456, ("f32_gain", 32, "fp32"): 370405376}
+OMEGAS = (0.5, 0.74, 1.0)
+U64, U32 = 2.0 ** -53, 2.0 ** -24
+# The stated error bound of a precision form, per instance: the normwise
+# relative error of the FFT form of Algorithm 1 grows with the size of the
+# ratio r = g/M it transforms (Sec. 3.3); measured on the oracle's FFT form in
+# FP32 and on the GPU paths, err <= ~0.6 u rms(r) with rms(r) over the whole
+# grid (r = 0 where cut).  Stated bound: BOUND_FACTOR u rms(r).
+BOUND_FACTOR = 4.0
+HBM_FALLBACK_GBS = 6800.0
+# Kernels bound by memory traffic, not by their arithmetic (rated in GB/s).
+HBM_KERNELS = ("combine", "fixes", "f32_head", "f32_tail")
+# DRAM bytes (read + write) per launch of a dominant kernel at the benchmark
+# workload from one ncu capture, with the sha256 (first 16 hex digits) of the
+# source files it was built from; reported as null once those sources change.
+NCU_TRAFFIC = {}
+KERNEL_SOURCES = {
+    "plane_inv_mh_fwd": ("lin_kernels.cuh", "fft.cuh", "lbo.cu"),
+    "f32_gain": ("lin_fused32.cu", "fused32.cuh", "tmem.cuh"),
+}
+
+
+def sources_sha16(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(kernel, ()):
+        with open(os.path.join(ROOT, "paper_2503_09580_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, n, precision):
+    rec = NCU_TRAFFIC.get((kernel, n, precision))
+    if rec is None or kernel not in KERNEL_SOURCES or rec[1] != sources_sha16(kernel):
+        return None
+    return rec[0]
+
+
+def hbm_peak():
+    """(GB/s, source) of the copy bandwidth measured on this machine's GPUs."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (copy bandwidth of this pool's GB300s)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback (one earlier GB300 measurement)"
 
 
 def transform_axis_flops(n):
@@ -95,21 +137,73 @@ def kernel_flops_per_instance(name, n, J=None):
             + KERNEL_POINTWISE.get(name, 0) * n ** 3 + extra)
 
 
-def kernel_rooflines(prof, n, batch, peak):
-    """Per kernel: average launch time (live CUDA events) and its own
-    algorithmic rate against the pipe's peak (TFLOP/s)."""
+def kernel_bytes_per_instance(name, n, real_bytes, groups=1):
+    """Compulsory HBM bytes per instance of the memory-bound kernels: what
+    the kernel must read and write once (FP64 ABI arrays, intermediate
+    fields in the transform precision)."""
+    n3, h = n ** 3, n * n * (n // 2 + 1)
+    if name == "combine":      # L+, u, w (transform precision) and g in; out
+        return 3 * real_bytes * n3 + 16 * n3
+    if name == "fixes":        # out read and written, twice (moments, then the correction)
+        return 32 * n3
+    if name == "f32_head":     # g in (FP64); r^ out (FP32 half spectrum)
+        return 8 * n3 + 8 * h
+    if name == "f32_tail":     # G partial spectra and the FP32 loss field in; out (FP64)
+        return groups * 8 * h + 4 * n3 + 8 * n3
+    return 0
+
+
+def kernel_rooflines(prof, n, batch, peak_tflops, hbm_gbs, real_bytes, groups=1):
+    """Per kernel: average launch time (live CUDA events) and its own bound:
+    algorithmic flops against the measured ALU peak, or compulsory bytes
+    against the measured HBM bandwidth for the memory-bound kernels."""
     out = {}
     for name, (cnt, tot) in sorted(prof.items()):
         per = tot / max(cnt, 1)
-        fl = kernel_flops_per_instance(name, n) * batch
-        ach = fl / (per * 1e-3) / 1e12 if per > 0 else 0.0
-        out[name] = {"launches": cnt, "ms_per_launch": per, "achieved_tflops": ach, "frac": ach / peak}
+        rec = {"launches": cnt, "ms_per_launch": per}
+        if name in HBM_KERNELS:
+            by = kernel_bytes_per_instance(name, n, real_bytes, groups) * batch
+            ach = by / (per * 1e-3) / 1e9 if per > 0 else 0.0
+            rec.update({"bound": "hbm", "achieved_gbs": ach, "frac": ach / hbm_gbs})
+        else:
+            fl = kernel_flops_per_instance(name, n) * batch
+            ach = fl / (per * 1e-3) / 1e12 if per > 0 else 0.0
+            rec.update({"bound": "alu", "achieved_tflops": ach, "frac": ach / peak_tflops})
+        out[name] = rec
     return out
 
 
 def apply_flops_per_instance(n, J):
     """(3J + 6) real 3-D transforms of n^3 points at 2.5 n^3 log2(n^3) flops."""
     return (3 * J + 6) * 3 * transform_axis_flops(n)
+
+
+def ratio_rms(params, g, n, L, eps=1e-9):
+    """Per instance: rms over the grid of r = g/M, 0 where the cut-off of
+    Eq. (3.9) applies -- the size of what the FFT form transforms."""
+    a = (np.arange(n) - n // 2) * (2 * L / n)
+    out = []
+    for b in range(params.shape[0]):
+        rho, u1, u2, u3, th = params[b]
+        d2 = (a[:, None, None] - u1) ** 2 + (a[None, :, None] - u2) ** 2 + (a[None, None, :] - u3) ** 2
+        M = rho * (2 * np.pi * th) ** -1.5 * np.exp(-d2 / (2 * th))
+        keep = d2 / (2 * th) <= np.log(1 / eps) - 1.5 * np.log(2 * np.pi * th)
+        r = np.where(keep, g[b] / np.where(keep, M, 1.0), 0.0)
+        out.append(float(np.sqrt(np.mean(r * r))))
+    return np.array(out)
+
+
+def error_report(got, ref, rms, unit):
+    """Measured normwise relative error per instance against the oracle and
+    the stated bound BOUND_FACTOR u rms(r) per instance."""
+    k = ref.shape[0]
+    errs = np.array([np.abs(got[b] - ref[b]).max() / np.abs(ref[b]).max() for b in range(k)])
+    bounds = BOUND_FACTOR * unit * rms[:k]
+    return {"rel_err_vs_oracle": float(errs.max()), "stated_bound": float(bounds.max()),
+            "worst_err_over_bound": float((errs / bounds).max()), "within_bound": bool(np.all(errs <= bounds)),
+            "instances": int(k),
+            "metric": "max over instances of max|gpu - oracle| / max|oracle|; bound %g u rms(r) per instance"
+                      % BOUND_FACTOR}
 
 
 class ClockSampler:
@@ -211,35 +305,192 @@ def oracle_sample(params, g, n, L, omega, seconds):
     return np.stack(outs), len(outs) / dt
 
 
+_W = {}
+
+
+def _oracle_worker_init(n, L, omega, batch, seed, noise):
+    """Pool worker: one numpy thread, the workload regenerated from its seed,
+    the oracle's tables built once."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    sys.path.insert(0, ROOT)
+    from oracle.linearized import Tables
+    from paper_2503_09580_gb300 import workloads
+    _W["params"], _W["g"] = workloads.batched_instances(n, L, batch=batch, seed=seed, noise=noise)
+    _W["tab"] = Tables(n, L, omega, n)
+
+
+def _oracle_worker_apply(b):
+    from oracle.linearized import apply_linearized
+    b = b % _W["params"].shape[0]
+    apply_linearized(_W["tab"], _W["params"][b:b + 1], _W["g"][b:b + 1])
+    return b
+
+
+class OraclePool:
+    """The oracle on every host core: a spawn-started process pool (no fork
+    after CUDA initialisation), one instance per task."""
+
+    def __init__(self, n, L, omega, batch, seed, noise):
+        import multiprocessing as mp
+        self.cores = os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init,
+                                                 initargs=(n, L, omega, batch, seed, noise))
+        self.pool.map(_oracle_worker_apply, range(self.cores), chunksize=1)  # warm every worker
+
+    def run(self, count):
+        """Apply the oracle to `count` instances (cycling through the batch)
+        on all cores; returns the wall time in seconds."""
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_worker_apply, range(count), chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def workload_config(omega, precision):
+    return {"workload": "batched L[g], N=32, batch 256 per GPU, per-instance Maxwellians "
+                        "rho~U[0.5,2], u_i~U[-0.5,0.5], theta~U[0.5,2], g = M * quartic (N(0,1) coefficients) "
+                        "+ 1e-3 N(0,1) grid noise",
+            "N": N_GRID, "box": BOX, "vhs_omega": omega, "radial_nodes": N_GRID, "batch_per_gpu": BATCH,
+            "precision": precision, "eps": 1e-9}
+
+
 def run_reference(args, world, rank):
+    """The oracle (numpy FFT form of Algorithm 1, FP64) on all host cores,
+    each step a bounded sample of the benchmark batch (one instance per
+    core)."""
     if rank != 0:
         return
-    from paper_2503_09580_gb300 import workloads
-    params, g = workloads.batched_instances(N_GRID, BOX, batch=BATCH, seed=args.seed, noise=1e-3)
-    from oracle.linearized import Tables, apply_linearized
-    tab = Tables(N_GRID, BOX, args.omega, N_GRID)
-    per_step = args.ref_instances
-    for w in range(args.warmup):
-        apply_linearized(tab, params[:1], g[:1])
-    t0 = time.perf_counter()
+    pool = OraclePool(N_GRID, BOX, args.omega, BATCH, args.seed, 1e-3)
+    per_step = pool.cores * args.ref_per_core
+    for _ in range(args.warmup):
+        pool.run(pool.cores)
+    secs = 0.0
     for k in range(args.steps):
-        s = (k * per_step) % BATCH
-        apply_linearized(tab, params[s:s + per_step], g[s:s + per_step])
-    dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
+        secs += pool.run(per_step)
+    pool.close()
+    value = per_step * args.steps / secs
+    sample = ("%d instances per step (%d per core, cycling through the batch), numpy FFT form of "
+              "Algorithm 1 in FP64, one process per core" % (per_step, args.ref_per_core))
+    cfg = workload_config(args.omega, "fp64")
+    cfg["workload"] += " (sampled %d instances per step)" % per_step
+    cfg["l2"] = "host"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": "batched L[g], N=32, batch 256 (sampled %d instances per step), "
-                               "per-instance Maxwellians, quartic polynomial + 1e-3 noise" % per_step,
-                   "N": N_GRID, "box": BOX, "vhs_omega": args.omega, "radial_nodes": N_GRID},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d instances per step, numpy FFT form of Algorithm 1" % per_step},
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def time_steps(plan, tp, tg, out, steps, stream, profile):
+    """CUDA-event time per application of the whole batch on `stream`, the
+    per-kernel event totals (profile) and the kernels launched."""
+    import torch
+    if profile:
+        plan.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(steps):
+        plan.apply_linearized(tp, tg, out)
+        launches += plan.last_launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = {}
+    if profile:
+        prof = plan.profile_read()
+        plan.profile(False)
+    return e0.elapsed_time(e1) / steps, prof, launches
+
+
+def dominant_roofline(prof, precision, peaks, hbm, hbm_src, groups=1):
+    name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    per = tot / max(cnt, 1)
+    share = tot / sum(v[1] for v in prof.values())
+    real_bytes = 8 if precision == "fp64" else 4
+    if name in HBM_KERNELS:
+        ach = kernel_bytes_per_instance(name, N_GRID, real_bytes, groups) * BATCH / (per * 1e-3) / 1e9
+        rf = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "peak_source": hbm_src}
+    else:
+        ach = kernel_flops_per_instance(name, N_GRID) * BATCH / (per * 1e-3) / 1e12
+        pk = peaks["fp64_tflops"] if precision == "fp64" else peaks["fp32_tflops"]
+        rf = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+              "peak_source": "measured in this run (lbo_measure_alu_peaks: dense %s chains, %d SMs at %.0f MHz)"
+                             % ("DFMA" if precision == "fp64" else "FFMA", peaks["sm_count"], peaks["sm_mhz"])}
+    rf.update({"frac": rf["achieved"] / rf["peak"], "traffic": ncu_traffic(name, N_GRID, precision),
+               "kernel": name, "kernel_share": share, "kernel_ms_per_launch": per,
+               "apply_flops_per_instance": apply_flops_per_instance(N_GRID, N_GRID)})
+    return rf
+
+
+def variant_leg(precision, tp, tg, tpc, tgc, stream, steps, peaks, hbm, ref, ref_clean, rms, rms_clean, k_clean):
+    """Another precision form on the same inputs: apps/s (same event timing),
+    its kernels' rooflines, and its error against the oracle with the
+    stated bound, on the noisy benchmark batch and on its noise-free twin."""
+    import torch
+    from paper_2503_09580_gb300 import lbo
+    plan = lbo.Plan(N_GRID, BOX, 0.5, N_GRID, precision=precision)
+    out = torch.empty_like(tg)
+    groups = plan.autotune(tp, tg, out) if precision == "fp32" else 0
+    for _ in range(3):
+        plan.apply_linearized(tp, tg, out)
+    torch.cuda.synchronize()
+    ms, prof, launches = time_steps(plan, tp, tg, out, steps, stream, True)
+    unit = U64 if precision == "fp64" else U32
+    real_bytes = 8 if precision == "fp64" else 4
+    peak = peaks["fp64_tflops"] if precision == "fp64" else peaks["fp32_tflops"]
+    res = {"value": BATCH / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "gpu_launches_per_step": launches // steps, "jgroups": groups or "n/a",
+           "kernel_rooflines": kernel_rooflines(prof, N_GRID, BATCH, peak, hbm, real_bytes, groups or 1)}
+    if ref is not None:
+        got = out.cpu().numpy()
+        res["accuracy_noisy"] = error_report(got, ref, rms, unit)
+        outc = torch.empty_like(tgc)
+        plan.apply_linearized(tpc, tgc, outc)
+        torch.cuda.synchronize()
+        res["accuracy_noise_free"] = error_report(outc.cpu().numpy()[:k_clean], ref_clean, rms_clean, unit)
+    plan.close()
+    return res
+
+
+def omega_sweep(tp, tg, tpc, tgc, params, g, pc, gc, stream, steps, with_oracle, k=3):
+    """The FP64 plain path at the three VHS exponents of the benchmark
+    workload: apps/s and error against the oracle (noise-free twin: 1e-12
+    bar; noisy input: stated bound), k sampled instances each."""
+    import torch
+    from paper_2503_09580_gb300 import lbo
+    from oracle.linearized import Tables, apply_linearized
+    res = {}
+    rms = ratio_rms(params[:k], g[:k], N_GRID, BOX)
+    for om in OMEGAS:
+        plan = lbo.Plan(N_GRID, BOX, om, N_GRID)
+        out = torch.empty_like(tg)
+        for _ in range(2):
+            plan.apply_linearized(tp, tg, out)
+        torch.cuda.synchronize()
+        ms, _, _ = time_steps(plan, tp, tg, out, steps, stream, False)
+        rec = {"value": BATCH / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps}
+        if with_oracle:
+            tab = Tables(N_GRID, BOX, om, N_GRID)
+            rec["accuracy_noisy"] = error_report(out.cpu().numpy()[:k], apply_linearized(tab, params[:k], g[:k]),
+                                                 rms, U64)
+            plan.apply_linearized(tpc, tgc, out)
+            torch.cuda.synchronize()
+            refc = apply_linearized(tab, pc[:k], gc[:k])
+            errc = float(max(np.abs(out.cpu().numpy()[b] - refc[b]).max() / np.abs(refc[b]).max()
+                             for b in range(k)))
+            rec["rel_err_noise_free"] = errc
+            rec["noise_free_within_1e-12"] = errc <= 1e-12
+        res["omega=%g" % om] = rec
+        plan.close()
+    return res
 
 
 def newton_leg(precision, kn, nx=128, n=32, L=8.0, residual_precision=None):
@@ -533,18 +784,20 @@ def run_ours(args, world, rank, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    prec = args.precision
     params, g = workloads.batched_instances(N_GRID, BOX, batch=BATCH, seed=args.seed + rank, noise=1e-3)
-    plan = lbo.Plan(N_GRID, BOX, args.omega, N_GRID, precision=args.precision)
+    tp, tg = torch.from_numpy(params).to(dev), torch.from_numpy(g).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    peaks = lbo.measure_alu_peaks(stream)
+    hbm, hbm_src = hbm_peak()
+    plan = lbo.Plan(N_GRID, BOX, args.omega, N_GRID, precision=prec)
     if args.eps is not None:
         plan.set("eps", args.eps)
     if args.moment_fix:
         plan.set("moment_fix", 1)
-    tp = torch.from_numpy(params).to(dev)
-    tg = torch.from_numpy(g).to(dev)
     out = torch.empty_like(tg)
-    stream = torch.cuda.current_stream(dev)
     # radial-node groups per CTA of the fused FP32 kernel, timed on this batch
-    jgroups = plan.autotune(tp, tg, out) if not args.no_autotune else 0
+    jgroups = plan.autotune(tp, tg, out) if prec == "fp32" and not args.no_autotune else 0
     for _ in range(args.warmup):
         plan.apply_linearized(tp, tg, out)
     torch.cuda.synchronize()
@@ -552,31 +805,13 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    plan.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    launches = 0
-    for _ in range(args.steps):
-        plan.apply_linearized(tp, tg, out)
-        launches += plan.last_launches
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, prof, launches = time_steps(plan, tp, tg, out, args.steps, stream, True)
     barrier(world)
-    ms = e0.elapsed_time(e1) / args.steps
-    prof = plan.profile_read()
-    plan.profile(False)
     clk = clocks.stop()
     ms_max = max_over_ranks(ms, world)
     value = world * BATCH / (ms_max * 1e-3)
-
-    # dominant kernel and its roofline
-    name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
-    per_launch_ms = tot / max(cnt, 1)
-    flops = kernel_flops_per_instance(name, N_GRID) * BATCH
-    achieved = flops / (per_launch_ms * 1e-3) / 1e12
-    peak = PEAK_TFLOPS[args.precision]
-    share = tot / sum(v[1] for v in prof.values())
-    traffic = NCU_TRAFFIC.get((name, N_GRID, args.precision))
+    real_bytes = 8 if prec == "fp64" else 4
+    peak = peaks["fp64_tflops"] if prec == "fp64" else peaks["fp32_tflops"]
 
     # end to end through the same C-ABI call with pinned host buffers
     hp = torch.from_numpy(params).pin_memory()
@@ -586,70 +821,70 @@ def run_ours(args, world, rank, local):
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         plan.apply_linearized(hp, hg, ho)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    e2e_s = max_over_ranks(e2e_s, world)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world)
 
+    cfg = workload_config(args.omega, prec)
+    cfg.update({"eps": args.eps if args.eps is not None else 1e-9,
+                "jgroups": jgroups if jgroups else "n/a",
+                "parallelism": "replicas (instances sharded, no collective)" if world > 1 else "single GPU",
+                "l2": "inputs 67 MB + outputs 67 MB + workspace per step > 129 MB L2"})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-        "config": {"workload": "batched L[g], N=32, batch 256 per GPU, per-instance Maxwellians, "
-                               "quartic polynomial + 1e-3 noise",
-                   "N": N_GRID, "box": BOX, "vhs_omega": args.omega, "radial_nodes": N_GRID,
-                   "batch_per_gpu": BATCH, "precision": args.precision,
-                   "eps": args.eps if args.eps is not None else 1e-9,
-                   "jgroups": jgroups if jgroups else "default",
-                   "parallelism": "replicas (instances sharded, no collective)" if world > 1 else "single GPU",
-                   "l2": "inputs 67 MB + outputs 67 MB + workspace 0.41 GB per step > 129 MB L2"},
-        "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": "derived: flop/clk/SM x 152 SMs x 2070 MHz",
-                     "kernel_share": share, "kernel_ms_per_launch": per_launch_ms,
-                     "apply_flops_per_instance": apply_flops_per_instance(N_GRID, N_GRID)},
-        "kernel_rooflines": kernel_rooflines(prof, N_GRID, BATCH, peak),
+        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+        "config": cfg, "gpu_launches": launches,
+        "roofline": dominant_roofline(prof, prec, peaks, hbm, hbm_src, jgroups or 1),
+        "kernel_rooflines": kernel_rooflines(prof, N_GRID, BATCH, peak, hbm, real_bytes, jgroups or 1),
+        "measured_peaks": dict(peaks, hbm_gbs=hbm, hbm_source=hbm_src),
         "e2e": {"value": world * BATCH / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(params.nbytes + g.nbytes), "d2h_bytes_per_step": int(g.nbytes)},
     }
     if clk is not None:
         line["clocks"] = clk
-    ref = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    solo = rank == 0 and world == 1
+    ref = ref_c = rms = rms_c = None
+    k_clean = 4
+    pc, gc = workloads.batched_instances(N_GRID, BOX, batch=BATCH, seed=args.seed + rank, noise=0.0)
+    tpc, tgc = torch.from_numpy(pc).to(dev), torch.from_numpy(gc).to(dev)
+    if solo and not args.no_cpu_baseline:
         got = out.cpu().numpy()
-        ref, cpu_rate = oracle_sample(params, g, N_GRID, BOX, args.omega, args.cpu_seconds)
+        ref, rate1 = oracle_sample(params, g, N_GRID, BOX, args.omega, args.cpu_seconds)
         k = ref.shape[0]
-        err = float(np.abs(got[:k] - ref).max() / np.abs(ref).max())
-        line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "first %d instances of the batch, numpy FFT form of "
-                                          "Algorithm 1, single process" % k}
-        line["rel_err_vs_oracle"] = {"value": err, "instances": k,
-                                     "metric": "max|gpu - oracle| / max|oracle| over the sampled instances"}
-    if args.precision != "fp64" and not args.no_fp64_leg:
-        # the plain FP64 GPU path on the same inputs, same timing method
-        p64 = lbo.Plan(N_GRID, BOX, args.omega, N_GRID, precision="fp64")
-        out64 = torch.empty_like(tg)
-        for _ in range(2):
-            p64.apply_linearized(tp, tg, out64)
+        rms = ratio_rms(params[:k], g[:k], N_GRID, BOX)
+        from oracle.linearized import Tables, apply_linearized
+        ref_c = apply_linearized(Tables(N_GRID, BOX, args.omega, N_GRID), pc[:k_clean], gc[:k_clean])
+        rms_c = ratio_rms(pc[:k_clean], gc[:k_clean], N_GRID, BOX)
+        unit = U64 if prec == "fp64" else U32
+        line["accuracy_noisy"] = error_report(got[:k], ref, rms, unit)
+        outc = torch.empty_like(tgc)
+        plan.apply_linearized(tpc, tgc, outc)
         torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p64.profile(True)
-        f0.record(stream)
-        for _ in range(args.fp64_steps):
-            p64.apply_linearized(tp, tg, out64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        prof64 = p64.profile_read()
-        p64.profile(False)
-        ms64 = max_over_ranks(f0.elapsed_time(f1) / args.fp64_steps, world)
-        line["fp64_plain"] = {"value": world * BATCH / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
-                              "speedup_of_value": value / (world * BATCH / (ms64 * 1e-3)),
-                              "kernel_rooflines": kernel_rooflines(prof64, N_GRID, BATCH, PEAK_TFLOPS["fp64"])}
-        if ref is not None:
-            k = ref.shape[0]
-            got64 = out64.cpu().numpy()[:k]
-            line["fp64_plain"]["rel_err_vs_oracle"] = float(np.abs(got64 - ref).max() / np.abs(ref).max())
-        p64.close()
-    if rank == 0 and world == 1 and not args.no_extra:
+        acc_c = error_report(outc.cpu().numpy()[:k_clean], ref_c, rms_c, unit)
+        if prec == "fp64":
+            acc_c["within_1e-12"] = acc_c["rel_err_vs_oracle"] <= 1e-12
+        line["accuracy_noise_free"] = acc_c
+        pool = OraclePool(N_GRID, BOX, args.omega, BATCH, args.seed, 1e-3)
+        count = max(pool.cores, int(rate1 * pool.cores * args.cpu_seconds))
+        secs = pool.run(count)
+        pool.close()
+        line["cpu_baseline"] = {
+            "value": count / secs, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": "%d instances of the benchmark batch (cycling), numpy FFT form of Algorithm 1 in FP64, "
+                      "one process per host core" % count,
+            "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                            "sample": "first %d instances of the batch, one process" % k}}
+    if solo and not args.no_variants:
+        line["variants"] = {}
+        for vp in ("fp32", "fp64"):
+            if vp == prec:
+                continue
+            rec = variant_leg(vp, tp, tg, tpc, tgc, stream, args.steps, peaks, hbm, ref, ref_c, rms, rms_c,
+                              k_clean)
+            rec["speedup_vs_value"] = rec["value"] / value
+            line["variants"][vp] = rec
+        line["omega_sweep_fp64"] = omega_sweep(tp, tg, tpc, tgc, params, g, pc, gc, stream, min(args.steps, 10),
+                                               not args.no_cpu_baseline)
+    if solo and not args.no_extra:
         line["newton_step"] = {"workload": "1-D steady slab, 128 cells, N=32, hard spheres, walls theta 1/2, "
                                            "Kn=1, first step from a global Maxwellian theta=1.5",
                                "fp32": newton_leg("fp32", 1.0), "fp64": newton_leg("fp64", 1.0),
@@ -679,12 +914,12 @@ def run_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
-    ap.add_argument("--no-fp64-leg", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="precision of the headline value (the other forms are reported as variants)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other precision forms and the omega sweep")
     ap.add_argument("--omega", type=float, default=0.5)
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--moment-fix", action="store_true")
@@ -694,7 +929,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--ref-instances", type=int, default=4)
+    ap.add_argument("--ref-per-core", type=int, default=1, help="reference arm: instances per core per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the Newton-step and mixed-N legs")
     args = ap.parse_args()

@@ -399,6 +399,20 @@ lbo_status lbo_group_apply_linearized(lbo_group *group, const double *const *par
                                       double *const *out, const int *batch);
 void lbo_group_destroy(lbo_group *group);
 
+/* Measured ALU peaks of the current device, the denominators of the
+ * library's roofline fractions for ALU-bound kernels (a measurement
+ * facility; the paper has no counterpart).  Runs dense chains of FP32 FFMA
+ * and FP64 DFMA (independent chains per thread, one full wave of 64 warps
+ * per SM, about 25 ms per launch), times them with CUDA events on `stream`
+ * (a cudaStream_t as void*, NULL = legacy default stream) and returns the
+ * best of three launches in TFLOP/s (an FMA counts 2 flops), the SM count
+ * from the device properties, and the SM clock seen by the FMA loop
+ * (clock64 cycles over the event time, MHz).  Any output pointer may be
+ * NULL.  Allocates and frees a small device buffer; synchronizes `stream`.
+ * Errors: LBO_ECUDA, LBO_ENOMEM. */
+lbo_status lbo_measure_alu_peaks(void *stream, double *fp32_tflops, double *fp64_tflops, int *sm_count,
+                                 double *sm_mhz);
+
 /* Free a plan (NULL is allowed). */
 void lbo_plan_destroy(lbo_plan *plan);
 

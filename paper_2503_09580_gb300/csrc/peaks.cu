@@ -1,0 +1,113 @@
+// lbo_measure_alu_peaks: dense FP32 FFMA and FP64 DFMA throughput of the
+// current device, measured with CUDA events (the denominators of the
+// library's roofline fractions for the ALU-bound kernels).
+//
+// Every thread runs ACC independent fused multiply-add chains
+// x <- x * a + b (a = 1 - 2^-10, b = 2^-10: the chains converge to 1, so no
+// overflow and no subnormal operands), enough independent work to hide the
+// pipe latency; the grid is SMs x 8 blocks of 256 threads (one full wave,
+// 64 warps per SM).  A store that depends on every chain keeps the work
+// alive.  Thread 0 of block 0 reads clock64() around its loop, which gives
+// the SM clock the peak was measured at.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "lbo_internal.h"
+
+namespace lbo {
+namespace {
+
+constexpr int kAcc = 8, kThreads = 256, kBlocksPerSM = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fma_chains(T* sink, long long* cycles, int iters, T a, T b) {
+  T x[kAcc];
+#pragma unroll
+  for (int i = 0; i < kAcc; ++i) x[i] = (T)(threadIdx.x + 1) * (T)(i + 1) * (T)0.0009765625;
+  const long long c0 = clock64();
+#pragma unroll 4
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) x[i] = fma(x[i], a, b);
+  }
+  const long long c1 = clock64();
+  T s = (T)0;
+#pragma unroll
+  for (int i = 0; i < kAcc; ++i) s += x[i];
+  if (s == (T)-1) sink[blockIdx.x * kThreads + threadIdx.x] = s;  // never taken: x stays near 1
+  if (blockIdx.x == 0 && threadIdx.x == 0) *cycles = c1 - c0;
+}
+
+template <typename T>
+lbo_status measure(cudaStream_t s, int sms, int iters, double* tflops, double* mhz, T* sink, long long* d_cyc) {
+  const int blocks = sms * kBlocksPerSM;
+  const T a = (T)(1.0 - 1.0 / 1024.0), b = (T)(1.0 / 1024.0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e, "peaks: event");
+  }
+  double best = 0.0, clk = 0.0;
+  k_fma_chains<T><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters / 8, a, b);  // warm-up
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(e0, s);
+    k_fma_chains<T><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters, a, b);
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    long long cyc = 0;
+    e = cudaMemcpy(&cyc, d_cyc, sizeof(cyc), cudaMemcpyDeviceToHost);
+    const double flops = 2.0 * kAcc * (double)iters * blocks * kThreads;
+    const double rate = flops / (ms * 1e-3) / 1e12;
+    if (rate > best) {
+      best = rate;
+      clk = (double)cyc / (ms * 1e-3) / 1e6;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "peaks: kernel");
+  *tflops = best;
+  *mhz = clk;
+  return LBO_OK;
+}
+
+}  // namespace
+}  // namespace lbo
+
+extern "C" lbo_status lbo_measure_alu_peaks(void* stream, double* fp32_tflops, double* fp64_tflops, int* sm_count,
+                                            double* sm_mhz) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return lbo::cuda_fail(e, "peaks: device");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* sink = nullptr;
+  long long* cyc = nullptr;
+  const size_t n = (size_t)sms * lbo::kBlocksPerSM * lbo::kThreads;
+  e = cudaMalloc(&sink, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&cyc, sizeof(long long));
+  if (e != cudaSuccess) {
+    if (sink) cudaFree(sink);
+    cudaGetLastError();
+    return LBO_ENOMEM;
+  }
+  // about 25 ms per launch on a GB300 (128 FP32 and 2 FP64 FMA lanes per SM)
+  double f32 = 0, f64 = 0, mhz32 = 0, mhz64 = 0;
+  lbo_status st = lbo::measure<float>(s, sms, 1 << 19, &f32, &mhz32, (float*)sink, cyc);
+  if (st == LBO_OK) st = lbo::measure<double>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
+  cudaFree(sink);
+  cudaFree(cyc);
+  if (st != LBO_OK) return st;
+  if (fp32_tflops) *fp32_tflops = f32;
+  if (fp64_tflops) *fp64_tflops = f64;
+  if (sm_count) *sm_count = sms;
+  if (sm_mhz) *sm_mhz = std::min(mhz32, mhz64);
+  return LBO_OK;
+}

@@ -32,7 +32,7 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_solver_destroy", "lbo_network_param_count", "lbo_network_loss_grad", "lbo_solver_collect",
            "lbo_solver_pair_count", "lbo_solver_train_network", "lbo_solver_get_network", "lbo_solver_set_network",
            "lbo_solver_network_param_count", "lbo_plan_autotune", "lbo_group_create", "lbo_group_set_stream",
-           "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy")
+           "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy", "lbo_measure_alu_peaks")
 
 _lib = None
 
@@ -119,6 +119,9 @@ def load():
     lib.lbo_noalloc_scratch_bytes.restype = ctypes.c_size_t
     lib.lbo_noalloc_bytes_per_instance.argtypes = [vp]
     lib.lbo_noalloc_bytes_per_instance.restype = ctypes.c_size_t
+    dpp = ctypes.POINTER(ctypes.c_double)
+    lib.lbo_measure_alu_peaks.argtypes = [vp, dpp, dpp, ctypes.POINTER(ip), dpp]
+    lib.lbo_measure_alu_peaks.restype = ip
     lib.lbo_solver_create.argtypes = [ctypes.POINTER(Problem), vp, ctypes.POINTER(vp)]
     lib.lbo_solver_create.restype = ip
     lib.lbo_newton_step.argtypes = [vp, dp, dp, ctypes.POINTER(NewtonStats)]
@@ -192,6 +195,21 @@ def _current_stream(*arrays):
             import torch
             return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
     return None
+
+
+def measure_alu_peaks(stream=None):
+    """lbo_measure_alu_peaks on the current device: {"fp32_tflops",
+    "fp64_tflops", "sm_count", "sm_mhz"} (stream: a torch.cuda.Stream or
+    None for torch's current stream)."""
+    lib = load()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    f32, f64, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    sms = ctypes.c_int()
+    _check(lib.lbo_measure_alu_peaks(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(f32), ctypes.byref(f64),
+                                     ctypes.byref(sms), ctypes.byref(mhz)), "lbo_measure_alu_peaks")
+    return {"fp32_tflops": f32.value, "fp64_tflops": f64.value, "sm_count": sms.value, "sm_mhz": mhz.value}
 
 
 class Plan:

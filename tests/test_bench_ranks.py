@@ -37,7 +37,7 @@ def _worker(rank, world, port, out):
     params, g = workloads.batched_instances(16, 8.0, batch=2, seed=7 + r, noise=1e-3)
     # the reference arm prints on rank 0 only; other ranks return at once
     class Args:
-        seed, omega, warmup, steps, ref_instances, gpus = 0, 0.5, 0, 0, 1, w
+        seed, omega, warmup, steps, ref_per_core, gpus = 0, 0.5, 0, 0, 1, w
     skipped = r != 0 and bench.run_reference(Args, w, r) is None
     out.put((r, w, ms, float(params[0, 0]), float(g.sum()), skipped))
     dist.destroy_process_group()
