@@ -53,8 +53,17 @@ typedef enum {
 
 typedef enum {
   LBO_PREC_FP64 = 0,     /* FP64 transforms and products (the plain path)   */
-  LBO_PREC_FP32 = 1      /* FP32 transforms and products, FP64 in/out,
+  LBO_PREC_FP32 = 1,     /* FP32 transforms and products, FP64 in/out,
                             FP64 Maxwellians, cut-off and final combination */
+  LBO_PREC_FP32X2 = 2,   /* transforms and products in pairs of FP32 numbers
+                            (hi + lo, about 48 significant bits, FP32
+                            exponent range) on the FP32 pipe; FP64
+                            Maxwellians, ratio, cut-off and combination     */
+  LBO_PREC_FP64X2 = 3    /* transforms and products in pairs of FP64 numbers
+                            (about 106 significant bits): the higher-
+                            precision convolution of Sec. 3.4 (the paper
+                            uses binary128), accurate without the cut-off
+                            where FP64 transforms lose max|r| u digits     */
 } lbo_precision;
 
 typedef enum {

@@ -15,6 +15,9 @@
 
 #include <cmath>
 
+#include "twiddles_hi.h"
+#include "twofold.cuh"
+
 namespace lbo {
 
 template <typename T>
@@ -51,31 +54,54 @@ __device__ __forceinline__ cpx<T> mul_mi(cpx<T> a) {
   return INV ? make_c(-a.y, a.x) : make_c(a.y, -a.x);
 }
 
-// W_64^m = exp(-2 pi i m / 64), m = 0..63.  Each translation unit has its own
-// copy (no relocatable device code); upload_twiddles() fills it once.
+// W_64^m = exp(-2 pi i m / 64), m = 0..63, and W_48^m (radix-3 sizes N = 24,
+// 48), in every transform precision: double, float, and the two-fold pairs
+// {re.hi, re.lo, im.hi, im.lo}.  Each translation unit has its own copy (no
+// relocatable device code); upload_twiddles() fills it once per device from
+// the double-pair table of twiddles_hi.h.
 static __constant__ double2 c_tw64_d[64];
 static __constant__ float2 c_tw64_f[64];
-// W_48^m, for the radix-3 sizes N = 24, 48
+static __constant__ float4 c_tw64_ff[64];
+static __constant__ double2 c_tw64_dd[2 * 64];  // [2m] = (re.hi, re.lo), [2m+1] = (im.hi, im.lo)
 static __constant__ double2 c_tw48_d[48];
 static __constant__ float2 c_tw48_f[48];
+static __constant__ float4 c_tw48_ff[48];
+static __constant__ double2 c_tw48_dd[2 * 48];
+
+// a double pair (hi, lo) as a float pair carrying ~48 bits
+static inline void split_to_float_pair(double hi, double lo, float* fh, float* fl) {
+  *fh = (float)hi;
+  *fl = (float)((hi - (double)*fh) + lo);
+}
+
+template <int NT>
+static void fill_tw(const double (*src)[4], double2* d, float2* f, float4* ff, double2* dd) {
+  for (int m = 0; m < NT; ++m) {
+    d[m] = make_double2(src[m][0], src[m][2]);
+    f[m] = make_float2((float)src[m][0], (float)src[m][2]);
+    float a, b, c, e;
+    split_to_float_pair(src[m][0], src[m][1], &a, &b);
+    split_to_float_pair(src[m][2], src[m][3], &c, &e);
+    ff[m] = make_float4(a, b, c, e);
+    dd[2 * m] = make_double2(src[m][0], src[m][1]);
+    dd[2 * m + 1] = make_double2(src[m][2], src[m][3]);
+  }
+}
 
 static cudaError_t upload_twiddles_now() {
-  double2 d[64], d48[48];
+  double2 d[64], d48[48], dd[128], dd48[96];
   float2 f[64], f48[48];
-  for (int m = 0; m < 64; ++m) {
-    long double a = -2.0L * 3.14159265358979323846264338327950288L * m / 64.0L;
-    d[m] = make_double2((double)cosl(a), (double)sinl(a));
-    f[m] = make_float2((float)d[m].x, (float)d[m].y);
-  }
-  for (int m = 0; m < 48; ++m) {
-    long double a = -2.0L * 3.14159265358979323846264338327950288L * m / 48.0L;
-    d48[m] = make_double2((double)cosl(a), (double)sinl(a));
-    f48[m] = make_float2((float)d48[m].x, (float)d48[m].y);
-  }
+  float4 ff[64], ff48[48];
+  fill_tw<64>(kTw64Hi, d, f, ff, dd);
+  fill_tw<48>(kTw48Hi, d48, f48, ff48, dd48);
   cudaError_t e = cudaMemcpyToSymbol(c_tw64_d, d, sizeof(d));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw64_f, f, sizeof(f));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw64_ff, ff, sizeof(ff));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw64_dd, dd, sizeof(dd));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw48_d, d48, sizeof(d48));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw48_f, f48, sizeof(f48));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw48_ff, ff48, sizeof(ff48));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tw48_dd, dd48, sizeof(dd48));
   return e;
 }
 
@@ -104,6 +130,17 @@ __device__ __forceinline__ cpx<float> tw64<float>(int m) {
   return make_c(t.x, t.y);
 }
 
+template <>
+__device__ __forceinline__ cpx<f32x2> tw64<f32x2>(int m) {
+  float4 t = c_tw64_ff[m & 63];
+  return make_c(f32x2(t.x, t.y), f32x2(t.z, t.w));
+}
+template <>
+__device__ __forceinline__ cpx<f64x2> tw64<f64x2>(int m) {
+  double2 a = c_tw64_dd[2 * (m & 63)], b = c_tw64_dd[2 * (m & 63) + 1];
+  return make_c(f64x2(a.x, a.y), f64x2(b.x, b.y));
+}
+
 template <typename T>
 __device__ __forceinline__ cpx<T> tw48(int m);
 template <>
@@ -115,6 +152,16 @@ template <>
 __device__ __forceinline__ cpx<float> tw48<float>(int m) {
   float2 t = c_tw48_f[m % 48];
   return make_c(t.x, t.y);
+}
+template <>
+__device__ __forceinline__ cpx<f32x2> tw48<f32x2>(int m) {
+  float4 t = c_tw48_ff[m % 48];
+  return make_c(f32x2(t.x, t.y), f32x2(t.z, t.w));
+}
+template <>
+__device__ __forceinline__ cpx<f64x2> tw48<f64x2>(int m) {
+  double2 a = c_tw48_dd[2 * (m % 48)], b = c_tw48_dd[2 * (m % 48) + 1];
+  return make_c(f64x2(a.x, a.y), f64x2(b.x, b.y));
 }
 
 // W_N^m for N dividing 64 or 48
@@ -144,7 +191,7 @@ __device__ __forceinline__ void dft4(cpx<T>* a) {
 
 template <typename T, bool INV>
 __device__ __forceinline__ void dft8(cpx<T>* a) {
-  const T r = (T)0.70710678118654752440084436210484903928483593768847;
+  const T r = kconst<T>(0x1.6a09e667f3bcdp-1, -0x1.bdd3413b26456p-55);  // 1/sqrt2
   cpx<T> e[4] = {a[0], a[2], a[4], a[6]};
   cpx<T> o[4] = {a[1], a[3], a[5], a[7]};
   dft4<T, INV>(e);
@@ -169,7 +216,7 @@ __device__ __forceinline__ void dft8(cpx<T>* a) {
 // s = -+i (sqrt3/2)(a1 - a2)
 template <typename T, bool INV>
 __device__ __forceinline__ void dft3(cpx<T>* a) {
-  const T c = (T)0.86602540378443864676372317075293618347140262690519;
+  const T c = kconst<T>(0x1.bb67ae8584caap-1, 0x1.cec95d0b5c1e3p-55);  // sqrt3/2
   cpx<T> t1 = a[1] + a[2], t2 = a[1] - a[2];
   cpx<T> m = make_c(a[0].x - (T)0.5 * t1.x, a[0].y - (T)0.5 * t1.y);
   cpx<T> sv = INV ? make_c(-c * t2.y, c * t2.x) : make_c(c * t2.y, -c * t2.x);
@@ -182,7 +229,7 @@ __device__ __forceinline__ void dft3(cpx<T>* a) {
 // X[k+3] = E[k] - W6^k O[k]
 template <typename T, bool INV>
 __device__ __forceinline__ void dft6(cpx<T>* a) {
-  const T c = (T)0.86602540378443864676372317075293618347140262690519;
+  const T c = kconst<T>(0x1.bb67ae8584caap-1, 0x1.cec95d0b5c1e3p-55);  // sqrt3/2
   cpx<T> e[3] = {a[0], a[2], a[4]};
   cpx<T> o[3] = {a[1], a[3], a[5]};
   dft3<T, INV>(e);

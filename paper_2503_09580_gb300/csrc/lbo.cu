@@ -13,7 +13,7 @@
 
 #include "../../include/lbo.h"
 #include "lbo_internal.h"
-#include "lin_kernels.cuh"
+#include "lin_generic.cuh"
 
 namespace lbo {
 static thread_local std::string g_last_error;
@@ -80,6 +80,7 @@ template <typename T, int N>
 static lbo_status build_phit(lbo_plan* p, const double* d_stab, T* d_phit);
 
 static void free_tables(lbo_plan* p) {
+  free_twofold_tables(p);
   void* ptrs[] = {p->d_phi64, p->d_omega64, p->d_phit64, p->d_phi32, p->d_omega32, p->d_phit32, p->d_dummy_params,
                   p->d_dct64, p->d_dct32};
   for (void* q : ptrs)
@@ -211,8 +212,9 @@ static lbo_status ensure_ws_bytes(lbo_plan* p, size_t bytes) {
 static lbo_status ensure_workspace(lbo_plan* p, int batch) {
   const size_t N = p->N, H = N * N * (N / 2 + 1), n3 = N * N * N, HN = N / 2 + 1;
   // generic path: 3 half spectra + 3 real fields + the u^_j DCT planes per
-  // instance, sized for FP64
-  return ensure_ws_bytes(p, (size_t)batch * (3 * H * 16 + 3 * n3 * 8 + HN * HN * HN * 8));
+  // instance, sized for FP64 (for the FP64 pairs: twice that)
+  const size_t rb = generic_real_bytes(p->precision);
+  return ensure_ws_bytes(p, (size_t)batch * (3 * H * 2 * rb + 3 * n3 * rb + HN * HN * HN * rb));
 }
 
 static lbo_status ensure_stage(lbo_plan* p, size_t in_doubles, size_t out_doubles, size_t par_doubles) {
@@ -234,14 +236,6 @@ static lbo_status ensure_stage(lbo_plan* p, size_t in_doubles, size_t out_double
   if (s == LBO_OK) s = grow(p->stage_par, p->stage_par_cap, par_doubles);
   return s;
 }
-
-template <typename K>
-static void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <int N>
-struct PlanePPC { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : (N == 24 ? 4 : (N == 48 ? 2 : 1))); };
 
 // phit_j = IDFT(s_j) for all j, FP64, then an FP32 copy.
 template <typename T, int N>
@@ -286,113 +280,15 @@ static lbo_status build_phit(lbo_plan* p, const double* d_stab, T* d_phit) {
   return LBO_OK;
 }
 
-// ------------------------------------------------------------ L[g]
-template <typename T, int N>
-static lbo_status run_linearized(lbo_plan* p, const double* params, const double* g, double* out, int B) {
-  constexpr int PPC = PlanePPC<N>::v, CW = 32, HC = N / 2 + 1;
-  const size_t H = (size_t)N * N * HC, n3 = (size_t)N * N * N;
-  cudaStream_t s = p->stream;
-  unsigned char* ws = (unsigned char*)p->ws;
-  cpx<T>* RH = (cpx<T>*)ws;
-  cpx<T>* W1 = RH + (size_t)B * H;
-  cpx<T>* LH = W1 + (size_t)B * H;
-  T* R1 = (T*)(LH + (size_t)B * H);
-  T* R2 = R1 + (size_t)B * n3;
-  T* R3 = R2 + (size_t)B * n3;
-  T* UP = R3 + (size_t)B * n3;  // [B][HC]^3 u^_j after the axis-3 and axis-2 DCTs
-  const bool f64 = sizeof(T) == 8;
-  const T* dct = (const T*)(f64 ? (void*)p->d_dct64 : (void*)p->d_dct32);
-  const T* phi = (const T*)(f64 ? (void*)p->d_phi64 : (void*)p->d_phi32);
-  const T* omg = (const T*)(f64 ? (void*)p->d_omega64 : (void*)p->d_omega32);
-  const T* phit = (const T*)(f64 ? (void*)p->d_phit64 : (void*)p->d_phit32);
-  const int Q = qmax_of(N);
-  const size_t sm = PlaneSmem<T, N, PPC>::BYTES;
-  const dim3 gp(N / PPC, B), ga((N * HC + CW - 1) / CW, B), blk(256);
-  set_smem(k_plane_fwd<T, N, PPC, SRC_RATIO>, sm);
-  set_smem(k_plane_fwd<T, N, PPC, SRC_REAL64>, sm);
-  set_smem(k_plane_fwd<T, N, PPC, SRC_MAXW>, sm);
-  set_smem(k_plane_inv<T, N, PPC, INV_MH_FWD>, sm);
-  set_smem(k_plane_inv<T, N, PPC, INV_TO_REAL>, sm);
-  PlaneArgs pa{};
-  pa.params = params;
-  pa.g = g;
-  pa.h = 2.0 * p->L / N;
-  pa.log_inv_eps = std::log(1.0 / p->eps);
-  pa.cutoff = p->cutoff;
-  auto kf_ratio = k_plane_fwd<T, N, PPC, SRC_RATIO>;
-  auto kf_real = k_plane_fwd<T, N, PPC, SRC_REAL64>;
-  auto kf_maxw = k_plane_fwd<T, N, PPC, SRC_MAXW>;
-  auto ki_mh = k_plane_inv<T, N, PPC, INV_MH_FWD>;
-  auto ki_real = k_plane_inv<T, N, PPC, INV_TO_REAL>;
-  auto ka_fwd = k_axis1<T, N, CW, AX_FWD_STORE>;
-  auto ka_mult = k_axis1<T, N, CW, AX_FWD_MULT_INV>;
-  auto ka_acc = k_axis1<T, N, CW, AX_FWD_ACC>;
-  auto ka_inv = k_axis1<T, N, CW, AX_INV_STORE>;
-  auto ka_uhat = k_axis1<T, N, CW, AX_UHAT_INV>;
-  constexpr int PL = UhatPlanes<N>::PL;  // octant planes per block
-  auto k_up = k_uhat_planes<T, N, PL>;
-  const size_t sm_up = sizeof(T) * ((size_t)PL * HC * HC + (size_t)HC * (N / 4));
-  set_smem(k_up, sm_up);
-  auto k_comb = k_combine<T, N>;
-  int launches = 0;
-  // r^ = FFT(r), r = g/M with the cut-off (Algorithm 1, gain term)
-  LBO_LAUNCH(p, "plane_fwd_ratio", s, kf_ratio, gp, blk, sm, pa, W1);
-  Axis1Args ax{};
-  LBO_LAUNCH(p, "axis1_fwd", s, ka_fwd, ga, blk, 0, ax, W1, RH);
-  launches += 2;
-  for (int j = 0; j < p->J; ++j) {
-    // u^_j = FFT(M^g phit_j), real and even: DCT-I of the octant, axes 3 and 2
-    LBO_LAUNCH(p, "uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params, phit + (size_t)j * n3,
-               dct, pa.h, UP);
-    // psi_j = InvFFT(u^_j r^), u^_j finished along axis 1 in the same kernel
-    Axis1Args a1{};
-    a1.uplanes = UP;
-    a1.dct = dct;
-    a1.scale = 1.0 / (double)n3;
-    LBO_LAUNCH(p, "axis1_uhat_inv", s, ka_uhat, ga, blk, 0, a1, RH, W1);
-    // psi_j <- M^h psi_j ; psi^_j = FFT(psi_j)
-    LBO_LAUNCH(p, "plane_inv_mh_fwd", s, ki_mh, gp, blk, sm, pa, W1, (T*)nullptr);
-    // L^+ += phi_j psi^_j
-    Axis1Args a2{};
-    a2.table = phi + (size_t)j * Q;
-    a2.first = j == 0;
-    LBO_LAUNCH(p, "axis1_fwd_acc", s, ka_acc, ga, blk, 0, a2, W1, LH);
-    launches += 4;
-  }
-  // L+ = InvFFT(L^+)
-  LBO_LAUNCH(p, "axis1_inv", s, ka_inv, ga, blk, 0, ax, LH, LH);
-  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, LH, R1);
-  // loss term: u = InvFFT(f^ omega), w = InvFFT(M^ omega)
-  Axis1Args a3{};
-  a3.table = omg;
-  LBO_LAUNCH(p, "plane_fwd_g", s, kf_real, gp, blk, sm, pa, W1);
-  LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
-  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R2);
-  LBO_LAUNCH(p, "plane_fwd_maxw", s, kf_maxw, gp, blk, sm, pa, W1);
-  LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
-  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R3);
-  LBO_LAUNCH(p, "combine", s, k_comb, dim3(N, B), 256, 0, params, g, R1, R2, R3, out, pa.h, pa.log_inv_eps);
-  launches += 9;
-  if (p->mass_fix || p->moment_fix) {
-    lbo_status st = launch_fixes(p, out, B, N, pa.h, s, &launches);
-    if (st != LBO_OK) return st;
-  }
-  p->last_launches = launches;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "linearized launch");
-  return LBO_OK;
-}
-
 template <typename T>
 static lbo_status dispatch_lin(lbo_plan* p, const double* params, const double* g, double* out, int B) {
-  switch (p->N) {
-    case 16: return run_linearized<T, 16>(p, params, g, out, B);
-    case 24: return run_linearized<T, 24>(p, params, g, out, B);
-    case 32: return run_linearized<T, 32>(p, params, g, out, B);
-    case 48: return run_linearized<T, 48>(p, params, g, out, B);
-    case 64: return run_linearized<T, 64>(p, params, g, out, B);
-    default: return LBO_EUNSUPPORTED;
-  }
+  const bool f64 = sizeof(T) == 8;
+  GenericTables<T> tb;
+  tb.phi = (const T*)(f64 ? (const void*)p->d_phi64 : (const void*)p->d_phi32);
+  tb.omega = (const T*)(f64 ? (const void*)p->d_omega64 : (const void*)p->d_omega32);
+  tb.phit = (const T*)(f64 ? (const void*)p->d_phit64 : (const void*)p->d_phit32);
+  tb.dct = (const T*)(f64 ? (const void*)p->d_dct64 : (const void*)p->d_dct32);
+  return dispatch_generic<T>(p, tb, params, g, out, B, p->ws);
 }
 
 static bool is_device_ptr(const void* ptr) {
@@ -476,7 +372,7 @@ lbo_status lbo_plan_set(lbo_plan* p, lbo_option key, double v) {
       p->hemi_p = (int)v;
       break;
     case LBO_OPT_PRECISION:
-      if (v != 0.0 && v != 1.0) return LBO_EINVAL;
+      if (v != 0.0 && v != 1.0 && v != 2.0 && v != 3.0) return LBO_EINVAL;
       p->precision = (int)v;
       break;
     case LBO_OPT_KERNEL:
@@ -535,6 +431,8 @@ lbo_status lbo_apply_linearized(lbo_plan* p, const double* params, const double*
     if (st == LBO_OK && (p->mass_fix || p->moment_fix))
       st = launch_fixes(p, dout, batch, p->N, 2.0 * p->L / p->N, p->stream, &launches);
     p->last_launches = launches;
+  } else if (is_twofold_precision(p->precision)) {
+    st = run_linearized_twofold(p, dp, dg, dout, batch);
   } else {
     st = p->precision == LBO_PREC_FP64 ? dispatch_lin<double>(p, dp, dg, dout, batch)
                                        : dispatch_lin<float>(p, dp, dg, dout, batch);

@@ -26,6 +26,9 @@ struct lbo_plan {
   double* d_dct64 = nullptr;    // [N/2+1][N/4] DCT-I coefficients of u^_j (lin_kernels.cuh)
   float* d_dct32 = nullptr;
   double* d_dummy_params = nullptr;
+  // two-fold tables {phit, phi, omega, dct}, built on first use (lin_twofold.cu)
+  void* d_x2f[4] = {nullptr, nullptr, nullptr, nullptr};  // pairs of FP32
+  void* d_x2d[4] = {nullptr, nullptr, nullptr, nullptr};  // pairs of FP64
   // workspace of the generic path
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -105,6 +108,13 @@ lbo_status launch_fixes(lbo_plan* p, double* out, int B, int N, double h, cudaSt
 void free_quadratic(lbo_plan* p);
 void gauss_legendre(int J, std::vector<double>& x, std::vector<double>& w);
 lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int B);
+// two-fold precisions FP32X2 / FP64X2 (lin_twofold.cu)
+lbo_status run_linearized_twofold(lbo_plan* p, const double* params, const double* g, double* out, int B);
+lbo_status twofold_tables(lbo_plan* p, const void** phi, const void** omega, const void** phit, const void** dct);
+void free_twofold_tables(lbo_plan* p);
+inline bool is_twofold_precision(int prec) { return prec == LBO_PREC_FP32X2 || prec == LBO_PREC_FP64X2; }
+// bytes of one real number in the transform precision of the generic path
+inline size_t generic_real_bytes(int prec) { return prec == LBO_PREC_FP64X2 ? 16 : 8; }
 // fused FP32 path for N = 32 (lin_fused32.cu)
 size_t fused32_workspace_bytes(int B, int G, int J);
 int fused32_default_groups(int B);

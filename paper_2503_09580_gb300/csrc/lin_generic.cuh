@@ -1,0 +1,144 @@
+// The generic launch sequence of L[g] (plane and axis-1 kernels of
+// lin_kernels.cuh), shared by the translation units that instantiate it for
+// their transform precisions (lbo.cu: FP64 and FP32; lin_twofold.cu: the
+// two-fold forms).  Each translation unit launches its own instances of the
+// kernels, so each uploads its own FFT twiddle tables (upload_twiddles).
+#pragma once
+#include <cmath>
+
+#include "lbo_internal.h"
+#include "lin_kernels.cuh"
+
+namespace lbo {
+
+// Device tables of Algorithm 1 in the transform precision T.
+template <typename T>
+struct GenericTables {
+  const T* phi;    // [J][3(N/2)^2+1] phi_j(|k|^2) / N^3
+  const T* omega;  // [3(N/2)^2+1] omega(|k|^2) / N^3
+  const T* phit;   // [J][N^3] phit_j, cyclic order
+  const T* dct;    // [N/2+1][N/4] DCT-I coefficients of u^_j
+};
+
+template <typename K>
+static inline void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int N>
+struct PlanePPC { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : (N == 24 ? 4 : (N == 48 ? 2 : 1))); };
+
+// The launch sequence of L[g] on the generic kernels (Algorithm 1, in
+// order): r^ = FFT(r); per radial node u^_j, psi_j = InvFFT(u^_j r^),
+// M^h psi_j, psi^_j = FFT, L^+ += phi_j psi^_j; L+ = InvFFT(L^+); the loss
+// term; the combination; the optional fixes.  ws: 3 half spectra + 3 real
+// fields + the u^_j octant planes per instance, in T.
+template <typename T, int N>
+static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb, const double* params,
+                                         const double* g, double* out, int B, void* ws_raw) {
+  constexpr int PPC = PlanePPC<N>::v, CW = 32, HC = N / 2 + 1;
+  const size_t H = (size_t)N * N * HC, n3 = (size_t)N * N * N;
+  cudaStream_t s = p->stream;
+  unsigned char* ws = (unsigned char*)ws_raw;
+  cpx<T>* RH = (cpx<T>*)ws;
+  cpx<T>* W1 = RH + (size_t)B * H;
+  cpx<T>* LH = W1 + (size_t)B * H;
+  T* R1 = (T*)(LH + (size_t)B * H);
+  T* R2 = R1 + (size_t)B * n3;
+  T* R3 = R2 + (size_t)B * n3;
+  T* UP = R3 + (size_t)B * n3;  // [B][HC]^3 u^_j after the axis-3 and axis-2 DCTs
+  const T *dct = tb.dct, *phi = tb.phi, *omg = tb.omega, *phit = tb.phit;
+  const int Q = 3 * (N / 2) * (N / 2) + 1;
+  static_assert(PlaneSmem<T, N, PPC>::BYTES <= 227 * 1024, "plane kernels: shared memory of a block");
+  static_assert(N * CW * sizeof(cpx<T>) + CW * HC * sizeof(T) <= 227 * 1024, "k_axis1: shared memory of a block");
+  const size_t sm = PlaneSmem<T, N, PPC>::BYTES;
+  const dim3 gp(N / PPC, B), ga((N * HC + CW - 1) / CW, B), blk(256);
+  set_smem(k_plane_fwd<T, N, PPC, SRC_RATIO>, sm);
+  set_smem(k_plane_fwd<T, N, PPC, SRC_REAL64>, sm);
+  set_smem(k_plane_fwd<T, N, PPC, SRC_MAXW>, sm);
+  set_smem(k_plane_inv<T, N, PPC, INV_MH_FWD>, sm);
+  set_smem(k_plane_inv<T, N, PPC, INV_TO_REAL>, sm);
+  PlaneArgs pa{};
+  pa.params = params;
+  pa.g = g;
+  pa.h = 2.0 * p->L / N;
+  pa.log_inv_eps = std::log(1.0 / p->eps);
+  pa.cutoff = p->cutoff;
+  auto kf_ratio = k_plane_fwd<T, N, PPC, SRC_RATIO>;
+  auto kf_real = k_plane_fwd<T, N, PPC, SRC_REAL64>;
+  auto kf_maxw = k_plane_fwd<T, N, PPC, SRC_MAXW>;
+  auto ki_mh = k_plane_inv<T, N, PPC, INV_MH_FWD>;
+  auto ki_real = k_plane_inv<T, N, PPC, INV_TO_REAL>;
+  auto ka_fwd = k_axis1<T, N, CW, AX_FWD_STORE>;
+  auto ka_mult = k_axis1<T, N, CW, AX_FWD_MULT_INV>;
+  auto ka_acc = k_axis1<T, N, CW, AX_FWD_ACC>;
+  auto ka_inv = k_axis1<T, N, CW, AX_INV_STORE>;
+  auto ka_uhat = k_axis1<T, N, CW, AX_UHAT_INV>;
+  constexpr int PL = UhatPlanes<N>::PL;  // octant planes per block
+  auto k_up = k_uhat_planes<T, N, PL>;
+  const size_t sm_up = sizeof(T) * ((size_t)PL * HC * HC + (size_t)HC * (N / 4));
+  set_smem(k_up, sm_up);
+  auto k_comb = k_combine<T, N>;
+  int launches = 0;
+  // r^ = FFT(r), r = g/M with the cut-off (Algorithm 1, gain term)
+  LBO_LAUNCH(p, "plane_fwd_ratio", s, kf_ratio, gp, blk, sm, pa, W1);
+  Axis1Args ax{};
+  LBO_LAUNCH(p, "axis1_fwd", s, ka_fwd, ga, blk, 0, ax, W1, RH);
+  launches += 2;
+  for (int j = 0; j < p->J; ++j) {
+    // u^_j = FFT(M^g phit_j), real and even: DCT-I of the octant, axes 3 and 2
+    LBO_LAUNCH(p, "uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params, phit + (size_t)j * n3,
+               dct, pa.h, UP);
+    // psi_j = InvFFT(u^_j r^), u^_j finished along axis 1 in the same kernel
+    Axis1Args a1{};
+    a1.uplanes = UP;
+    a1.dct = dct;
+    a1.scale = 1.0 / (double)n3;
+    LBO_LAUNCH(p, "axis1_uhat_inv", s, ka_uhat, ga, blk, 0, a1, RH, W1);
+    // psi_j <- M^h psi_j ; psi^_j = FFT(psi_j)
+    LBO_LAUNCH(p, "plane_inv_mh_fwd", s, ki_mh, gp, blk, sm, pa, W1, (T*)nullptr);
+    // L^+ += phi_j psi^_j
+    Axis1Args a2{};
+    a2.table = phi + (size_t)j * Q;
+    a2.first = j == 0;
+    LBO_LAUNCH(p, "axis1_fwd_acc", s, ka_acc, ga, blk, 0, a2, W1, LH);
+    launches += 4;
+  }
+  // L+ = InvFFT(L^+)
+  LBO_LAUNCH(p, "axis1_inv", s, ka_inv, ga, blk, 0, ax, LH, LH);
+  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, LH, R1);
+  // loss term: u = InvFFT(f^ omega), w = InvFFT(M^ omega)
+  Axis1Args a3{};
+  a3.table = omg;
+  LBO_LAUNCH(p, "plane_fwd_g", s, kf_real, gp, blk, sm, pa, W1);
+  LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
+  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R2);
+  LBO_LAUNCH(p, "plane_fwd_maxw", s, kf_maxw, gp, blk, sm, pa, W1);
+  LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
+  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R3);
+  LBO_LAUNCH(p, "combine", s, k_comb, dim3(N, B), 256, 0, params, g, R1, R2, R3, out, pa.h, pa.log_inv_eps);
+  launches += 9;
+  if (p->mass_fix || p->moment_fix) {
+    lbo_status st = launch_fixes(p, out, B, N, pa.h, s, &launches);
+    if (st != LBO_OK) return st;
+  }
+  p->last_launches = launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "linearized launch");
+  return LBO_OK;
+}
+
+template <typename T>
+static lbo_status dispatch_generic(lbo_plan* p, const GenericTables<T>& tb, const double* params, const double* g,
+                                  double* out, int B, void* ws) {
+  switch (p->N) {
+    case 16: return run_linearized_generic<T, 16>(p, tb, params, g, out, B, ws);
+    case 24: return run_linearized_generic<T, 24>(p, tb, params, g, out, B, ws);
+    case 32: return run_linearized_generic<T, 32>(p, tb, params, g, out, B, ws);
+    case 48: return run_linearized_generic<T, 48>(p, tb, params, g, out, B, ws);
+    case 64: return run_linearized_generic<T, 64>(p, tb, params, g, out, B, ws);
+    default: return LBO_EUNSUPPORTED;
+  }
+}
+
+}  // namespace lbo

@@ -242,9 +242,15 @@ __global__ void __launch_bounds__(256) k_plane_inv(PlaneArgs a, cpx<T>* __restri
   cpx<T>* A = (cpx<T>*)smem_raw;
   cpx<T>* B = A + PlaneSmem<T, N, PPC>::A_ELEMS;
   __shared__ double eh[3 * N];
+  __shared__ T ehT[is_twofold<T>::value ? 3 * N : 1];  // eh in T: the two-fold forms stay on their pipe
   const int b = blockIdx.y, i1_0 = blockIdx.x * PPC;
   const InstanceParams q = load_params(a.params, b);
-  if constexpr (MODE == INV_MH_FWD) fill_mh_tables<N>(eh, q, a.h);
+  if constexpr (MODE == INV_MH_FWD) {
+    fill_mh_tables<N>(eh, q, a.h);
+    if constexpr (is_twofold<T>::value) {
+      for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) ehT[t] = T(eh[t]);
+    }
+  }
   plane_load_B<T, N, PPC>(B, src, b, i1_0);
   plane_inverse_to_A<T, N, PPC>(A, B);
   if constexpr (MODE == INV_TO_REAL) {
@@ -259,10 +265,16 @@ __global__ void __launch_bounds__(256) k_plane_inv(PlaneArgs a, cpx<T>* __restri
     for (int t = threadIdx.x; t < PPC * (N / 2) * N; t += blockDim.x) {
       int i3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
       int i1 = i1_0 + pp;
-      double m13 = eh[i1] * eh[2 * N + i3];
       cpx<T>& z = A[(pp * (N / 2) + qq) * N + i3];
-      z.x = (T)((double)z.x * (m13 * eh[N + 2 * qq]));
-      z.y = (T)((double)z.y * (m13 * eh[N + 2 * qq + 1]));
+      if constexpr (is_twofold<T>::value) {
+        const T m13 = ehT[i1] * ehT[2 * N + i3];
+        z.x = z.x * (m13 * ehT[N + 2 * qq]);
+        z.y = z.y * (m13 * ehT[N + 2 * qq + 1]);
+      } else {
+        double m13 = eh[i1] * eh[2 * N + i3];
+        z.x = (T)((double)z.x * (m13 * eh[N + 2 * qq]));
+        z.y = (T)((double)z.y * (m13 * eh[N + 2 * qq + 1]));
+      }
     }
     __syncthreads();
     plane_forward_from_A<T, N, PPC>(A, B);
@@ -348,6 +360,7 @@ __global__ void __launch_bounds__(256) k_uhat_planes(const double* __restrict__ 
   T* W = (T*)smem_raw;            // [PL][HN][HN]
   T* tab = W + PL * HN * HN;      // [HN][Q4]
   __shared__ double mg[HN + 1];   // mg[HN] = rho (pi theta)^-3/2
+  __shared__ T mgT[is_twofold<T>::value ? HN + 1 : 1];
   const int b = blockIdx.y, d1_0 = blockIdx.x * PL;
   const int np = HN - d1_0 < PL ? HN - d1_0 : PL;
   const double rho = params[5 * b], theta = params[5 * b + 4];
@@ -361,10 +374,18 @@ __global__ void __launch_bounds__(256) k_uhat_planes(const double* __restrict__ 
   }
   for (int t = threadIdx.x; t < HN * Q4; t += blockDim.x) tab[t] = dct[t];
   __syncthreads();
+  if constexpr (is_twofold<T>::value) {
+    for (int t = threadIdx.x; t <= HN; t += blockDim.x) mgT[t] = T(mg[t]);
+    __syncthreads();
+  }
   for (int t = threadIdx.x; t < np * HN * HN; t += blockDim.x) {
     const int d3 = t % HN, d2 = (t / HN) % HN, p = t / (HN * HN), d1 = d1_0 + p;
-    const double w = mg[HN] * (mg[d1] * mg[d2]) * mg[d3];
-    W[t] = (T)(w * (double)phit[((size_t)d1 * N + d2) * N + d3]);
+    if constexpr (is_twofold<T>::value) {
+      W[t] = (mgT[HN] * (mgT[d1] * mgT[d2]) * mgT[d3]) * phit[((size_t)d1 * N + d2) * N + d3];
+    } else {
+      const double w = mg[HN] * (mg[d1] * mg[d2]) * mg[d3];
+      W[t] = (T)(w * (double)phit[((size_t)d1 * N + d2) * N + d3]);
+    }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < np * HN; t += blockDim.x) {  // axis 3: pencil (p, d2)
@@ -412,12 +433,13 @@ __global__ void __launch_bounds__(256) k_axis1(Axis1Args a, const cpx<T>* __rest
       for (int k = gsub; k < HC; k += 8) Uc[c * HC + k] = pen.out(k, dct);
     }
     __syncthreads();
+    const T sc = (T)a.scale;
     for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
       int c = t % CW, r = t / CW;
       if (c0 + c < NC) {
         int k1 = centred<N>(freq_of_pos<N>(r));
         k1 = k1 < 0 ? -k1 : k1;
-        S[t] = cscale(S[t], (T)(Uc[c * HC + k1] * (T)a.scale));
+        S[t] = cscale(S[t], (T)(Uc[c * HC + k1] * sc));
       }
     }
     __syncthreads();

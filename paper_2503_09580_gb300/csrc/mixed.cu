@@ -377,7 +377,7 @@ lbo_status mixed_apply_op(lbo_solver* S, const double* v, double* out) {
     if (st != LBO_OK) return st;
   }
   // neighbours resampled in the operator plan's precision
-  transport(S, v, S->Lv, out, -1.0 / S->pb.kn, 0.0, S->shift, S->plan->precision == LBO_PREC_FP64);
+  transport(S, v, S->Lv, out, -1.0 / S->pb.kn, 0.0, S->shift, S->plan->precision != LBO_PREC_FP32);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LBO_OK : cuda_fail(e, "mixed operator");
 }

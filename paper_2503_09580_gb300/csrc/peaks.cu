@@ -7,8 +7,9 @@
 // overflow and no subnormal operands), enough independent work to hide the
 // pipe latency; the grid is SMs x 8 blocks of 256 threads (one full wave,
 // 64 warps per SM).  A store that depends on every chain keeps the work
-// alive.  Thread 0 of block 0 reads clock64() around its loop, which gives
-// the SM clock the peak was measured at.
+// alive.  Thread 0 of every block reads clock64() around its loop; the
+// longest loop over the blocks of the single wave, divided by the event
+// time, gives the SM clock the peak was measured at.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_fma_chains(T* sink, long long* cyc
 #pragma unroll
   for (int i = 0; i < kAcc; ++i) s += x[i];
   if (s == (T)-1) sink[blockIdx.x * kThreads + threadIdx.x] = s;  // never taken: x stays near 1
-  if (blockIdx.x == 0 && threadIdx.x == 0) *cycles = c1 - c0;
+  if (threadIdx.x == 0) atomicMax((unsigned long long*)cycles, (unsigned long long)(c1 - c0));
 }
 
 template <typename T>
@@ -53,6 +54,7 @@ lbo_status measure(cudaStream_t s, int sms, int iters, double* tflops, double* m
   double best = 0.0, clk = 0.0;
   k_fma_chains<T><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters / 8, a, b);  // warm-up
   for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    cudaMemsetAsync(d_cyc, 0, sizeof(long long), s);
     cudaEventRecord(e0, s);
     k_fma_chains<T><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters, a, b);
     cudaEventRecord(e1, s);
@@ -108,6 +110,6 @@ extern "C" lbo_status lbo_measure_alu_peaks(void* stream, double* fp32_tflops, d
   if (fp32_tflops) *fp32_tflops = f32;
   if (fp64_tflops) *fp64_tflops = f64;
   if (sm_count) *sm_count = sms;
-  if (sm_mhz) *sm_mhz = std::min(mhz32, mhz64);
+  if (sm_mhz) *sm_mhz = std::max(mhz32, mhz64);
   return LBO_OK;
 }

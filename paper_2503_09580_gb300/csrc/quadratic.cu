@@ -15,25 +15,11 @@
 #include <cmath>
 #include <vector>
 
-#include "lbo_internal.h"
-#include "lin_kernels.cuh"
+#include "quad_generic.cuh"
 
 namespace lbo {
 
-struct QuadState {
-  int p = 0;                   // hemisphere order of the cached rule
-  std::vector<double> sig, wm;  // M x 3, M
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  double* d_gsw = nullptr;      // device copy: radial nodes, sigma, w_m (fused path)
-  int gsw_p = -1;
-  const void* gsw_plan_tables = nullptr;
-};
-
 namespace {
-
-template <int N>
-struct PPCq { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : (N == 24 ? 4 : (N == 48 ? 2 : 1))); };
 
 // Product hemisphere rule: p Gauss-Legendre nodes in cos(theta) on (0, 1)
 // times 2p equispaced azimuths; weights sum to 1 (Eq. (2.13) carries 2 pi).
@@ -52,242 +38,6 @@ void hemisphere_rule(int p, std::vector<double>& sig, std::vector<double>& wm) {
       sig.push_back(mu);
       wm.push_back(0.5 * w[a] / na);
     }
-  }
-}
-
-// F (after all three forward passes) -> x E and x conj(E), inverse axis 1 of
-// both, for hemisphere node m0 + blockIdx.z: alpha_d = c sigma_(m,d), results
-// at W1, W2 + blockIdx.z * mstride.
-template <typename T, int N, int CW>
-__global__ void __launch_bounds__(256) k_axis1_phase(const cpx<T>* __restrict__ FH, cpx<T>* __restrict__ W1b,
-                                                     cpx<T>* __restrict__ W2b, const double* __restrict__ sig,
-                                                     int m0, double cj, size_t mstride) {
-  constexpr int HC = N / 2 + 1, NC = N * HC;
-  __shared__ __align__(16) cpx<T> S1[N * CW];
-  __shared__ __align__(16) cpx<T> S2[N * CW];
-  __shared__ cpx<double> mf[3 * N];  // per-axis factors, indexed by cyclic frequency
-  const int b = blockIdx.y, c0 = blockIdx.x * CW, m = m0 + blockIdx.z;
-  const double al1 = cj * sig[3 * m], al2 = cj * sig[3 * m + 1], al3 = cj * sig[3 * m + 2];
-  cpx<T>* W1 = W1b + blockIdx.z * mstride;
-  cpx<T>* W2 = W2b + blockIdx.z * mstride;
-  const size_t inst = (size_t)b * N * NC;
-  for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) {
-    const int d = t / N, k = t % N;
-    const double al = d == 0 ? al1 : (d == 1 ? al2 : al3);
-    if (k == N / 2) {
-      mf[t] = make_c(cos(al * (N / 2)), 0.0);
-    } else {
-      double s, c;
-      sincos(al * (double)centred<N>(k), &s, &c);
-      mf[t] = make_c(c, s);
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
-    const int c = t % CW, r = t / CW, col = c0 + c;
-    if (col < NC) {
-      const int p2 = col / HC, k3 = col % HC;
-      // 1/N^3 normalises the (unnormalised) inverse transforms of T+ and T-
-      const cpx<double> e = cscale(cmul(cmul(mf[freq_of_pos<N>(r)], mf[N + freq_of_pos<N>(p2)]), mf[2 * N + k3]),
-                                   1.0 / ((double)N * N * N));
-      const cpx<T> f = FH[inst + (size_t)r * NC + col];
-      const cpx<double> fd = make_c((double)f.x, (double)f.y);
-      const cpx<double> a = cmul(fd, e), bb = cmulc(fd, e);
-      S1[t] = make_c((T)a.x, (T)a.y);
-      S2[t] = make_c((T)bb.x, (T)bb.y);
-    } else {
-      S1[t] = make_c((T)0, (T)0);
-      S2[t] = make_c((T)0, (T)0);
-    }
-  }
-  __syncthreads();
-  smem_fft<T, N, true, true>(S1, CW, 1, CW);
-  smem_fft<T, N, true, true>(S2, CW, 1, CW);
-  for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
-    const int c = t % CW, r = t / CW;
-    if (c0 + c >= NC) continue;
-    const size_t o = inst + (size_t)r * NC + c0 + c;
-    W1[o] = S1[t];
-    W2[o] = S2[t];
-  }
-}
-
-// Inverse planes of W1, W2 -> T+, T-; P = 4 w_m T+ T- (real field, T) for
-// hemisphere node m0 + blockIdx.z (inputs and output offset by blockIdx.z).
-template <typename T, int N, int PPC>
-__global__ void __launch_bounds__(256) k_plane_inv_prod(const cpx<T>* __restrict__ W1b, const cpx<T>* __restrict__ W2b,
-                                                        T* __restrict__ Pb, const double* __restrict__ wm, int m0,
-                                                        size_t mstride, size_t pstride) {
-  const cpx<T>* W1 = W1b + blockIdx.z * mstride;
-  const cpx<T>* W2 = W2b + blockIdx.z * mstride;
-  T* P = Pb + blockIdx.z * pstride;
-  // 4 w_m: phi_j carries 4 pi^2 w_j B_j s_j / N^3, Eq. (2.14) needs 16 pi^2
-  const double scale = 4.0 * wm[m0 + blockIdx.z];
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int E = PlaneSmem<T, N, PPC>::A_ELEMS + PlaneSmem<T, N, PPC>::B_ELEMS;
-  cpx<T>* A1 = (cpx<T>*)smem_raw;
-  cpx<T>* B1 = A1 + PlaneSmem<T, N, PPC>::A_ELEMS;
-  cpx<T>* A2 = A1 + E;
-  cpx<T>* B2 = A2 + PlaneSmem<T, N, PPC>::A_ELEMS;
-  const int b = blockIdx.y, i1_0 = blockIdx.x * PPC;
-  plane_load_B<T, N, PPC>(B1, W1, b, i1_0);
-  plane_inverse_to_A<T, N, PPC>(A1, B1);
-  plane_load_B<T, N, PPC>(B2, W2, b, i1_0);
-  plane_inverse_to_A<T, N, PPC>(A2, B2);
-  const T sc = (T)scale;
-  for (int t = threadIdx.x; t < PPC * (N / 2) * N; t += blockDim.x) {
-    const int i3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
-    const cpx<T> zp = A1[(pp * (N / 2) + qq) * N + i3], zm = A2[(pp * (N / 2) + qq) * N + i3];
-    const size_t o = (((size_t)b * N + i1_0 + pp) * N + 2 * qq) * N + i3;
-    P[o] = sc * zp.x * zm.x;
-    P[o + N] = sc * zp.y * zm.y;
-  }
-}
-
-// Ps (+)= sum over the chunk's hemisphere nodes of P_m, in the order of m
-__global__ void k_sum_m_f(const float* __restrict__ Pm, float* __restrict__ Ps, int mb, size_t pstride, size_t total,
-                          int first) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    float acc = first ? Pm[t] : Ps[t] + Pm[t];
-    for (int z = 1; z < mb; ++z) acc += Pm[z * pstride + t];
-    Ps[t] = acc;
-  }
-}
-__global__ void k_sum_m_d(const double* __restrict__ Pm, double* __restrict__ Ps, int mb, size_t pstride,
-                          size_t total, int first) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    double acc = first ? Pm[t] : Ps[t] + Pm[t];
-    for (int z = 1; z < mb; ++z) acc += Pm[z * pstride + t];
-    Ps[t] = acc;
-  }
-}
-
-// hemisphere nodes per launch: all M, unless their buffers would pass 1 GiB
-int q_chunk(int B, int M, int N) {
-  const size_t H = (size_t)N * N * (N / 2 + 1), n3 = (size_t)N * N * N;
-  const size_t per_m = (size_t)B * (2 * H * 16 + n3 * 8);
-  const size_t cap = (size_t)1 << 30;
-  int mb = (int)std::max<size_t>(1, cap / std::max<size_t>(per_m, 1));
-  return std::min(mb, std::max(M, 1));
-}
-
-// out = Q+ - f u  (FP64)
-template <typename T, int N>
-__global__ void k_combine_q(const double* __restrict__ f, const T* __restrict__ Qp, const T* __restrict__ uu,
-                            double* __restrict__ out, size_t total) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x)
-    out[t] = (double)Qp[t] - f[t] * (double)uu[t];
-}
-
-template <typename K>
-void smem_attr(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <typename T, int N>
-lbo_status run_quadratic(lbo_plan* p, QuadState* qs, const double* f, double* out, int B) {
-  constexpr int PPC = PPCq<N>::v, CW = 32, HC = N / 2 + 1;
-  const size_t H = (size_t)N * N * HC, n3 = (size_t)N * N * N;
-  const int Q = 3 * (N / 2) * (N / 2) + 1;
-  cudaStream_t s = p->stream;
-  cpx<T>* FH = (cpx<T>*)qs->ws;
-  cpx<T>* W1 = FH + (size_t)B * H;
-  cpx<T>* W2 = W1 + (size_t)B * H;
-  cpx<T>* QH = W2 + (size_t)B * H;
-  T* Ps = (T*)(QH + (size_t)B * H);
-  T* R1 = Ps + (size_t)B * n3;
-  T* R2 = R1 + (size_t)B * n3;
-  const bool f64 = sizeof(T) == 8;
-  const T* phi = (const T*)(f64 ? (const void*)p->d_phi64 : (const void*)p->d_phi32);
-  const T* omg = (const T*)(f64 ? (const void*)p->d_omega64 : (const void*)p->d_omega32);
-  const size_t sm = PlaneSmem<T, N, PPC>::BYTES;
-  const dim3 gp(N / PPC, B), ga((N * HC + CW - 1) / CW, B), blk(256);
-  auto kf_real = k_plane_fwd<T, N, PPC, SRC_REAL64>;
-  auto kf_t = k_plane_fwd<T, N, PPC, SRC_REALT>;
-  auto ki_real = k_plane_inv<T, N, PPC, INV_TO_REAL>;
-  auto ka_fwd = k_axis1<T, N, CW, AX_FWD_STORE>;
-  auto ka_mult = k_axis1<T, N, CW, AX_FWD_MULT_INV>;
-  auto ka_acc = k_axis1<T, N, CW, AX_FWD_ACC>;
-  auto ka_inv = k_axis1<T, N, CW, AX_INV_STORE>;
-  auto ka_ph = k_axis1_phase<T, N, CW>;
-  auto kp_prod = k_plane_inv_prod<T, N, PPC>;
-  auto k_comb = k_combine_q<T, N>;
-  smem_attr(kf_real, sm);
-  smem_attr(kf_t, sm);
-  smem_attr(ki_real, sm);
-  smem_attr(kp_prod, 2 * sm);
-  PlaneArgs pa{};
-  pa.params = p->d_dummy_params;  // not read by these sources
-  pa.g = f;
-  pa.h = 2.0 * p->L / N;
-  int launches = 0;
-  // F = FFT(f)
-  LBO_LAUNCH(p, "q_plane_fwd_f", s, kf_real, gp, blk, sm, pa, W1);
-  Axis1Args ax{};
-  LBO_LAUNCH(p, "q_axis1_fwd", s, ka_fwd, ga, blk, 0, ax, W1, FH);
-  launches += 2;
-  const int M = (int)qs->wm.size();
-  const double pi = 3.141592653589793238462643383279502884;
-  // hemisphere nodes in chunks of MB per launch (grid z): their inverse
-  // transforms and products land in separate slots, summed in the order of m
-  const int MB = q_chunk(B, M, N);
-  cpx<T>* Wm1 = (cpx<T>*)(R2 + (size_t)B * n3);
-  cpx<T>* Wm2 = Wm1 + (size_t)MB * B * H;
-  T* Pm = (T*)(Wm2 + (size_t)MB * B * H);
-  const double* dsig = qs->d_gsw + p->J;
-  const double* dwm = dsig + 3 * M;
-  const size_t total = (size_t)B * n3;
-  const int cb = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
-  for (int j = 0; j < p->J; ++j) {
-    const double c = pi * p->gj[j] / (2.0 * p->L);
-    for (int m0 = 0; m0 < M; m0 += MB) {
-      const int mb = std::min(MB, M - m0);
-      LBO_LAUNCH(p, "q_axis1_phase", s, ka_ph, dim3(ga.x, B, mb), blk, 0, FH, Wm1, Wm2, dsig, m0, c,
-                 (size_t)B * H);
-      LBO_LAUNCH(p, "q_plane_inv_prod", s, kp_prod, dim3(gp.x, B, mb), blk, 2 * sm, Wm1, Wm2, Pm, dwm, m0,
-                 (size_t)B * H, total);
-      if constexpr (sizeof(T) == 8)
-        LBO_LAUNCH(p, "q_sum_m", s, k_sum_m_d, cb, 256, 0, Pm, Ps, mb, total, total, m0 == 0 ? 1 : 0);
-      else
-        LBO_LAUNCH(p, "q_sum_m", s, k_sum_m_f, cb, 256, 0, Pm, Ps, mb, total, total, m0 == 0 ? 1 : 0);
-      launches += 3;
-    }
-    pa.src = Ps;
-    LBO_LAUNCH(p, "q_plane_fwd_p", s, kf_t, gp, blk, sm, pa, W1);
-    Axis1Args a2{};
-    a2.table = phi + (size_t)j * Q;
-    a2.first = j == 0;
-    LBO_LAUNCH(p, "q_axis1_fwd_acc", s, ka_acc, ga, blk, 0, a2, W1, QH);
-    launches += 2;
-  }
-  LBO_LAUNCH(p, "q_axis1_inv", s, ka_inv, ga, blk, 0, ax, QH, QH);
-  LBO_LAUNCH(p, "q_plane_inv", s, ki_real, gp, blk, sm, pa, QH, R1);
-  // loss: f InvFFT(F omega)
-  Axis1Args a3{};
-  a3.table = omg;
-  LBO_LAUNCH(p, "q_plane_fwd_f", s, kf_real, gp, blk, sm, pa, W1);
-  LBO_LAUNCH(p, "q_axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
-  LBO_LAUNCH(p, "q_plane_inv", s, ki_real, gp, blk, sm, pa, W1, R2);
-  LBO_LAUNCH(p, "q_combine", s, k_comb, cb, 256, 0, f, R1, R2, out, total);
-  launches += 6;
-  if (p->mass_fix || p->moment_fix) {
-    lbo_status st = launch_fixes(p, out, B, N, pa.h, s, &launches);
-    if (st != LBO_OK) return st;
-  }
-  p->last_launches = launches;
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "quadratic launch");
-}
-
-template <typename T>
-lbo_status dispatch_q(lbo_plan* p, QuadState* qs, const double* f, double* out, int B) {
-  switch (p->N) {
-    case 16: return run_quadratic<T, 16>(p, qs, f, out, B);
-    case 24: return run_quadratic<T, 24>(p, qs, f, out, B);
-    case 32: return run_quadratic<T, 32>(p, qs, f, out, B);
-    case 48: return run_quadratic<T, 48>(p, qs, f, out, B);
-    case 64: return run_quadratic<T, 64>(p, qs, f, out, B);
-    default: return LBO_EUNSUPPORTED;
   }
 }
 
@@ -318,9 +68,10 @@ lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int
   const int G = fused ? (p->jgroups > 0 ? std::min(p->jgroups, p->J) : std::min(fused32_default_groups(B), p->J)) : 0;
   const size_t N = p->N, H = N * N * (N / 2 + 1), n3 = N * N * N;
   const int M = (int)qs->wm.size();
-  const size_t MB = fused ? 0 : (size_t)q_chunk(B, M, (int)N);
+  const size_t rb = generic_real_bytes(p->precision);
+  const size_t MB = fused ? 0 : (size_t)q_chunk(B, M, (int)N, rb);
   const size_t need = fused ? quad_fused32_workspace_bytes(B, G)
-                            : (size_t)B * (4 * H * 16 + 3 * n3 * 8) + MB * (size_t)B * (2 * H * 16 + n3 * 8);
+                            : (size_t)B * (4 * H * 2 * rb + 3 * n3 * rb) + MB * (size_t)B * (2 * H * 2 * rb + n3 * rb);
   if (need > qs->ws_bytes) {
     if (qs->ws) cudaFree(qs->ws);
     qs->ws = nullptr;
@@ -356,7 +107,11 @@ lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int
     p->last_launches = launches;
     return st;
   }
-  return p->precision == LBO_PREC_FP64 ? dispatch_q<double>(p, qs, f, out, B) : dispatch_q<float>(p, qs, f, out, B);
+  switch (p->precision) {
+    case LBO_PREC_FP64: return dispatch_q<double>(p, qs, f, out, B, p->d_phi64, p->d_omega64);
+    case LBO_PREC_FP32: return dispatch_q<float>(p, qs, f, out, B, p->d_phi32, p->d_omega32);
+    default: return run_quadratic_twofold(p, qs, f, out, B);
+  }
 }
 
 }  // namespace lbo

@@ -1,0 +1,164 @@
+"""The two-fold precisions through the C ABI: FP32X2 (pairs of FP32 numbers,
+about 48 significant bits on the FP32 pipe) and FP64X2 (pairs of FP64
+numbers, about 106 bits), against the CPU oracle.
+
+Bounds.  The FFT form of Algorithm 1 loses accuracy in proportion to the
+size of the ratio r = g/M it transforms (Sec. 3.3); per instance the stated
+bound is 4 u rms(r) (u the unit roundoff of the transform arithmetic:
+2^-48 for FP32X2, 2^-105 for FP64X2; rms over the grid, r = 0 where cut),
+and 1e-12 on inputs g = M p (noise-free) for both forms.
+
+The higher-precision convolution of Sec. 3.4: without the cut-off of
+Eq. (3.9) the FP64 transforms of a bimodal gas (a cold Maxwellian plus a
+hotter population, whose ratio to the cold one reaches 3e19 at the box
+corners) lose every digit, while the direct sums of Eq. (3.8) do not; FP64X2
+transforms recover them to ~1e-14 without the cut-off, whose own error on
+this input is 5e-4."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import grid
+from oracle.direct import direct_linearized
+from oracle.linearized import Tables, apply_linearized, maxwellians
+from oracle.quadratic import apply_quadratic
+from oracle.quadrature import hemisphere_rule
+from paper_2503_09580_gb300 import lbo, workloads
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+U_F32X2, U_F64X2 = 2.0 ** -48, 2.0 ** -105
+
+
+def run(plan, params, g):
+    tp, tg = torch.from_numpy(params).to(DEV), torch.from_numpy(g).to(DEV)
+    out = torch.empty_like(tg)
+    plan.apply_linearized(tp, tg, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def errs(got, ref):
+    return np.array([np.abs(got[b] - ref[b]).max() / np.abs(ref[b]).max() for b in range(ref.shape[0])])
+
+
+def rms_r(params, g, n, L, cutoff=True, eps=1e-9):
+    a = workloads.velocity_axis(n, L)
+    out = []
+    for b in range(params.shape[0]):
+        rho, u1, u2, u3, th = params[b]
+        d2 = (a[:, None, None] - u1) ** 2 + (a[None, :, None] - u2) ** 2 + (a[None, None, :] - u3) ** 2
+        M = rho * (2 * np.pi * th) ** -1.5 * np.exp(-d2 / (2 * th))
+        keep = d2 / (2 * th) <= np.log(1 / eps) - 1.5 * np.log(2 * np.pi * th) if cutoff else np.ones_like(d2, bool)
+        r = np.where(keep, g[b] / M, 0.0)
+        out.append(np.sqrt(np.mean(r * r)))
+    return np.array(out)
+
+
+_TAB = {}
+
+
+def tables(n, L, om):
+    if (n, L, om) not in _TAB:
+        _TAB[(n, L, om)] = Tables(n, L, om, n)
+    return _TAB[(n, L, om)]
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_fp32x2_noise_free_matches_oracle(n):
+    L = 8.0
+    params, g = workloads.batched_instances(n, L, batch=3, seed=41, noise=0.0)
+    got = run(lbo.Plan(n, L, 0.5, n, precision="fp32x2"), params, g)
+    e = errs(got, apply_linearized(tables(n, L, 0.5), params, g))
+    print("fp32x2 n=%d noise-free errors" % n, e)
+    assert np.all(e <= 1e-12)
+    assert np.all(e <= 4 * U_F32X2 * rms_r(params, g, n, L))
+
+
+@pytest.mark.parametrize("n", [24, 32, 48, 64])
+def test_fp32x2_noisy_within_stated_bound(n):
+    """The benchmark recipe (per-instance Maxwellians, quartic + 1e-3 noise)
+    at every built size of the pairs of FP32."""
+    L = 8.0
+    params, g = workloads.batched_instances(n, L, batch=1 if n == 64 else 2, seed=42, noise=1e-3)
+    got = run(lbo.Plan(n, L, 0.5, n, precision="fp32x2"), params, g)
+    e = errs(got, apply_linearized(tables(n, L, 0.5), params, g))
+    bound = 4 * U_F32X2 * rms_r(params, g, n, L)
+    print("fp32x2 n=%d noisy errors" % n, e, "bounds", bound)
+    assert np.all(e <= bound)
+
+
+def test_fp32x2_close_to_fp64_on_the_benchmark_batch():
+    """A larger batch against the FP64 path on the GPU (both within their
+    bounds of the oracle, so within the sum of the two of each other)."""
+    n, L = 32, 8.0
+    params, g = workloads.batched_instances(n, L, batch=16, seed=43, noise=1e-3)
+    a = run(lbo.Plan(n, L, 0.74, n, precision="fp32x2"), params, g)
+    b = run(lbo.Plan(n, L, 0.74, n), params, g)
+    bound = 4 * (U_F32X2 + 2.0 ** -53) * rms_r(params, g, n, L)
+    assert np.all(errs(a, b) <= bound)
+
+
+def bimodal(n, L, theta_hot=2.0):
+    """A cold Maxwellian (rho 1, small drift, theta 1) perturbed by a hotter
+    population (rho 0.2, theta 2) minus as much cold mass, plus a small
+    polynomial part; r = g/M of the cold Maxwellian reaches ~3e19."""
+    params = np.array([[1.0, 0.1, -0.2, 0.05, 1.0]])
+    M, *_ = maxwellians(n, L, 1.0, params[0, 1:4], 1.0)
+    Mh, *_ = maxwellians(n, L, 0.2, np.zeros(3), theta_hot)
+    v1, v2, v3 = grid.velocity_grid(n, L)
+    g_cyc = M * (0.3 * v1 - 0.2 * v2 * v3) + (Mh - 0.2 * M)
+    return params, grid.to_centred(g_cyc)[None], g_cyc
+
+
+def test_fp64x2_without_cutoff_recovers_the_direct_sums():
+    n, L = 16, 8.0
+    params, g, g_cyc = bimodal(n, L)
+    tab = tables(n, L, 0.5)
+    ref = grid.to_centred(direct_linearized(tab, 1.0, params[0, 1:4], 1.0, g_cyc, cutoff=False))[None]
+    e64 = errs(run(lbo.Plan(n, L, 0.5, n, cutoff=0), params, g), ref)[0]
+    e128 = errs(run(lbo.Plan(n, L, 0.5, n, precision="fp64x2", cutoff=0), params, g), ref)[0]
+    ecut = errs(run(lbo.Plan(n, L, 0.5, n), params, g), ref)[0]
+    print("no cut-off: FP64 %.2e, FP64X2 %.2e; FP64 with the cut-off %.2e" % (e64, e128, ecut))
+    assert e64 > 1.0          # FP64 transforms: no digit left (Sec. 3.3)
+    assert e128 <= 1e-12      # pairs of FP64: the direct sums' accuracy
+    assert 1e-5 < ecut < 1e-3  # the cut-off's own error on this input
+
+
+def test_fp64x2_noise_free_n32_matches_oracle():
+    n, L = 32, 8.0
+    params, g = workloads.batched_instances(n, L, batch=2, seed=44, noise=0.0)
+    got = run(lbo.Plan(n, L, 1.0, n, precision="fp64x2"), params, g)
+    e = errs(got, apply_linearized(tables(n, L, 1.0), params, g))
+    assert np.all(e <= 1e-12)
+
+
+def test_fp64x2_unbuilt_size_is_refused():
+    n, L = 24, 8.0
+    params, g = workloads.batched_instances(n, L, batch=1, seed=45, noise=0.0)
+    with pytest.raises(lbo.LboError) as ei:
+        run(lbo.Plan(n, L, 0.5, n, precision="fp64x2"), params, g)
+    assert ei.value.status == 7
+
+
+@pytest.mark.parametrize("precision,n", [("fp32x2", 16), ("fp32x2", 32), ("fp64x2", 16)])
+def test_quadratic_twofold_matches_oracle(precision, n):
+    L, p = 8.0, 2
+    params, g = workloads.batched_instances(n, L, batch=2, seed=46, noise=0.0)
+    a = workloads.velocity_axis(n, L)
+    f = []
+    for b in range(2):
+        rho, u1, u2, u3, th = params[b]
+        d2 = (a[:, None, None] - u1) ** 2 + (a[None, :, None] - u2) ** 2 + (a[None, None, :] - u3) ** 2
+        f.append(rho * (2 * np.pi * th) ** -1.5 * np.exp(-d2 / (2 * th)) + 0.3 * g[b])
+    f = np.stack(f)
+    plan = lbo.Plan(n, L, 0.5, n, hemisphere_p=p, precision=precision)
+    tf = torch.from_numpy(f).to(DEV)
+    out = torch.empty_like(tf)
+    plan.apply_quadratic(tf, out)
+    torch.cuda.synchronize()
+    sig, w = hemisphere_rule(p)
+    e = errs(out.cpu().numpy(), apply_quadratic(tables(n, L, 0.5), f, sig, w))
+    print("Q %s n=%d errors" % (precision, n), e)
+    assert np.all(e <= 1e-12)
