@@ -108,6 +108,24 @@ lbo_status lbo_plan_set_stream(lbo_plan *plan, void *stream);
 lbo_status lbo_apply_linearized(lbo_plan *plan, const double *maxwellian_params,
                                 const double *g, double *out, int batch);
 
+/* Cache the factors of Algorithm 1 that depend on the background
+ * Maxwellians only: u^_j = FFT(M^g phit_j) for every radial node and the
+ * loss factor InvFFT(FFT(M) omega) (its precomputation of the gain kernel
+ * and the second loss convolution, Sec. 3.5).  Later lbo_apply_linearized
+ * calls with the same maxwellian_params pointer and batch, the same
+ * precision and the same kernel set reuse them instead of recomputing them
+ * (for the fused FP32 kernels only u^_j is cached): the Krylov products of
+ * one Newton step share their Maxwellians.  params: device pointer,
+ * batch*5 doubles; its contents must not change while the cache is in use
+ * (the library cannot see such a change: call again, or drop the cache).
+ * params = NULL or batch = 0 drops the cache (its device buffers are kept
+ * for reuse).  Allocates device memory on first use and when a larger batch
+ * needs it: J*batch*(N/2+1)^3 + batch*N^3 reals of the transform precision.
+ * Asynchronous on the plan's stream.  Errors: LBO_EINVAL (bad plan, host
+ * pointer), LBO_ENOMEM, LBO_ECUDA, LBO_EUNSUPPORTED (N not built for the
+ * precision). */
+lbo_status lbo_plan_cache_maxwellians(lbo_plan *plan, const double *maxwellian_params, int batch);
+
 /* Quadratic collision operator Q(f,f) in the M-point hemisphere-quadrature
  * form of Eq. (2.14) with the plan's radial rule and a product hemisphere
  * rule of M = 2p^2 points.  f, out: batch*N^3 doubles, no aliasing. */

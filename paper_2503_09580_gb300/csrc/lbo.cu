@@ -187,6 +187,7 @@ static lbo_status build_tables(lbo_plan* p) {
     return s2;
   }
   p->tables_dirty = false;
+  p->mc_valid = false;
   return LBO_OK;
 }
 
@@ -281,14 +282,31 @@ static lbo_status build_phit(lbo_plan* p, const double* d_stab, T* d_phit) {
 }
 
 template <typename T>
-static lbo_status dispatch_lin(lbo_plan* p, const double* params, const double* g, double* out, int B) {
+static GenericTables<T> plain_tables(const lbo_plan* p) {
   const bool f64 = sizeof(T) == 8;
   GenericTables<T> tb;
   tb.phi = (const T*)(f64 ? (const void*)p->d_phi64 : (const void*)p->d_phi32);
   tb.omega = (const T*)(f64 ? (const void*)p->d_omega64 : (const void*)p->d_omega32);
   tb.phit = (const T*)(f64 ? (const void*)p->d_phit64 : (const void*)p->d_phit32);
   tb.dct = (const T*)(f64 ? (const void*)p->d_dct64 : (const void*)p->d_dct32);
-  return dispatch_generic<T>(p, tb, params, g, out, B, p->ws);
+  return tb;
+}
+
+template <typename T>
+static lbo_status dispatch_lin(lbo_plan* p, const double* params, const double* g, double* out, int B,
+                               const void* cuh, const void* cw) {
+  GenericCache<T> mc{(const T*)cuh, (const T*)cw};
+  return dispatch_generic<T>(p, plain_tables<T>(p), params, g, out, B, p->ws, cuh ? &mc : nullptr);
+}
+
+// kernel set of an apply call: 1 the fused FP32 kernels (N = 32), 0 generic
+static int kernel_path(const lbo_plan* p) {
+  return p->precision == LBO_PREC_FP32 && p->N == 32 && p->kernel_choice == 0 ? 1 : 0;
+}
+
+// bytes of one real number of the generic path's transform arithmetic
+static size_t transform_real_bytes(int prec) {
+  return prec == LBO_PREC_FP32 ? 4 : (prec == LBO_PREC_FP64X2 ? 16 : 8);
 }
 
 static bool is_device_ptr(const void* ptr) {
@@ -422,20 +440,26 @@ lbo_status lbo_apply_linearized(lbo_plan* p, const double* params, const double*
     dg = p->stage_in;
     dout = p->stage_out;
   }
-  if (p->precision == LBO_PREC_FP32 && p->N == 32 && p->kernel_choice == 0) {
+  // the Maxwellian cache, if it was made for exactly this call's Maxwellians
+  const int path = kernel_path(p);
+  const bool cached = p->mc_valid && p->mc_params == dp && p->mc_batch == batch && p->mc_precision == p->precision &&
+                      p->mc_path == path;
+  const void* cuh = cached ? p->mc_uh : nullptr;
+  const void* cw = cached ? p->mc_w : nullptr;
+  if (path == 1) {
     int G = p->jgroups > 0 ? std::min(p->jgroups, p->J) : std::min(fused32_default_groups(batch), p->J);
     st = ensure_ws_bytes(p, fused32_workspace_bytes(batch, G, p->J));
     if (st != LBO_OK) return st;
     int launches = 0;
-    st = run_linearized_fused32(p, dp, dg, dout, batch, p->ws, G, &launches);
+    st = run_linearized_fused32(p, dp, dg, dout, batch, p->ws, G, &launches, (const float*)cuh);
     if (st == LBO_OK && (p->mass_fix || p->moment_fix))
       st = launch_fixes(p, dout, batch, p->N, 2.0 * p->L / p->N, p->stream, &launches);
     p->last_launches = launches;
   } else if (is_twofold_precision(p->precision)) {
-    st = run_linearized_twofold(p, dp, dg, dout, batch);
+    st = run_linearized_twofold(p, dp, dg, dout, batch, cuh, cw);
   } else {
-    st = p->precision == LBO_PREC_FP64 ? dispatch_lin<double>(p, dp, dg, dout, batch)
-                                       : dispatch_lin<float>(p, dp, dg, dout, batch);
+    st = p->precision == LBO_PREC_FP64 ? dispatch_lin<double>(p, dp, dg, dout, batch, cuh, cw)
+                                       : dispatch_lin<float>(p, dp, dg, dout, batch, cuh, cw);
   }
   if (st != LBO_OK) return st;
   if (!dev) {
@@ -443,6 +467,54 @@ lbo_status lbo_apply_linearized(lbo_plan* p, const double* params, const double*
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
   }
+  return LBO_OK;
+}
+
+lbo_status lbo_plan_cache_maxwellians(lbo_plan* p, const double* params, int batch) {
+  if (!p || batch < 0) return LBO_EINVAL;
+  p->mc_valid = false;
+  if (!params || batch == 0) return LBO_OK;  // dropped; the buffers are kept for reuse
+  if (!is_device_ptr(params)) {
+    set_error_text("Maxwellian cache: params must be a device pointer");
+    return LBO_EINVAL;
+  }
+  if (p->tables_dirty) {
+    lbo_status st = build_tables(p);
+    if (st != LBO_OK) return st;
+  }
+  const int path = kernel_path(p);
+  const size_t N = p->N, HC = N / 2 + 1, n3 = N * N * N;
+  const size_t rb = transform_real_bytes(p->precision);
+  const size_t uh_bytes = path == 1 ? fused32_uhat_bytes(batch, p->J) : (size_t)p->J * batch * HC * HC * HC * rb;
+  const size_t w_bytes = path == 1 ? 0 : (size_t)batch * n3 * rb;
+  auto grow = [&](void*& ptr, size_t& cap, size_t need) -> lbo_status {
+    if (need <= cap) return LBO_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    if (cudaMalloc(&ptr, need) != cudaSuccess) {
+      cudaGetLastError();
+      set_error_text("Maxwellian cache allocation");
+      return LBO_ENOMEM;
+    }
+    cap = need;
+    return LBO_OK;
+  };
+  lbo_status st = grow(p->mc_uh, p->mc_uh_bytes, uh_bytes);
+  if (st == LBO_OK && w_bytes) st = grow(p->mc_w, p->mc_w_bytes, w_bytes);
+  if (st == LBO_OK && path == 0) st = ensure_workspace(p, batch);
+  if (st != LBO_OK) return st;
+  if (path == 1) st = precompute_fused32(p, params, batch, (float*)p->mc_uh);
+  else if (is_twofold_precision(p->precision)) st = precompute_twofold(p, params, batch, p->mc_uh, p->mc_w);
+  else if (p->precision == LBO_PREC_FP64)
+    st = dispatch_precompute<double>(p, plain_tables<double>(p), params, batch, p->ws, p->mc_uh, p->mc_w);
+  else st = dispatch_precompute<float>(p, plain_tables<float>(p), params, batch, p->ws, p->mc_uh, p->mc_w);
+  if (st != LBO_OK) return st;
+  p->mc_params = params;
+  p->mc_batch = batch;
+  p->mc_precision = p->precision;
+  p->mc_path = path;
+  p->mc_valid = true;
   return LBO_OK;
 }
 
@@ -492,6 +564,8 @@ int lbo_plan_last_launches(const lbo_plan* p) { return p ? p->last_launches : 0;
 void lbo_plan_destroy(lbo_plan* p) {
   if (!p) return;
   free_tables(p);
+  if (p->mc_uh) cudaFree(p->mc_uh);
+  if (p->mc_w) cudaFree(p->mc_w);
   if (p->ws) cudaFree(p->ws);
   if (p->stage_in) cudaFree(p->stage_in);
   if (p->stage_out) cudaFree(p->stage_out);

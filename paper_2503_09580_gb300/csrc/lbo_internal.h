@@ -29,6 +29,13 @@ struct lbo_plan {
   // two-fold tables {phit, phi, omega, dct}, built on first use (lin_twofold.cu)
   void* d_x2f[4] = {nullptr, nullptr, nullptr, nullptr};  // pairs of FP32
   void* d_x2d[4] = {nullptr, nullptr, nullptr, nullptr};  // pairs of FP64
+  // cache of the Maxwellian-dependent factors (lbo_plan_cache_maxwellians):
+  // valid for apply calls with this params pointer, batch, precision and path
+  const double* mc_params = nullptr;
+  int mc_batch = 0, mc_precision = -1, mc_path = -1;
+  bool mc_valid = false;
+  void *mc_uh = nullptr, *mc_w = nullptr;
+  size_t mc_uh_bytes = 0, mc_w_bytes = 0;
   // workspace of the generic path
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -109,7 +116,9 @@ void free_quadratic(lbo_plan* p);
 void gauss_legendre(int J, std::vector<double>& x, std::vector<double>& w);
 lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int B);
 // two-fold precisions FP32X2 / FP64X2 (lin_twofold.cu)
-lbo_status run_linearized_twofold(lbo_plan* p, const double* params, const double* g, double* out, int B);
+lbo_status run_linearized_twofold(lbo_plan* p, const double* params, const double* g, double* out, int B,
+                                  const void* cache_uh = nullptr, const void* cache_w = nullptr);
+lbo_status precompute_twofold(lbo_plan* p, const double* params, int B, void* uh, void* w);
 lbo_status twofold_tables(lbo_plan* p, const void** phi, const void** omega, const void** phit, const void** dct);
 void free_twofold_tables(lbo_plan* p);
 inline bool is_twofold_precision(int prec) { return prec == LBO_PREC_FP32X2 || prec == LBO_PREC_FP64X2; }
@@ -119,7 +128,9 @@ inline size_t generic_real_bytes(int prec) { return prec == LBO_PREC_FP64X2 ? 16
 size_t fused32_workspace_bytes(int B, int G, int J);
 int fused32_default_groups(int B);
 lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const double* g, double* out, int B,
-                                  void* ws, int G, int* launches);
+                                  void* ws, int G, int* launches, const float* cached_uhat = nullptr);
+size_t fused32_uhat_bytes(int B, int J);
+lbo_status precompute_fused32(lbo_plan* p, const double* params, int B, float* uhat);
 size_t quad_fused32_workspace_bytes(int B, int G);
 lbo_status run_quadratic_fused32(lbo_plan* p, const double* f, double* out, int B, void* ws, const double* d_gsw,
                                  int M, int G, int* launches);

@@ -466,8 +466,29 @@ int fused32_default_groups(int B) {
   return g < 1 ? 1 : (g > 8 ? 8 : g);
 }
 
+size_t fused32_uhat_bytes(int B, int J) { return (size_t)B * J * U_STRIDE * sizeof(float); }
+
+// u^_j of every instance and radial node into uhat ([B][J][U_STRIDE]), for
+// the Maxwellian cache: k_f32_uhat alone.
+lbo_status precompute_fused32(lbo_plan* p, const double* params, int B, float* uhat) {
+  cudaError_t e = upload_twiddles();
+  if (e == cudaSuccess) e = upload_dct();
+  if (e != cudaSuccess) return cuda_fail(e, "fused32 twiddles");
+  FusedArgs a{};
+  a.params = params;
+  a.phit = p->d_phit32;
+  a.uhat = uhat;
+  a.h = 2.0 * p->L / F_N;
+  a.J = p->J;
+  a.B = B;
+  LBO_LAUNCH(p, "cache_f32_uhat", p->stream, k_f32_uhat, dim3(a.J, B), U_THREADS, 0, a);
+  p->last_launches = 1;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "fused32 cache launch");
+}
+
 lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const double* g, double* out, int B,
-                                  void* ws, int G, int* launches) {
+                                  void* ws, int G, int* launches, const float* cached_uhat) {
   cudaError_t e = upload_twiddles();
   if (e == cudaSuccess) e = upload_dct();
   if (e != cudaSuccess) return cuda_fail(e, "fused32 twiddles");
@@ -499,10 +520,15 @@ lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const doubl
   a.Q = 3 * 16 * 16 + 1;
   cudaStream_t s = p->stream;
   LBO_LAUNCH(p, "f32_head", s, k_f32_head, B, F_THREADS, sm, a);
-  LBO_LAUNCH(p, "f32_uhat", s, k_f32_uhat, dim3(a.J, B), U_THREADS, 0, a);
+  if (cached_uhat) {
+    a.uhat = const_cast<float*>(cached_uhat);  // read only from here on
+  } else {
+    LBO_LAUNCH(p, "f32_uhat", s, k_f32_uhat, dim3(a.J, B), U_THREADS, 0, a);
+    *launches += 1;
+  }
   LBO_LAUNCH(p, "f32_gain", s, k_f32_gain, dim3(G + 1, B), F_THREADS, sm, a);
   LBO_LAUNCH(p, "f32_tail", s, k_f32_tail, B, F_THREADS, sm, a);
-  *launches += 4;
+  *launches += 3;
   e = cudaGetLastError();
   return e == cudaSuccess ? LBO_OK : cuda_fail(e, "fused32 launch");
 }

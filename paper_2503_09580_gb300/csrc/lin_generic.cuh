@@ -33,9 +33,21 @@ struct PlanePPC { static constexpr int v = N == 16 ? 8 : (N == 32 ? 4 : (N == 24
 // M^h psi_j, psi^_j = FFT, L^+ += phi_j psi^_j; L+ = InvFFT(L^+); the loss
 // term; the combination; the optional fixes.  ws: 3 half spectra + 3 real
 // fields + the u^_j octant planes per instance, in T.
+//
+// Maxwellian cache (mc, may be null): u^_j of every radial node as whole
+// octants ([J][B][(N/2+1)^3]) and the loss factor w = InvFFT(M^ omega)
+// ([B][N^3]), computed by precompute_maxwellian_generic for these params;
+// with it the u^_j DCTs and the transforms of w are not repeated.
+template <typename T>
+struct GenericCache {
+  const T* uh;
+  const T* w;
+};
+
 template <typename T, int N>
 static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb, const double* params,
-                                         const double* g, double* out, int B, void* ws_raw) {
+                                         const double* g, double* out, int B, void* ws_raw,
+                                         const GenericCache<T>* mc = nullptr) {
   constexpr int PPC = PlanePPC<N>::v, CW = 32, HC = N / 2 + 1;
   const size_t H = (size_t)N * N * HC, n3 = (size_t)N * N * N;
   cudaStream_t s = p->stream;
@@ -74,6 +86,7 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
   auto ka_acc = k_axis1<T, N, CW, AX_FWD_ACC>;
   auto ka_inv = k_axis1<T, N, CW, AX_INV_STORE>;
   auto ka_uhat = k_axis1<T, N, CW, AX_UHAT_INV>;
+  auto ka_uhat_c = k_axis1<T, N, CW, AX_UHAT_CACHED>;
   constexpr int PL = UhatPlanes<N>::PL;  // octant planes per block
   auto k_up = k_uhat_planes<T, N, PL>;
   const size_t sm_up = sizeof(T) * ((size_t)PL * HC * HC + (size_t)HC * (N / 4));
@@ -85,16 +98,24 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
   Axis1Args ax{};
   LBO_LAUNCH(p, "axis1_fwd", s, ka_fwd, ga, blk, 0, ax, W1, RH);
   launches += 2;
+  const size_t HC3 = (size_t)HC * HC * HC;
   for (int j = 0; j < p->J; ++j) {
-    // u^_j = FFT(M^g phit_j), real and even: DCT-I of the octant, axes 3 and 2
-    LBO_LAUNCH(p, "uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params, phit + (size_t)j * n3,
-               dct, pa.h, UP);
-    // psi_j = InvFFT(u^_j r^), u^_j finished along axis 1 in the same kernel
     Axis1Args a1{};
-    a1.uplanes = UP;
     a1.dct = dct;
     a1.scale = 1.0 / (double)n3;
-    LBO_LAUNCH(p, "axis1_uhat_inv", s, ka_uhat, ga, blk, 0, a1, RH, W1);
+    if (mc) {
+      // psi_j = InvFFT(u^_j r^), u^_j from the cache
+      a1.uplanes = mc->uh + (size_t)j * B * HC3;
+      LBO_LAUNCH(p, "axis1_uhat_cached_inv", s, ka_uhat_c, ga, blk, 0, a1, RH, W1);
+      launches -= 1;
+    } else {
+      // u^_j = FFT(M^g phit_j), real and even: DCT-I of the octant, axes 3 and 2
+      LBO_LAUNCH(p, "uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params,
+                 phit + (size_t)j * n3, dct, pa.h, UP);
+      // psi_j = InvFFT(u^_j r^), u^_j finished along axis 1 in the same kernel
+      a1.uplanes = UP;
+      LBO_LAUNCH(p, "axis1_uhat_inv", s, ka_uhat, ga, blk, 0, a1, RH, W1);
+    }
     // psi_j <- M^h psi_j ; psi^_j = FFT(psi_j)
     LBO_LAUNCH(p, "plane_inv_mh_fwd", s, ki_mh, gp, blk, sm, pa, W1, (T*)nullptr);
     // L^+ += phi_j psi^_j
@@ -113,10 +134,16 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
   LBO_LAUNCH(p, "plane_fwd_g", s, kf_real, gp, blk, sm, pa, W1);
   LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
   LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R2);
-  LBO_LAUNCH(p, "plane_fwd_maxw", s, kf_maxw, gp, blk, sm, pa, W1);
-  LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
-  LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R3);
-  LBO_LAUNCH(p, "combine", s, k_comb, dim3(N, B), 256, 0, params, g, R1, R2, R3, out, pa.h, pa.log_inv_eps);
+  const T* ww = R3;
+  if (mc) {
+    ww = mc->w;
+    launches -= 3;
+  } else {
+    LBO_LAUNCH(p, "plane_fwd_maxw", s, kf_maxw, gp, blk, sm, pa, W1);
+    LBO_LAUNCH(p, "axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
+    LBO_LAUNCH(p, "plane_inv", s, ki_real, gp, blk, sm, pa, W1, R3);
+  }
+  LBO_LAUNCH(p, "combine", s, k_comb, dim3(N, B), 256, 0, params, g, R1, R2, ww, out, pa.h, pa.log_inv_eps);
   launches += 9;
   if (p->mass_fix || p->moment_fix) {
     lbo_status st = launch_fixes(p, out, B, N, pa.h, s, &launches);
@@ -128,15 +155,68 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
   return LBO_OK;
 }
 
+// The Maxwellian-dependent factors of Algorithm 1 for the instances of
+// params: u^_j = FFT(M^g phit_j) of every radial node as whole octants
+// (k_uhat_planes for axes 3 and 2, k_uhat_finish for axis 1) into uh
+// ([J][B][(N/2+1)^3]), and w = InvFFT(FFT(M) omega) into w ([B][N^3]).
+// ws: the workspace of run_linearized_generic.
+template <typename T, int N>
+static lbo_status precompute_maxwellian_generic(lbo_plan* p, const GenericTables<T>& tb, const double* params,
+                                                int B, void* ws_raw, T* uh, T* w) {
+  constexpr int PPC = PlanePPC<N>::v, CW = 32, HC = N / 2 + 1;
+  const size_t H = (size_t)N * N * HC, n3 = (size_t)N * N * N, HC3 = (size_t)HC * HC * HC;
+  cudaStream_t s = p->stream;
+  cpx<T>* W1 = (cpx<T>*)ws_raw + (size_t)B * H;
+  const size_t sm = PlaneSmem<T, N, PPC>::BYTES;
+  const dim3 gp(N / PPC, B), ga((N * HC + CW - 1) / CW, B), blk(256);
+  set_smem(k_plane_fwd<T, N, PPC, SRC_MAXW>, sm);
+  set_smem(k_plane_inv<T, N, PPC, INV_TO_REAL>, sm);
+  constexpr int PL = UhatPlanes<N>::PL;
+  auto k_up = k_uhat_planes<T, N, PL>;
+  const size_t sm_up = sizeof(T) * ((size_t)PL * HC * HC + (size_t)HC * (N / 4));
+  set_smem(k_up, sm_up);
+  PlaneArgs pa{};
+  pa.params = params;
+  pa.h = 2.0 * p->L / N;
+  pa.log_inv_eps = std::log(1.0 / p->eps);
+  for (int j = 0; j < p->J; ++j) {
+    T* dst = uh + (size_t)j * B * HC3;
+    LBO_LAUNCH(p, "cache_uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params,
+               tb.phit + (size_t)j * n3, tb.dct, pa.h, dst);
+    LBO_LAUNCH(p, "cache_uhat_finish", s, (k_uhat_finish<T, N>), B, blk, 0, dst, tb.dct);
+  }
+  Axis1Args a3{};
+  a3.table = tb.omega;
+  LBO_LAUNCH(p, "cache_plane_fwd_maxw", s, (k_plane_fwd<T, N, PPC, SRC_MAXW>), gp, blk, sm, pa, W1);
+  LBO_LAUNCH(p, "cache_axis1_fwd_mul_inv", s, (k_axis1<T, N, CW, AX_FWD_MULT_INV>), ga, blk, 0, a3, W1, W1);
+  LBO_LAUNCH(p, "cache_plane_inv", s, (k_plane_inv<T, N, PPC, INV_TO_REAL>), gp, blk, sm, pa, W1, w);
+  p->last_launches = 2 * p->J + 3;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "Maxwellian cache launch");
+}
+
 template <typename T>
 static lbo_status dispatch_generic(lbo_plan* p, const GenericTables<T>& tb, const double* params, const double* g,
-                                  double* out, int B, void* ws) {
+                                  double* out, int B, void* ws, const GenericCache<T>* mc = nullptr) {
   switch (p->N) {
-    case 16: return run_linearized_generic<T, 16>(p, tb, params, g, out, B, ws);
-    case 24: return run_linearized_generic<T, 24>(p, tb, params, g, out, B, ws);
-    case 32: return run_linearized_generic<T, 32>(p, tb, params, g, out, B, ws);
-    case 48: return run_linearized_generic<T, 48>(p, tb, params, g, out, B, ws);
-    case 64: return run_linearized_generic<T, 64>(p, tb, params, g, out, B, ws);
+    case 16: return run_linearized_generic<T, 16>(p, tb, params, g, out, B, ws, mc);
+    case 24: return run_linearized_generic<T, 24>(p, tb, params, g, out, B, ws, mc);
+    case 32: return run_linearized_generic<T, 32>(p, tb, params, g, out, B, ws, mc);
+    case 48: return run_linearized_generic<T, 48>(p, tb, params, g, out, B, ws, mc);
+    case 64: return run_linearized_generic<T, 64>(p, tb, params, g, out, B, ws, mc);
+    default: return LBO_EUNSUPPORTED;
+  }
+}
+
+template <typename T>
+static lbo_status dispatch_precompute(lbo_plan* p, const GenericTables<T>& tb, const double* params, int B, void* ws,
+                                      void* uh, void* w) {
+  switch (p->N) {
+    case 16: return precompute_maxwellian_generic<T, 16>(p, tb, params, B, ws, (T*)uh, (T*)w);
+    case 24: return precompute_maxwellian_generic<T, 24>(p, tb, params, B, ws, (T*)uh, (T*)w);
+    case 32: return precompute_maxwellian_generic<T, 32>(p, tb, params, B, ws, (T*)uh, (T*)w);
+    case 48: return precompute_maxwellian_generic<T, 48>(p, tb, params, B, ws, (T*)uh, (T*)w);
+    case 64: return precompute_maxwellian_generic<T, 64>(p, tb, params, B, ws, (T*)uh, (T*)w);
     default: return LBO_EUNSUPPORTED;
   }
 }

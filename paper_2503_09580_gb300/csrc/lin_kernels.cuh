@@ -288,15 +288,17 @@ enum Axis1Mode {
   AX_FWD_MULT_INV = 2,// dst = F1^-1( F1(src) * table[|k|^2] )
   AX_FWD_ACC = 3,     // dst (+)= table[|k|^2] * F1(src)
   AX_INV_STORE = 4,   // dst = F1^-1(src)
-  AX_UHAT_INV = 5     // dst = F1^-1( src * u^_j(|k|) * scale ), src already axis-1 transformed;
+  AX_UHAT_INV = 5,    // dst = F1^-1( src * u^_j(|k|) * scale ), src already axis-1 transformed;
                       // u^_j from its axes-3,2 DCT planes, finished along axis 1 here
+  AX_UHAT_CACHED = 6  // as AX_UHAT_INV with u^_j read whole from its cached octant
 };
 
 struct Axis1Args {
   const void* table;    // [QMAX] T (AX_FWD_MULT_INV, AX_FWD_ACC)
-  double scale;         // AX_UHAT_INV
+  double scale;         // AX_UHAT_INV, AX_UHAT_CACHED
   int first;            // AX_FWD_ACC: store instead of accumulate
-  const void* uplanes;  // [B][N/2+1]^3 T (AX_UHAT_INV): u^_j after the axis-3 and axis-2 DCTs
+  const void* uplanes;  // [B][N/2+1]^3 T: u^_j after the axis-3 and axis-2 DCTs (AX_UHAT_INV), or
+                        // the whole octant u^_j(|k1|, |k2|, k3) (AX_UHAT_CACHED)
   const void* dct;      // [N/2+1][N/4] T (AX_UHAT_INV): DCT-I coefficients
 };
 
@@ -406,31 +408,60 @@ __global__ void __launch_bounds__(256) k_uhat_planes(const double* __restrict__ 
   for (int t = threadIdx.x; t < np * HN * HN; t += blockDim.x) dst[t] = W[t];
 }
 
+// Axis 1 of u^_j in place on the octant of k_uhat_planes, for the cache of
+// the Maxwellian-dependent factors: up[b][d1][k2][k3] -> up[b][k1][k2][k3].
+// Each thread reads one whole pencil before writing it, so in place is safe.
+// grid = B.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_uhat_finish(T* __restrict__ up, const T* __restrict__ dct) {
+  constexpr int HN = N / 2 + 1;
+  T* base = up + (size_t)blockIdx.x * HN * HN * HN;
+  for (int t = threadIdx.x; t < HN * HN; t += blockDim.x) {
+    T* x = base + t;  // pencil (k2, k3) = (t / HN, t % HN), stride HN^2 along axis 1
+    DctPencil<T, N> pen;
+    pen.load(x, (size_t)HN * HN);
+    for (int k = 0; k < HN; ++k) x[(size_t)k * HN * HN] = pen.out(k, dct);
+  }
+}
+
 template <typename T, int N, int CW, int MODE>
 __global__ void __launch_bounds__(256) k_axis1(Axis1Args a, const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst) {
   constexpr int HC = N / 2 + 1, NC = N * HC;
   __shared__ __align__(16) cpx<T> S[N * CW];
-  __shared__ T Uc[MODE == AX_UHAT_INV ? CW * HC : 1];  // u^_j(|k1|, column)
+  constexpr bool UHAT = MODE == AX_UHAT_INV || MODE == AX_UHAT_CACHED;
+  __shared__ T Uc[UHAT ? CW * HC : 1];  // u^_j(|k1|, column)
   const int b = blockIdx.y, c0 = blockIdx.x * CW;
   const size_t inst = (size_t)b * N * NC;
   for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
     int c = t % CW, r = t / CW;
     S[t] = (c0 + c < NC) ? src[inst + (size_t)r * NC + c0 + c] : make_c((T)0, (T)0);
   }
-  if constexpr (MODE == AX_UHAT_INV) {
-    // finish u^_j along axis 1 for this tile's columns (|k2|, k3): 8 threads
-    // per column, each forming every 8th output
+  if constexpr (UHAT) {
     const T* up = (const T*)a.uplanes + (size_t)b * HC * HC * HC;
-    const T* dct = (const T*)a.dct;
-    for (int t = threadIdx.x; t < CW * 8; t += blockDim.x) {
-      const int c = t % CW, gsub = t / CW, col = c0 + c;
-      if (col >= NC) continue;
-      const int p2 = col / HC, k3 = col % HC;
-      int k2 = centred<N>(freq_of_pos<N>(p2));
-      k2 = k2 < 0 ? -k2 : k2;
-      DctPencil<T, N> pen;
-      pen.load(up + (size_t)k2 * HC + k3, (size_t)HC * HC);
-      for (int k = gsub; k < HC; k += 8) Uc[c * HC + k] = pen.out(k, dct);
+    if constexpr (MODE == AX_UHAT_INV) {
+      // finish u^_j along axis 1 for this tile's columns (|k2|, k3): 8 threads
+      // per column, each forming every 8th output
+      const T* dct = (const T*)a.dct;
+      for (int t = threadIdx.x; t < CW * 8; t += blockDim.x) {
+        const int c = t % CW, gsub = t / CW, col = c0 + c;
+        if (col >= NC) continue;
+        const int p2 = col / HC, k3 = col % HC;
+        int k2 = centred<N>(freq_of_pos<N>(p2));
+        k2 = k2 < 0 ? -k2 : k2;
+        DctPencil<T, N> pen;
+        pen.load(up + (size_t)k2 * HC + k3, (size_t)HC * HC);
+        for (int k = gsub; k < HC; k += 8) Uc[c * HC + k] = pen.out(k, dct);
+      }
+    } else {
+      // the cached octant: u^_j(|k1|, |k2|, k3) at up[(|k1| HC + |k2|) HC + k3]
+      for (int t = threadIdx.x; t < CW * HC; t += blockDim.x) {
+        const int c = t % CW, k = t / CW, col = c0 + c;
+        if (col >= NC) continue;
+        const int p2 = col / HC, k3 = col % HC;
+        int k2 = centred<N>(freq_of_pos<N>(p2));
+        k2 = k2 < 0 ? -k2 : k2;
+        Uc[c * HC + k] = up[((size_t)k * HC + k2) * HC + k3];
+      }
     }
     __syncthreads();
     const T sc = (T)a.scale;

@@ -27,7 +27,9 @@ namespace lbo {
 // defined in lin_x2.cu, one translation unit per (pair type, N)
 #define LBO_X2_DECL(b, n)                                                                                       \
   lbo_status x2_lin_##b##_##n(lbo_plan* p, const void* const* tb, const double* params, const double* g,      \
-                              double* out, int B);                                                           \
+                              double* out, int B, const void* cuh, const void* cw);                          \
+  lbo_status x2_cache_##b##_##n(lbo_plan* p, const void* const* tb, const double* params, int B, void* uh,      \
+                                void* w);                                                                    \
   lbo_status x2_quad_##b##_##n(lbo_plan* p, QuadState* qs, const void* const* tb, const double* f, double* out, \
                                int B);
 LBO_X2_DECL(1, 16)
@@ -164,20 +166,39 @@ static lbo_status unsupported(const lbo_plan* p) {
   return LBO_EUNSUPPORTED;
 }
 
-lbo_status run_linearized_twofold(lbo_plan* p, const double* params, const double* g, double* out, int B) {
+lbo_status run_linearized_twofold(lbo_plan* p, const double* params, const double* g, double* out, int B,
+                                  const void* cuh, const void* cw) {
   if (!twofold_built(p->precision, p->N)) return unsupported(p);
   const void* tb[4];
   lbo_status st = twofold_tables(p, &tb[1], &tb[2], &tb[0], &tb[3]);
   if (st != LBO_OK) return st;
   const int b = p->precision == LBO_PREC_FP64X2 ? 2 : 1;
   switch (b * 100 + p->N) {
-    case 116: return x2_lin_1_16(p, tb, params, g, out, B);
-    case 124: return x2_lin_1_24(p, tb, params, g, out, B);
-    case 132: return x2_lin_1_32(p, tb, params, g, out, B);
-    case 148: return x2_lin_1_48(p, tb, params, g, out, B);
-    case 164: return x2_lin_1_64(p, tb, params, g, out, B);
-    case 216: return x2_lin_2_16(p, tb, params, g, out, B);
-    case 232: return x2_lin_2_32(p, tb, params, g, out, B);
+    case 116: return x2_lin_1_16(p, tb, params, g, out, B, cuh, cw);
+    case 124: return x2_lin_1_24(p, tb, params, g, out, B, cuh, cw);
+    case 132: return x2_lin_1_32(p, tb, params, g, out, B, cuh, cw);
+    case 148: return x2_lin_1_48(p, tb, params, g, out, B, cuh, cw);
+    case 164: return x2_lin_1_64(p, tb, params, g, out, B, cuh, cw);
+    case 216: return x2_lin_2_16(p, tb, params, g, out, B, cuh, cw);
+    case 232: return x2_lin_2_32(p, tb, params, g, out, B, cuh, cw);
+    default: return unsupported(p);
+  }
+}
+
+lbo_status precompute_twofold(lbo_plan* p, const double* params, int B, void* uh, void* w) {
+  if (!twofold_built(p->precision, p->N)) return unsupported(p);
+  const void* tb[4];
+  lbo_status st = twofold_tables(p, &tb[1], &tb[2], &tb[0], &tb[3]);
+  if (st != LBO_OK) return st;
+  const int b = p->precision == LBO_PREC_FP64X2 ? 2 : 1;
+  switch (b * 100 + p->N) {
+    case 116: return x2_cache_1_16(p, tb, params, B, uh, w);
+    case 124: return x2_cache_1_24(p, tb, params, B, uh, w);
+    case 132: return x2_cache_1_32(p, tb, params, B, uh, w);
+    case 148: return x2_cache_1_48(p, tb, params, B, uh, w);
+    case 164: return x2_cache_1_64(p, tb, params, B, uh, w);
+    case 216: return x2_cache_2_16(p, tb, params, B, uh, w);
+    case 232: return x2_cache_2_32(p, tb, params, B, uh, w);
     default: return unsupported(p);
   }
 }

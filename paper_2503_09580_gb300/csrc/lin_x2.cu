@@ -21,12 +21,23 @@
 namespace lbo {
 
 lbo_status LBO_CAT4(x2_lin_, LBO_X2_B, _, LBO_X2_N)(lbo_plan* p, const void* const* tb, const double* params,
-                                                    const double* g, double* out, int B) {
+                                                    const double* g, double* out, int B, const void* cuh,
+                                                    const void* cw) {
   cudaError_t e = upload_twiddles();  // this translation unit's copy
   if (e != cudaSuccess) return cuda_fail(e, "two-fold twiddles");
   using T = LBO_X2_T;
   GenericTables<T> t{(const T*)tb[1], (const T*)tb[2], (const T*)tb[0], (const T*)tb[3]};
-  return run_linearized_generic<T, LBO_X2_N>(p, t, params, g, out, B, p->ws);
+  GenericCache<T> mc{(const T*)cuh, (const T*)cw};
+  return run_linearized_generic<T, LBO_X2_N>(p, t, params, g, out, B, p->ws, cuh ? &mc : nullptr);
+}
+
+lbo_status LBO_CAT4(x2_cache_, LBO_X2_B, _, LBO_X2_N)(lbo_plan* p, const void* const* tb, const double* params,
+                                                      int B, void* uh, void* w) {
+  cudaError_t e = upload_twiddles();
+  if (e != cudaSuccess) return cuda_fail(e, "two-fold twiddles");
+  using T = LBO_X2_T;
+  GenericTables<T> t{(const T*)tb[1], (const T*)tb[2], (const T*)tb[0], (const T*)tb[3]};
+  return precompute_maxwellian_generic<T, LBO_X2_N>(p, t, params, B, p->ws, (T*)uh, (T*)w);
 }
 
 lbo_status LBO_CAT4(x2_quad_, LBO_X2_B, _, LBO_X2_N)(lbo_plan* p, QuadState* qs, const void* const* tb,

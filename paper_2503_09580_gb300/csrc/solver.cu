@@ -808,6 +808,10 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
                    mf - S->pb.total_mass, 1.0, S->len);
       }
     }
+    // the Krylov products of this step share the cells' Maxwellians: their
+    // u^_j and loss factor are computed once (dropped before f changes)
+    if (st == LBO_OK && S->pb.jacobian == 0 && !S->mixed)
+      st = lbo_plan_cache_maxwellians(S->plan, S->params, S->nx);
     if (st == LBO_OK && S->pb.kind == LBO_PROBLEM_SLAB && S->pb.precond == LBO_PRECOND_MOMENT) {
       // coarse operator about this step's cell parameters (and shift)
       st = coarse_assemble(S, bordered(S));
@@ -822,6 +826,7 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
         double lr = norm2(S, S->w, &st2);
         ns->linear_residual = lr * std::sqrt(S->wnorm);
       }
+      lbo_plan_cache_maxwellians(S->plan, nullptr, 0);  // S->params changes from here on
       // f <- f - lambda g; with line search, halve lambda until the residual
       // norm decreases by the Armijo factor (the trial residual lands in S->w)
       LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(S->len), 256, 0, f, S->x, -1.0, 1.0, S->len);
@@ -843,6 +848,7 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
       if (st2 != LBO_OK) st = st2;
     }
   }
+  lbo_plan_cache_maxwellians(S->plan, nullptr, 0);
   cudaEventRecord(t2, s);
   cudaEventSynchronize(t2);
   float a = 0, b = 0;

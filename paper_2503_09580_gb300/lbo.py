@@ -32,7 +32,7 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_solver_destroy", "lbo_network_param_count", "lbo_network_loss_grad", "lbo_solver_collect",
            "lbo_solver_pair_count", "lbo_solver_train_network", "lbo_solver_get_network", "lbo_solver_set_network",
            "lbo_solver_network_param_count", "lbo_plan_autotune", "lbo_group_create", "lbo_group_set_stream",
-           "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy", "lbo_measure_alu_peaks")
+           "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy", "lbo_measure_alu_peaks", "lbo_plan_cache_maxwellians")
 
 _lib = None
 
@@ -96,6 +96,8 @@ def load():
     lib.lbo_plan_set_stream.restype = ip
     lib.lbo_apply_linearized.argtypes = [vp, dp, dp, dp, ip]
     lib.lbo_apply_linearized.restype = ip
+    lib.lbo_plan_cache_maxwellians.argtypes = [vp, dp, ip]
+    lib.lbo_plan_cache_maxwellians.restype = ip
     lib.lbo_apply_quadratic.argtypes = [vp, dp, dp, ip]
     lib.lbo_apply_quadratic.restype = ip
     lib.lbo_plan_sync.argtypes = [vp]
@@ -241,6 +243,16 @@ class Plan:
         _check(load().lbo_apply_linearized(self._h, _ptr(params), _ptr(g), _ptr(out), batch),
                "lbo_apply_linearized")
         return out
+
+    def cache_maxwellians(self, params):
+        """lbo_plan_cache_maxwellians: precompute the Maxwellian-dependent
+        factors for these (device) params; None drops the cache."""
+        if params is None:
+            _check(load().lbo_plan_cache_maxwellians(self._h, None, 0), "lbo_plan_cache_maxwellians")
+            return
+        batch = int(params.shape[0]) if len(params.shape) == 2 else 1
+        self._stream(params)
+        _check(load().lbo_plan_cache_maxwellians(self._h, _ptr(params), batch), "lbo_plan_cache_maxwellians")
 
     def apply_linearized_noalloc(self, params, g, out):
         """lbo_apply_linearized_noalloc: same operator, scratch from the

@@ -5,8 +5,10 @@ numbers, about 106 bits), against the CPU oracle.
 Bounds.  The FFT form of Algorithm 1 loses accuracy in proportion to the
 size of the ratio r = g/M it transforms (Sec. 3.3); per instance the stated
 bound is 4 u rms(r) (u the unit roundoff of the transform arithmetic:
-2^-48 for FP32X2, 2^-105 for FP64X2; rms over the grid, r = 0 where cut),
-and 1e-12 on inputs g = M p (noise-free) for both forms.
+2^-48 for FP32X2, 2^-105 for FP64X2; rms over the grid, r = 0 where cut).
+FP64X2 also meets the FP64 bar of 1e-12 on inputs g = M p; FP32X2 (48
+significant bits, fewer than FP64's 53) lands at ~1e-12 there, u rms(r)
+with rms(r) ~ 300 for the quartic perturbations.
 
 The higher-precision convolution of Sec. 3.4: without the cut-off of
 Eq. (3.9) the FP64 transforms of a bimodal gas (a cold Maxwellian plus a
@@ -71,9 +73,10 @@ def test_fp32x2_noise_free_matches_oracle(n):
     params, g = workloads.batched_instances(n, L, batch=3, seed=41, noise=0.0)
     got = run(lbo.Plan(n, L, 0.5, n, precision="fp32x2"), params, g)
     e = errs(got, apply_linearized(tables(n, L, 0.5), params, g))
-    print("fp32x2 n=%d noise-free errors" % n, e)
-    assert np.all(e <= 1e-12)
-    assert np.all(e <= 4 * U_F32X2 * rms_r(params, g, n, L))
+    bound = 4 * U_F32X2 * rms_r(params, g, n, L)
+    print("fp32x2 n=%d noise-free errors" % n, e, "bounds", bound)
+    assert np.all(e <= bound)
+    assert np.all(e <= 4e-12)
 
 
 @pytest.mark.parametrize("n", [24, 32, 48, 64])
@@ -161,4 +164,7 @@ def test_quadratic_twofold_matches_oracle(precision, n):
     sig, w = hemisphere_rule(p)
     e = errs(out.cpu().numpy(), apply_quadratic(tables(n, L, 0.5), f, sig, w))
     print("Q %s n=%d errors" % (precision, n), e)
-    assert np.all(e <= 1e-12)
+    # Q transforms f itself (no ratio to a Maxwellian): the FP64 form sits near
+    # 1e-14; the pairs of FP32 carry 2^5 times its rounding, the pairs of FP64
+    # are limited by the FP64 oracle
+    assert np.all(e <= (1024 * U_F32X2 if precision == "fp32x2" else 1e-12))
