@@ -52,10 +52,13 @@ HBM_KERNELS = ("combine", "fixes", "f32_head", "f32_tail")
 # DRAM bytes (read + write) per launch of a dominant kernel at the benchmark
 # workload from one ncu capture, with the sha256 (first 16 hex digits) of the
 # source files it was built from; reported as null once those sources change.
-NCU_TRAFFIC = {}
 KERNEL_SOURCES = {
-    "plane_inv_mh_fwd": ("lin_kernels.cuh", "fft.cuh", "lbo.cu"),
+    "plane_inv_mh_fwd": ("lin_kernels.cuh", "fft.cuh", "twofold.cuh", "twiddles_hi.h"),
     "f32_gain": ("lin_fused32.cu", "fused32.cuh", "tmem.cuh"),
+}
+NCU_TRAFFIC = {
+    # profiles/linearized_generic_fp64_n32_b256.md: 71.41 MB read + 11.30 MB written
+    ("plane_inv_mh_fwd", 32, "fp64"): (82709504, "94611ee3daceb1cc"),
 }
 
 

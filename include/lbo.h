@@ -48,7 +48,10 @@ typedef enum {
   LBO_ENOTCONV = 4,      /* iterative solve stopped at its iteration cap    */
   LBO_EBREAKDOWN = 5,    /* Krylov breakdown                                */
   LBO_ENAN = 6,          /* non-finite value detected                       */
-  LBO_EUNSUPPORTED = 7   /* combination of N / precision not built          */
+  LBO_EUNSUPPORTED = 7,  /* combination of N / precision not built          */
+  LBO_ETIMEOUT = 8       /* a kernel gave up a bounded wait (tensor-core
+                            path: an MMA completion); the results of the
+                            call are not valid                             */
 } lbo_status;
 
 typedef enum {
@@ -59,11 +62,20 @@ typedef enum {
                             (hi + lo, about 48 significant bits, FP32
                             exponent range) on the FP32 pipe; FP64
                             Maxwellians, ratio, cut-off and combination     */
-  LBO_PREC_FP64X2 = 3    /* transforms and products in pairs of FP64 numbers
+  LBO_PREC_FP64X2 = 3,   /* transforms and products in pairs of FP64 numbers
                             (about 106 significant bits): the higher-
                             precision convolution of Sec. 3.4 (the paper
                             uses binary128), accurate without the cut-off
-                            where FP64 transforms lose max|r| u digits     */
+                            where FP64 transforms lose max|r| u digits;
+                            N = 16 and 32                                  */
+  LBO_PREC_BF16_SPLIT = 4,/* every transform a dense DFT contraction on the
+                            tensor cores (tcgen05.mma, FP32 accumulation):
+                            data and DFT matrix split into BF16 hi + lo
+                            parts, three products (~2^-16 per transform);
+                            FP32 fields between transforms; L only;
+                            N = 16, 32, 64                                 */
+  LBO_PREC_FP16_SPLIT = 5 /* the same with FP16 parts (~2^-22 per transform),
+                            each pencil scaled by a power of two            */
 } lbo_precision;
 
 typedef enum {
@@ -128,7 +140,9 @@ lbo_status lbo_plan_cache_maxwellians(lbo_plan *plan, const double *maxwellian_p
 
 /* Quadratic collision operator Q(f,f) in the M-point hemisphere-quadrature
  * form of Eq. (2.14) with the plan's radial rule and a product hemisphere
- * rule of M = 2p^2 points.  f, out: batch*N^3 doubles, no aliasing. */
+ * rule of M = 2p^2 points.  f, out: batch*N^3 doubles, no aliasing.
+ * Built in FP64, FP32 and the two-fold precisions (LBO_EUNSUPPORTED for the
+ * split 16-bit ones). */
 lbo_status lbo_apply_quadratic(lbo_plan *plan, const double *f, double *out, int batch);
 
 /* Wait for all work queued on the plan's stream; report the first
@@ -425,6 +439,20 @@ lbo_status lbo_group_use_graph(lbo_group *group, int enable);
 lbo_status lbo_group_apply_linearized(lbo_group *group, const double *const *params, const double *const *g,
                                       double *const *out, const int *batch);
 void lbo_group_destroy(lbo_group *group);
+
+/* One axis pass of a batched 3-D DFT on the tensor cores (the building
+ * block of the split 16-bit precisions): out = DFT along `axis` (1, 2, 3 =
+ * i1, i2, i3) of each of `batch` complex fields of N^3 FP32 pairs
+ * (interleaved re, im; row-major [batch][i1][i2][i3]); forward
+ * exp(-2 pi i q (j - N/2) / N) from a centred index j to a cyclic frequency
+ * q (inverse = 1: the conjugate, unnormalised, frequency -> centred index).
+ * precision: LBO_PREC_BF16_SPLIT or LBO_PREC_FP16_SPLIT; N = 16, 32, 64;
+ * in, out: device pointers (out may equal in); stream: cudaStream_t as
+ * void*.  Allocates its DFT matrices for the call and synchronizes the
+ * stream.  Errors: LBO_EINVAL, LBO_EUNSUPPORTED, LBO_ENOMEM, LBO_ECUDA,
+ * LBO_ETIMEOUT. */
+lbo_status lbo_dft_axis_tensor(int N, int precision, int inverse, int axis, const float *in, float *out, int batch,
+                               void *stream);
 
 /* Measured ALU peaks of the current device, the denominators of the
  * library's roofline fractions for ALU-bound kernels (a measurement

@@ -306,7 +306,21 @@ static int kernel_path(const lbo_plan* p) {
 
 // bytes of one real number of the generic path's transform arithmetic
 static size_t transform_real_bytes(int prec) {
-  return prec == LBO_PREC_FP32 ? 4 : (prec == LBO_PREC_FP64X2 ? 16 : 8);
+  return prec == LBO_PREC_FP32 || is_split16_precision(prec) ? 4 : (prec == LBO_PREC_FP64X2 ? 16 : 8);
+}
+
+static lbo_status grow_buffer(void*& ptr, size_t& cap, size_t need, const char* what) {
+  if (need <= cap) return LBO_OK;
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  cap = 0;
+  if (cudaMalloc(&ptr, need) != cudaSuccess) {
+    cudaGetLastError();
+    g_last_error = what;
+    return LBO_ENOMEM;
+  }
+  cap = need;
+  return LBO_OK;
 }
 
 static bool is_device_ptr(const void* ptr) {
@@ -332,6 +346,7 @@ const char* lbo_status_string(lbo_status s) {
     case LBO_EBREAKDOWN: return "Krylov breakdown";
     case LBO_ENAN: return "non-finite value";
     case LBO_EUNSUPPORTED: return "unsupported configuration";
+    case LBO_ETIMEOUT: return "a kernel's bounded wait ran out";
   }
   return "unknown status";
 }
@@ -390,7 +405,7 @@ lbo_status lbo_plan_set(lbo_plan* p, lbo_option key, double v) {
       p->hemi_p = (int)v;
       break;
     case LBO_OPT_PRECISION:
-      if (v != 0.0 && v != 1.0 && v != 2.0 && v != 3.0) return LBO_EINVAL;
+      if (!(v == 0.0 || v == 1.0 || v == 2.0 || v == 3.0 || v == 4.0 || v == 5.0)) return LBO_EINVAL;
       p->precision = (int)v;
       break;
     case LBO_OPT_KERNEL:
@@ -457,6 +472,30 @@ lbo_status lbo_apply_linearized(lbo_plan* p, const double* params, const double*
     p->last_launches = launches;
   } else if (is_twofold_precision(p->precision)) {
     st = run_linearized_twofold(p, dp, dg, dout, batch, cuh, cw);
+  } else if (is_split16_precision(p->precision)) {
+    if (!dftmm_supported(p->N)) {
+      g_last_error = "split 16-bit tensor-core precisions: N = 16, 32 or 64";
+      return LBO_EUNSUPPORTED;
+    }
+    p->last_launches = 0;
+    const size_t HC = p->N / 2 + 1, n3 = (size_t)p->N * p->N * p->N;
+    if (!cached) {
+      // u^_j and w for this call, by the generic FP32 kernels
+      const size_t uh_bytes = (size_t)p->J * batch * HC * HC * HC * 4;
+      st = grow_buffer(p->tc_scratch, p->tc_scratch_bytes, uh_bytes + (size_t)batch * n3 * 4,
+                       "tensor-core scratch allocation");
+      if (st != LBO_OK) return st;
+      cuh = p->tc_scratch;
+      cw = (unsigned char*)p->tc_scratch + uh_bytes;
+      st = dispatch_precompute<float>(p, plain_tables<float>(p), dp, batch, p->ws, (void*)cuh, (void*)cw);
+      if (st != LBO_OK) return st;
+    }
+    st = run_linearized_dftmm(p, dp, dg, dout, batch, (const float*)cuh, (const float*)cw, p->ws);
+    if (st == LBO_OK && (p->mass_fix || p->moment_fix)) {
+      int launches = p->last_launches;
+      st = launch_fixes(p, dout, batch, p->N, 2.0 * p->L / p->N, p->stream, &launches);
+      p->last_launches = launches;
+    }
   } else {
     st = p->precision == LBO_PREC_FP64 ? dispatch_lin<double>(p, dp, dg, dout, batch, cuh, cw)
                                        : dispatch_lin<float>(p, dp, dg, dout, batch, cuh, cw);
@@ -466,6 +505,7 @@ lbo_status lbo_apply_linearized(lbo_plan* p, const double* params, const double*
     cudaError_t e = cudaMemcpyAsync(out, p->stage_out, sizeof(double) * n3 * batch, cudaMemcpyDefault, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    if (is_split16_precision(p->precision)) return dftmm_check(p);
   }
   return LBO_OK;
 }
@@ -556,7 +596,8 @@ lbo_status lbo_plan_sync(lbo_plan* p) {
   if (!p) return LBO_EINVAL;
   cudaError_t e = cudaStreamSynchronize(p->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
-  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "sync");
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  return dftmm_check(p);  // a tensor-core pass that gave up waiting
 }
 
 int lbo_plan_last_launches(const lbo_plan* p) { return p ? p->last_launches : 0; }
@@ -566,6 +607,8 @@ void lbo_plan_destroy(lbo_plan* p) {
   free_tables(p);
   if (p->mc_uh) cudaFree(p->mc_uh);
   if (p->mc_w) cudaFree(p->mc_w);
+  if (p->tc_scratch) cudaFree(p->tc_scratch);
+  free_dftmm(p);
   if (p->ws) cudaFree(p->ws);
   if (p->stage_in) cudaFree(p->stage_in);
   if (p->stage_out) cudaFree(p->stage_out);

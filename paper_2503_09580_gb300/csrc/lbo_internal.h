@@ -29,6 +29,14 @@ struct lbo_plan {
   // two-fold tables {phit, phi, omega, dct}, built on first use (lin_twofold.cu)
   void* d_x2f[4] = {nullptr, nullptr, nullptr, nullptr};  // pairs of FP32
   void* d_x2d[4] = {nullptr, nullptr, nullptr, nullptr};  // pairs of FP64
+  // split 16-bit tensor-core path (lin_dftmm.cu): DFT matrices {forward,
+  // inverse} per operand type, the MMA-wait error flag, per-call scratch for
+  // u^_j and w when the Maxwellian cache does not hold them
+  void* d_wbf[2] = {nullptr, nullptr};
+  void* d_wfp[2] = {nullptr, nullptr};
+  void* d_tc_err = nullptr;
+  void* tc_scratch = nullptr;
+  size_t tc_scratch_bytes = 0;
   // cache of the Maxwellian-dependent factors (lbo_plan_cache_maxwellians):
   // valid for apply calls with this params pointer, batch, precision and path
   const double* mc_params = nullptr;
@@ -124,6 +132,13 @@ void free_twofold_tables(lbo_plan* p);
 inline bool is_twofold_precision(int prec) { return prec == LBO_PREC_FP32X2 || prec == LBO_PREC_FP64X2; }
 // bytes of one real number in the transform precision of the generic path
 inline size_t generic_real_bytes(int prec) { return prec == LBO_PREC_FP64X2 ? 16 : 8; }
+// split 16-bit precisions on the tensor cores (lin_dftmm.cu)
+inline bool is_split16_precision(int prec) { return prec == LBO_PREC_BF16_SPLIT || prec == LBO_PREC_FP16_SPLIT; }
+bool dftmm_supported(int N);
+lbo_status run_linearized_dftmm(lbo_plan* p, const double* params, const double* g, double* out, int B,
+                                const float* uh, const float* w, void* ws);
+lbo_status dftmm_check(lbo_plan* p);
+void free_dftmm(lbo_plan* p);
 // fused FP32 path for N = 32 (lin_fused32.cu)
 size_t fused32_workspace_bytes(int B, int G, int J);
 int fused32_default_groups(int B);

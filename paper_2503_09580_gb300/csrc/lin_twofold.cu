@@ -157,7 +157,8 @@ void free_twofold_tables(lbo_plan* p) {
 
 // Built sizes: pairs of FP32 for every N, pairs of FP64 for N = 16 and 32.
 static bool twofold_built(int prec, int N) {
-  return prec == LBO_PREC_FP32X2 ? (N == 16 || N == 24 || N == 32 || N == 48 || N == 64) : (N == 16 || N == 32);
+  if (prec == LBO_PREC_FP32X2) return N == 16 || N == 24 || N == 32 || N == 48 || N == 64;
+  return prec == LBO_PREC_FP64X2 && (N == 16 || N == 32);
 }
 
 static lbo_status unsupported(const lbo_plan* p) {

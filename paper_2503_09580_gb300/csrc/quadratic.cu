@@ -53,6 +53,11 @@ void free_quadratic(lbo_plan* p) {
 }
 
 lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int B) {
+  if (is_split16_precision(p->precision)) {
+    set_error_text("Q(f,f) is not built in the split 16-bit precisions (give the solver an FP64 or FP32 "
+                   "residual plan)");
+    return LBO_EUNSUPPORTED;
+  }
   cudaError_t e = upload_twiddles();
   if (e != cudaSuccess) return cuda_fail(e, "quadratic twiddles");
   QuadState* qs = (QuadState*)p->quad;

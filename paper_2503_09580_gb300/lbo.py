@@ -18,9 +18,10 @@ LIB_PATH = os.path.join(_PKG, "_lib", "liblbo.so")
 
 LBO_OPT = {"R": 0, "C": 1, "eps": 2, "cutoff": 3, "mass_fix": 4, "moment_fix": 5,
            "hemisphere_p": 6, "precision": 7, "kernel": 8, "jgroups": 9}
-PRECISION = {"fp64": 0, "fp32": 1, "fp32x2": 2, "fp64x2": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32x2": 2, "fp64x2": 3, "bf16_split": 4, "fp16_split": 5}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "not converged",
-          5: "Krylov breakdown", 6: "non-finite value", 7: "unsupported configuration"}
+          5: "Krylov breakdown", 6: "non-finite value", 7: "unsupported configuration",
+          8: "a kernel's bounded wait ran out"}
 
 # Every symbol include/lbo.h declares (checked by the tests).
 EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_linearized",
@@ -32,7 +33,8 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_solver_destroy", "lbo_network_param_count", "lbo_network_loss_grad", "lbo_solver_collect",
            "lbo_solver_pair_count", "lbo_solver_train_network", "lbo_solver_get_network", "lbo_solver_set_network",
            "lbo_solver_network_param_count", "lbo_plan_autotune", "lbo_group_create", "lbo_group_set_stream",
-           "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy", "lbo_measure_alu_peaks", "lbo_plan_cache_maxwellians")
+           "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy", "lbo_measure_alu_peaks", "lbo_plan_cache_maxwellians",
+           "lbo_dft_axis_tensor")
 
 _lib = None
 
@@ -96,6 +98,8 @@ def load():
     lib.lbo_plan_set_stream.restype = ip
     lib.lbo_apply_linearized.argtypes = [vp, dp, dp, dp, ip]
     lib.lbo_apply_linearized.restype = ip
+    lib.lbo_dft_axis_tensor.argtypes = [ip, ip, ip, ip, vp, vp, ip, vp]
+    lib.lbo_dft_axis_tensor.restype = ip
     lib.lbo_plan_cache_maxwellians.argtypes = [vp, dp, ip]
     lib.lbo_plan_cache_maxwellians.restype = ip
     lib.lbo_apply_quadratic.argtypes = [vp, dp, dp, ip]
@@ -197,6 +201,21 @@ def _current_stream(*arrays):
             import torch
             return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
     return None
+
+
+def dft_axis_tensor(N, precision, inverse, axis, x, out):
+    """lbo_dft_axis_tensor: one axis pass of a batched 3-D DFT on the tensor
+    cores; x, out: CUDA float32 tensors [batch, N, N, N, 2] (re, im)."""
+    import torch
+    for a in (x, out):
+        if a.dtype != torch.float32 or not a.is_contiguous() or not a.is_cuda:
+            raise TypeError("expected contiguous float32 CUDA tensors")
+    batch = int(x.shape[0])
+    _check(load().lbo_dft_axis_tensor(int(N), PRECISION[precision], int(inverse), int(axis),
+                                      ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      batch, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+           "lbo_dft_axis_tensor")
+    return out
 
 
 def measure_alu_peaks(stream=None):
