@@ -39,7 +39,10 @@ N_GRID, BOX, BATCH = 32, 8.0, 256
 OMEGAS = (0.5, 0.74, 1.0)
 U64, U32 = 2.0 ** -53, 2.0 ** -24
 # unit roundoff of the transform arithmetic of each precision form
-UNIT_ROUNDOFF = {"fp64": U64, "fp32": U32, "fp32x2": 2.0 ** -48, "fp64x2": 2.0 ** -105}
+UNIT_ROUNDOFF = {"fp64": U64, "fp32": U32, "fp32x2": 2.0 ** -48, "fp64x2": 2.0 ** -105,
+                 # effective unit of a split 16-bit transform on the tensor cores (BF16 parts; FP16 parts
+                 # down to the FP32 accumulation floor)
+                 "bf16_split": 2.0 ** -16, "fp16_split": 2.0 ** -21}
 # The stated error bound of a precision form, per instance: the normwise
 # relative error of the FFT form of Algorithm 1 grows with the size of the
 # ratio r = g/M it transforms (Sec. 3.3); measured on the oracle's FFT form in
@@ -48,7 +51,7 @@ UNIT_ROUNDOFF = {"fp64": U64, "fp32": U32, "fp32x2": 2.0 ** -48, "fp64x2": 2.0 *
 BOUND_FACTOR = 4.0
 HBM_FALLBACK_GBS = 6800.0
 # Kernels bound by memory traffic, not by their arithmetic (rated in GB/s).
-HBM_KERNELS = ("combine", "fixes", "f32_head", "f32_tail")
+HBM_KERNELS = ("combine", "fixes", "f32_head", "f32_tail", "tc_combine")
 # DRAM bytes (read + write) per launch of a dominant kernel at the benchmark
 # workload from one ncu capture, with the sha256 (first 16 hex digits) of the
 # source files it was built from; reported as null once those sources change.
@@ -155,17 +158,45 @@ def kernel_bytes_per_instance(name, n, real_bytes, groups=1):
         return 8 * n3 + 8 * h
     if name == "f32_tail":     # G partial spectra and the FP32 loss field in; out (FP64)
         return groups * 8 * h + 4 * n3 + 8 * n3
+    if name == "tc_combine":   # L+, u (FP64), w (FP32), g in; out
+        return 8 * n3 * 4 + 4 * n3
     return 0
+
+
+def tensor_peak():
+    """(TFLOP/s, source): the pool's measured cuBLAS bf16 rate, sustained (a
+    tensor kernel timed inside a long step); FP16 has the same dense rate."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["bf16_tflops_sustained"]), "measured (sustained cuBLAS bf16 GEMM)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback (sustained bf16 GEMM of an earlier GB300 measurement)"
 
 
 def kernel_rooflines(prof, n, batch, peak_tflops, hbm_gbs, real_bytes, groups=1):
     """Per kernel: average launch time (live CUDA events) and its own bound:
     algorithmic flops against the measured ALU peak, or compulsory bytes
-    against the measured HBM bandwidth for the memory-bound kernels."""
+    against the measured HBM bandwidth for the memory-bound kernels.  The
+    tensor-core passes (tc_*): executed MMA flops (3 split products of the
+    (2n x 2n) real DFT matrix per pencil of n complex values: 6 (2n)^2 per
+    pencil, n^2 pencils per instance) against the measured sustained tensor
+    peak, and their bytes (read and write of a complex FP32 field, plus the
+    FP64 input or output of the first and last passes) against HBM."""
     out = {}
+    tpk, _ = tensor_peak()
     for name, (cnt, tot) in sorted(prof.items()):
         per = tot / max(cnt, 1)
         rec = {"launches": cnt, "ms_per_launch": per}
+        if name.startswith("tc_") and name != "tc_combine":
+            fl = 6.0 * (2 * n) ** 2 * n * n * batch
+            by = batch * n ** 3 * (8 + 8 + (8 if ("ratio" in name or "_g" in name or "real64" in name) else 0))
+            ach = fl / (per * 1e-3) / 1e12 if per > 0 else 0.0
+            gbs = by / (per * 1e-3) / 1e9 if per > 0 else 0.0
+            rec.update({"bound": "tensor", "achieved_tflops": ach, "frac": ach / tpk, "achieved_gbs": gbs,
+                        "frac_of_hbm": gbs / hbm_gbs})
+            out[name] = rec
+            continue
         if name in HBM_KERNELS:
             by = kernel_bytes_per_instance(name, n, real_bytes, groups) * batch
             ach = by / (per * 1e-3) / 1e9 if per > 0 else 0.0
@@ -449,7 +480,7 @@ def variant_leg(precision, tp, tg, tpc, tgc, stream, steps, peaks, hbm, ref, ref
     torch.cuda.synchronize()
     ms, prof, launches = time_steps(plan, tp, tg, out, steps, stream, True)
     unit = UNIT_ROUNDOFF[precision]
-    real_bytes = 4 if precision == "fp32" else 8
+    real_bytes = 8 if precision in ("fp64", "fp32x2") else 4
     # the pairs of FP32 run on the FP32 pipe: their algorithmic (FP64-class)
     # flop rate is rated against the FFMA peak, and also shown against the
     # DFMA peak of the FP64 form they replace
@@ -729,7 +760,8 @@ def n64_leg(with_oracle, batch=64, steps=3, L=8.0):
     params, g = workloads.batched_instances(n, L, batch=batch, seed=7, noise=1e-3)
     tp, tg = torch.from_numpy(params).cuda(), torch.from_numpy(g).cuda()
     res, outs = {}, {}
-    for prec in ("fp32", "fp64"):
+    precs = ("fp32", "fp16_split", "bf16_split", "fp32x2", "fp64")
+    for prec in precs:
         plan = lbo.Plan(n, L, 0.5, n, precision=prec)
         out = torch.empty_like(tg)
         for _ in range(2):
@@ -745,16 +777,20 @@ def n64_leg(with_oracle, batch=64, steps=3, L=8.0):
         res[prec] = {"value": batch / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms}
         outs[prec] = out.cpu().numpy()
         plan.close()
-    a, b = outs["fp32"], outs["fp64"]
-    res["fp32"]["rel_err_vs_fp64"] = float(max(np.abs(a[i] - b[i]).max() / np.abs(b[i]).max() for i in range(batch)))
-    res["fp32"]["speedup_vs_fp64"] = res["fp32"]["value"] / res["fp64"]["value"]
+    b = outs["fp64"]
+    for prec in precs[:-1]:
+        a = outs[prec]
+        res[prec]["rel_err_vs_fp64"] = float(max(np.abs(a[i] - b[i]).max() / np.abs(b[i]).max() for i in range(batch)))
+        res[prec]["speedup_vs_fp64"] = res[prec]["value"] / res["fp64"]["value"]
     if with_oracle:
         from oracle.linearized import Tables, apply_linearized
         t0 = time.perf_counter()
         ref = apply_linearized(Tables(n, L, 0.5, n), params[:1], g[:1])[0]
-        res["fp64"]["rel_err_vs_oracle"] = float(np.abs(b[0] - ref).max() / np.abs(ref).max())
-        res["fp32"]["rel_err_vs_oracle"] = float(np.abs(a[0] - ref).max() / np.abs(ref).max())
         res["oracle_seconds_per_instance"] = time.perf_counter() - t0
+        rms = ratio_rms(params[:1], g[:1], n, L)[0]
+        for prec in precs:
+            res[prec]["rel_err_vs_oracle"] = float(np.abs(outs[prec][0] - ref).max() / np.abs(ref).max())
+            res[prec]["stated_bound"] = BOUND_FACTOR * UNIT_ROUNDOFF[prec] * rms
     res["workload"] = "batched L[g], N=64, J=64, batch 64, per-instance Maxwellians, quartic + 1e-3 noise"
     return res
 
@@ -887,7 +923,7 @@ def run_ours(args, world, rank, local):
                             "sample": "first %d instances of the batch, one process" % k}}
     if solo and not args.no_variants:
         line["variants"] = {}
-        for vp in ("fp32x2", "fp32", "fp64"):
+        for vp in ("fp32x2", "fp32", "fp16_split", "bf16_split", "fp64"):
             if vp == prec:
                 continue
             rec = variant_leg(vp, tp, tg, tpc, tgc, stream, args.steps, peaks, hbm, ref, ref_c, rms, rms_c,

@@ -5,8 +5,11 @@ numpy's FFT, and L[g] against the CPU oracle.
 Stated bounds.  A split operand x = x_hi + x_lo (16-bit parts) leaves
 ~2^-16 (BF16, 8-bit significands) or ~2^-22 (FP16, 11 bits, with the
 pencil's power-of-two scale) of |x|, and the dropped product x_lo W_lo is
-of the same order, so a transform carries a relative error u_eff = 2^-16 or
-2^-22 of the data's size.  For one axis pass the bound is 4 u_eff sqrt(N)
+of the same order; the FP32 accumulation of the 2N products of an output
+adds ~2^-24 sqrt(2N) of their size, which is the larger term for FP16.  So a
+transform carries a relative error u_eff = 2^-16 (BF16) or 2^-21 (FP16, the
+accumulation floor) of the data's size (measured: 0.06 and 0.5-0.6 of the
+one-pass bound below).  For one axis pass the bound is 4 u_eff sqrt(N)
 max|x| on max|y - y_ref|.  For L[g] the FFT form's error grows with the ratio
 r = g/M it transforms (Sec. 3.3): the bound is 4 u_eff rms(r), as for the
 other reduced precisions."""
@@ -20,7 +23,7 @@ from paper_2503_09580_gb300 import lbo, workloads
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-U_EFF = {"bf16_split": 2.0 ** -16, "fp16_split": 2.0 ** -22}
+U_EFF = {"bf16_split": 2.0 ** -16, "fp16_split": 2.0 ** -21}
 
 
 def numpy_axis_dft(x, axis, inverse):
