@@ -257,7 +257,9 @@ __global__ void __launch_bounds__(kTile) k_dft_pass(PassArgs a) {
       }
       int e = 0;
       if (mx > 0.f) frexpf(mx, &e);
-      s = ldexpf(1.f, -e);  // max |x| s in [0.5, 1)
+      // max |x| s in [0.5, 1); a pencil whose largest value is subnormal (M^h
+      // underflows at the box corners) keeps s <= 2^125, so s and 1/s stay finite
+      s = ldexpf(1.f, -max(e, -125));
     }
     for (int j0 = 0; j0 < N; j0 += 4) {  // 8 reals = one 16-byte row of a core matrix
       uint32_t hi[4], lo[4];
