@@ -90,8 +90,15 @@ typedef enum {
   LBO_OPT_PRECISION = 7,   /* lbo_precision                                   */
   LBO_OPT_KERNEL = 8,      /* 0: fastest built kernel set for (N, precision)
                               (default), 1: the generic plane/axis kernels    */
-  LBO_OPT_JGROUPS = 9      /* radial nodes per CTA of the fused FP32 kernel are
+  LBO_OPT_JGROUPS = 9,     /* radial nodes per CTA of the fused FP32 kernel are
                               J / jgroups; 0 (default): chosen from the batch */
+  LBO_OPT_Q_SINC_QUADRATURE = 10 /* Q(f,f) only.  1: the loss multiplier
+                              sum_j w_j B(g_j) sinc(pi g_j |k| / L) replaced by
+                              its hemisphere quadrature
+                              sum_m w_m cos(pi g_j sigma_m . k / L), the
+                              second mass fix of Sec. 2.3 (Eq. (2.16)): Q^_0
+                              vanishes up to rounding.  Takes the generic
+                              kernels (also for FP32 at N = 32); 0: off   */
 } lbo_option;
 
 /* Create a plan for N^3 grids on [-box, box]^3, VHS exponent vhs_omega in

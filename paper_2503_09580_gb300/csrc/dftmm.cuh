@@ -128,7 +128,8 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, float s, uint32_t& l
 // stepping ulps (the test is monotone in |v-u|^2).
 template <int N>
 struct InstTables {
-  double a[3 * N], em[3 * N], ei[3 * N], eh[3 * N];
+  double a[3 * N], em[3 * N], ei[3 * N];
+  float eif[3 * N], ehf[3 * N];  // 1/M and M^h factors in FP32 (the operands are 16-bit)
   double dstar;
   int b;
 };
@@ -151,7 +152,8 @@ __device__ void fill_inst(InstTables<N>& T, const double* params, int b, double 
     }
     T.em[t] = em;
     T.ei[t] = ei;
-    T.eh[t] = eh;
+    T.eif[t] = (float)ei;
+    T.ehf[t] = (float)eh;
   }
   if (threadIdx.x == 0) {
     const double twoth = __dmul_rn(2.0, q.theta);
@@ -173,8 +175,12 @@ __device__ __forceinline__ float2 load_pre(const PassArgs& a, const InstTables<N
   const size_t e = elem<N, AXIS>(P, j);
   if constexpr (PRE == PRE_RATIO) {
     if (a.cutoff) {
+      // the cut-off decision in FP64 exactly as the oracle forms it; a point
+      // that passes has |v-u|^2/(2 theta) below the threshold, so the FP32
+      // product of its 1/M factors stays finite
       const double d2 = __dadd_rn(__dadd_rn(T.a[i1], T.a[N + i2]), T.a[2 * N + i3]);
       if (d2 >= T.dstar) return make_float2(0.f, 0.f);
+      return make_float2((float)a.g[e] * ((T.eif[i1] * T.eif[N + i2]) * T.eif[2 * N + i3]), 0.f);
     }
     return make_float2((float)(a.g[e] * ((T.ei[i1] * T.ei[N + i2]) * T.ei[2 * N + i3])), 0.f);
   } else if constexpr (PRE == PRE_REAL64) {
@@ -188,7 +194,7 @@ __device__ __forceinline__ float2 load_pre(const PassArgs& a, const InstTables<N
       x.x *= s;
       x.y *= s;
     } else if constexpr (PRE == PRE_MH) {
-      x.x = (float)((double)x.x * ((T.eh[i1] * T.eh[N + i2]) * T.eh[2 * N + i3]));
+      x.x *= (T.ehf[i1] * T.ehf[N + i2]) * T.ehf[2 * N + i3];
       x.y = 0.f;
     }
     return x;

@@ -416,6 +416,10 @@ lbo_status lbo_plan_set(lbo_plan* p, lbo_option key, double v) {
       if (!(v >= 0.0 && v <= 64.0)) return LBO_EINVAL;
       p->jgroups = (int)v;
       break;
+    case LBO_OPT_Q_SINC_QUADRATURE:
+      if (v != 0.0 && v != 1.0) return LBO_EINVAL;
+      p->q_sinc_quad = (int)v;
+      break;
     default: return LBO_EINVAL;
   }
   return LBO_OK;

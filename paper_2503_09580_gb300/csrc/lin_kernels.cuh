@@ -290,7 +290,9 @@ enum Axis1Mode {
   AX_INV_STORE = 4,   // dst = F1^-1(src)
   AX_UHAT_INV = 5,    // dst = F1^-1( src * u^_j(|k|) * scale ), src already axis-1 transformed;
                       // u^_j from its axes-3,2 DCT planes, finished along axis 1 here
-  AX_UHAT_CACHED = 6  // as AX_UHAT_INV with u^_j read whole from its cached octant
+  AX_UHAT_CACHED = 6, // as AX_UHAT_INV with u^_j read whole from its cached octant
+  AX_FWD_MULT3_INV = 7 // dst = F1^-1( F1(src) * table3[position] ), a multiplier per half-spectrum
+                       // position ([N][N][N/2+1], the spectrum's own layout)
 };
 
 struct Axis1Args {
@@ -488,6 +490,13 @@ __global__ void __launch_bounds__(256) k_axis1(Axis1Args a, const cpx<T>* __rest
         int k1 = centred<N>(freq_of_pos<N>(r)), k2 = centred<N>(freq_of_pos<N>(p2));
         S[t] = cscale(S[t], ((const T*)a.table)[k1 * k1 + k2 * k2 + k3 * k3]);
       }
+    }
+    __syncthreads();
+    smem_fft<T, N, true, true>(S, CW, 1, CW);
+  } else if constexpr (MODE == AX_FWD_MULT3_INV) {
+    for (int t = threadIdx.x; t < N * CW; t += blockDim.x) {
+      int c = t % CW, r = t / CW;
+      if (c0 + c < NC) S[t] = cscale(S[t], ((const T*)a.table)[(size_t)r * NC + c0 + c]);
     }
     __syncthreads();
     smem_fft<T, N, true, true>(S, CW, 1, CW);

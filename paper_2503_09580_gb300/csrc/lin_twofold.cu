@@ -31,7 +31,7 @@ namespace lbo {
   lbo_status x2_cache_##b##_##n(lbo_plan* p, const void* const* tb, const double* params, int B, void* uh,      \
                                 void* w);                                                                    \
   lbo_status x2_quad_##b##_##n(lbo_plan* p, QuadState* qs, const void* const* tb, const double* f, double* out, \
-                               int B);
+                               int B, const void* omg3);
 LBO_X2_DECL(1, 16)
 LBO_X2_DECL(1, 24)
 LBO_X2_DECL(1, 32)
@@ -204,20 +204,20 @@ lbo_status precompute_twofold(lbo_plan* p, const double* params, int B, void* uh
   }
 }
 
-lbo_status run_quadratic_twofold(lbo_plan* p, QuadState* qs, const double* f, double* out, int B) {
+lbo_status run_quadratic_twofold(lbo_plan* p, QuadState* qs, const double* f, double* out, int B, const void* omg3) {
   if (!twofold_built(p->precision, p->N)) return unsupported(p);
   const void* tb[4];
   lbo_status st = twofold_tables(p, &tb[1], &tb[2], &tb[0], &tb[3]);
   if (st != LBO_OK) return st;
   const int b = p->precision == LBO_PREC_FP64X2 ? 2 : 1;
   switch (b * 100 + p->N) {
-    case 116: return x2_quad_1_16(p, qs, tb, f, out, B);
-    case 124: return x2_quad_1_24(p, qs, tb, f, out, B);
-    case 132: return x2_quad_1_32(p, qs, tb, f, out, B);
-    case 148: return x2_quad_1_48(p, qs, tb, f, out, B);
-    case 164: return x2_quad_1_64(p, qs, tb, f, out, B);
-    case 216: return x2_quad_2_16(p, qs, tb, f, out, B);
-    case 232: return x2_quad_2_32(p, qs, tb, f, out, B);
+    case 116: return x2_quad_1_16(p, qs, tb, f, out, B, omg3);
+    case 124: return x2_quad_1_24(p, qs, tb, f, out, B, omg3);
+    case 132: return x2_quad_1_32(p, qs, tb, f, out, B, omg3);
+    case 148: return x2_quad_1_48(p, qs, tb, f, out, B, omg3);
+    case 164: return x2_quad_1_64(p, qs, tb, f, out, B, omg3);
+    case 216: return x2_quad_2_16(p, qs, tb, f, out, B, omg3);
+    case 232: return x2_quad_2_32(p, qs, tb, f, out, B, omg3);
     default: return unsupported(p);
   }
 }

@@ -41,11 +41,11 @@ lbo_status LBO_CAT4(x2_cache_, LBO_X2_B, _, LBO_X2_N)(lbo_plan* p, const void* c
 }
 
 lbo_status LBO_CAT4(x2_quad_, LBO_X2_B, _, LBO_X2_N)(lbo_plan* p, QuadState* qs, const void* const* tb,
-                                                     const double* f, double* out, int B) {
+                                                     const double* f, double* out, int B, const void* omg3) {
   cudaError_t e = upload_twiddles();
   if (e != cudaSuccess) return cuda_fail(e, "two-fold twiddles");
   using T = LBO_X2_T;
-  return run_quadratic<T, LBO_X2_N>(p, qs, f, out, B, (const T*)tb[1], (const T*)tb[2]);
+  return run_quadratic<T, LBO_X2_N>(p, qs, f, out, B, (const T*)tb[1], (const T*)tb[2], (const T*)omg3);
 }
 
 }  // namespace lbo

@@ -26,6 +26,11 @@ namespace lbo {
 struct QuadState {
   int p = 0;                   // hemisphere order of the cached rule
   std::vector<double> sig, wm;  // M x 3, M
+  // loss multiplier of Eq. (2.16) per half-spectrum position, in the
+  // transform precision of omq_prec, for hemisphere order omq_p
+  void* d_omq = nullptr;
+  int omq_prec = -1, omq_p = -1;
+  const void* omq_tables = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   double* d_gsw = nullptr;      // device copy: radial nodes, sigma, w_m (fused path)
@@ -178,7 +183,7 @@ inline void smem_attr(K kernel, size_t bytes) {
 
 template <typename T, int N>
 static lbo_status run_quadratic(lbo_plan* p, QuadState* qs, const double* f, double* out, int B, const T* phi,
-                         const T* omg) {
+                         const T* omg, const T* omg3 = nullptr) {
   // 32-byte complex numbers (pairs of FP64): half the planes per block and
   // half the axis-1 tile, so that k_plane_inv_prod's two plane buffers and
   // k_axis1_phase's two tiles stay within the shared memory of a block
@@ -204,6 +209,7 @@ static lbo_status run_quadratic(lbo_plan* p, QuadState* qs, const double* f, dou
   auto ki_real = k_plane_inv<T, N, PPC, INV_TO_REAL>;
   auto ka_fwd = k_axis1<T, N, CW, AX_FWD_STORE>;
   auto ka_mult = k_axis1<T, N, CW, AX_FWD_MULT_INV>;
+  auto ka_mult3 = k_axis1<T, N, CW, AX_FWD_MULT3_INV>;
   auto ka_acc = k_axis1<T, N, CW, AX_FWD_ACC>;
   auto ka_inv = k_axis1<T, N, CW, AX_INV_STORE>;
   auto ka_ph = k_axis1_phase<T, N, CW>;
@@ -256,11 +262,13 @@ static lbo_status run_quadratic(lbo_plan* p, QuadState* qs, const double* f, dou
   }
   LBO_LAUNCH(p, "q_axis1_inv", s, ka_inv, ga, blk, 0, ax, QH, QH);
   LBO_LAUNCH(p, "q_plane_inv", s, ki_real, gp, blk, sm, pa, QH, R1);
-  // loss: f InvFFT(F omega)
+  // loss: f InvFFT(F omega), omega of Algorithm 1 (radial) or its hemisphere
+  // quadrature, Eq. (2.16) (a multiplier per position)
   Axis1Args a3{};
-  a3.table = omg;
+  a3.table = omg3 ? (const void*)omg3 : (const void*)omg;
   LBO_LAUNCH(p, "q_plane_fwd_f", s, kf_real, gp, blk, sm, pa, W1);
-  LBO_LAUNCH(p, "q_axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
+  if (omg3) LBO_LAUNCH(p, "q_axis1_fwd_mul3_inv", s, ka_mult3, ga, blk, 0, a3, W1, W1);
+  else LBO_LAUNCH(p, "q_axis1_fwd_mul_inv", s, ka_mult, ga, blk, 0, a3, W1, W1);
   LBO_LAUNCH(p, "q_plane_inv", s, ki_real, gp, blk, sm, pa, W1, R2);
   LBO_LAUNCH(p, "q_combine", s, k_comb, cb, 256, 0, f, R1, R2, out, total);
   launches += 6;
@@ -275,20 +283,22 @@ static lbo_status run_quadratic(lbo_plan* p, QuadState* qs, const double* f, dou
 
 template <typename T>
 static lbo_status dispatch_q(lbo_plan* p, QuadState* qs, const double* f, double* out, int B, const void* phi_v,
-                      const void* omg_v) {
-  const T *phi = (const T*)phi_v, *omg = (const T*)omg_v;
+                      const void* omg_v, const void* omg3_v = nullptr) {
+  const T *phi = (const T*)phi_v, *omg = (const T*)omg_v, *omg3 = (const T*)omg3_v;
   switch (p->N) {
-    case 16: return run_quadratic<T, 16>(p, qs, f, out, B, phi, omg);
-    case 24: return run_quadratic<T, 24>(p, qs, f, out, B, phi, omg);
-    case 32: return run_quadratic<T, 32>(p, qs, f, out, B, phi, omg);
-    case 48: return run_quadratic<T, 48>(p, qs, f, out, B, phi, omg);
-    case 64: return run_quadratic<T, 64>(p, qs, f, out, B, phi, omg);
+    case 16: return run_quadratic<T, 16>(p, qs, f, out, B, phi, omg, omg3);
+    case 24: return run_quadratic<T, 24>(p, qs, f, out, B, phi, omg, omg3);
+    case 32: return run_quadratic<T, 32>(p, qs, f, out, B, phi, omg, omg3);
+    case 48: return run_quadratic<T, 48>(p, qs, f, out, B, phi, omg, omg3);
+    case 64: return run_quadratic<T, 64>(p, qs, f, out, B, phi, omg, omg3);
     default: return LBO_EUNSUPPORTED;
   }
 }
 
 
-// Q(f,f) in the two-fold precisions (lin_twofold.cu, quad_x2.cu)
-lbo_status run_quadratic_twofold(lbo_plan* p, QuadState* qs, const double* f, double* out, int B);
+// Q(f,f) in the two-fold precisions (lin_twofold.cu, lin_x2.cu); omg3: the
+// Eq. (2.16) loss multiplier in the pair type, or null
+lbo_status run_quadratic_twofold(lbo_plan* p, QuadState* qs, const double* f, double* out, int B,
+                                 const void* omg3 = nullptr);
 
 }  // namespace lbo

@@ -164,3 +164,22 @@ def test_quadratic_fp64_n64_bkw_configuration_matches_oracle():
     sig, w = hemisphere_rule(p)
     ref = apply_quadratic(Tables(n, L, 1.0, n), f, sig, w)
     assert relerr(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n,p,precision,tol", [(16, 2, "fp64", 1e-12), (32, 4, "fp64", 1e-12),
+                                               (32, 2, "fp32", 64 * 2.0 ** -24), (16, 2, "fp32x2", 1e-12)])
+def test_quadratic_sinc_quadrature_fix(n, p, precision, tol):
+    """Eq. (2.16): Q with the hemisphere quadrature of the loss multiplier
+    against the oracle, and its mass zero to rounding (Sec. 2.3)."""
+    L = 8.0
+    params, g = workloads.batched_instances(n, L, batch=2, seed=36, noise=0.0)
+    f = maxwell_batch(n, L, params) + 0.3 * g
+    plan = lbo.Plan(n, L, 0.5, n, hemisphere_p=p, precision=precision, q_sinc_quadrature=1)
+    got = run_q(plan, f)
+    sig, w = hemisphere_rule(p)
+    ref = apply_quadratic(Tables(n, L, 0.5, n), f, sig, w, mass_fix="sinc_quadrature")
+    assert relerr(got, ref) <= tol
+    for b in range(2):
+        assert abs(got[b].sum()) <= 64 * (2.0 ** -24 if precision == "fp32" else 2.0 ** -48) * np.abs(got[b]).sum()
+    plain = run_q(lbo.Plan(n, L, 0.5, n, hemisphere_p=p, precision=precision), f)
+    assert abs(plain[0].sum()) > 1e-7 * np.abs(plain[0]).sum()

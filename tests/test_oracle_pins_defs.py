@@ -133,3 +133,52 @@ def test_projection_check_rejects_oblique_projection():
     mom, idem, off = projection_defects(_oblique_projection, n, L, x)
     assert mom < 1e-12 and idem < 1e-10  # passes the two weaker checks
     assert off > 1e-3                    # fails the span check
+
+
+# ------------------------------------------------ Eq. (2.16) mass fix of Q
+def _q_mass(Q, n, L):
+    return (2 * L / n) ** 3 * Q.sum(), (2 * L / n) ** 3 * np.abs(Q).sum()
+
+
+def _anisotropic_f(n, L):
+    from oracle.linearized import maxwellians
+    M, *_ = maxwellians(n, L, 1.0, np.array([0.3, -0.2, 0.1]), 0.9)
+    v1, v2, v3 = grid.velocity_grid(n, L)
+    return M * (1 + 0.4 * v1 * v2 - 0.3 * v3 ** 2 + 0.2 * v1 ** 3)
+
+
+def test_sinc_quadrature_loss_conserves_mass():
+    """Sec. 2.3: with the loss multiplier's sinc replaced by its hemisphere
+    quadrature, Eq. (2.16), the bracket of Eq. (2.15) vanishes term by term,
+    so Q^_0 = 0 up to rounding; with the exact sinc it does not."""
+    from oracle.linearized import Tables
+    from oracle.quadratic import quadratic_operator
+    from oracle.quadrature import hemisphere_rule
+    n, L = 16, 8.0
+    tab = Tables(n, L, 0.5, n)
+    f = _anisotropic_f(n, L)
+    sig, w = hemisphere_rule(2)
+    m0, a0 = _q_mass(quadratic_operator(tab, f, sig, w), n, L)
+    m1, a1 = _q_mass(quadratic_operator(tab, f, sig, w, mass_fix="sinc_quadrature"), n, L)
+    assert abs(m0) > 1e-6 * a0     # the plain M-point form loses mass
+    assert abs(m1) < 1e-14 * a1    # Eq. (2.16) keeps it to rounding
+
+
+def test_sinc_quadrature_check_rejects_the_gain_argument():
+    """A planted mistake: the loss quadrature taken at the gain's argument
+    pi g_j sigma . k / (2L) (Eq. (2.14)) instead of pi g_j sigma . k / L."""
+    from oracle.linearized import FFT, InvFFT, Tables
+    from oracle.quadratic import phase_multiplier, quadratic_operator
+    from oracle.quadrature import hemisphere_rule
+    n, L = 16, 8.0
+    tab = Tables(n, L, 0.5, n)
+    f = _anisotropic_f(n, L)
+    sig, w = hemisphere_rule(2)
+    _, Qp, _ = quadratic_operator(tab, f, sig, w, return_parts=True)
+    om = np.zeros((n,) * 3)
+    for j in range(tab.J):
+        acc = sum(w[m] * np.real(phase_multiplier(n, np.pi * tab.g[j] * sig[m] / (2 * L))) for m in range(len(w)))
+        om += tab.w[j] * tab.B[j] * acc
+    Qbad = Qp - f * np.real(InvFFT(FFT(f) * 16 * np.pi ** 2 * om))
+    m, a = _q_mass(Qbad, n, L)
+    assert abs(m) > 1e-3 * a
