@@ -53,14 +53,21 @@ def _gain_pair_product(Ff, Fg, E):
 def loss_multiplier(tab, sig=None, wm=None, sinc_quadrature=False):
     """omega_k of Algorithm 1, or -- for the second mass fix of Sec. 2.3,
     Eq. (2.16) -- the same with sinc(pi g_j |k| / L) replaced by its M-point
-    hemisphere quadrature sum_m w_m cos(pi g_j sigma_m . k / L)."""
+    hemisphere quadrature sum_m w_m cos(pi g_j sigma_m . k / L).
+
+    Reading at the Nyquist planes: Eq. (2.16) is there to make the bracket of
+    Eq. (2.15) vanish, i.e. to give the loss term at k = 0 the gain's own
+    kernel.  With the gain's per-axis factor E_d(k) = exp(i alpha_d k) and
+    cos(alpha_d N_p) at the Nyquist index (alpha = pi g_j sigma_m / (2L)),
+    that kernel is Re prod_d E_d(k_d)^2: cos(pi g_j sigma_m . k / L) away
+    from the Nyquist planes and cos^2(alpha_d N_p) on them."""
     if not sinc_quadrature:
         return tab.omega
     om = np.zeros((tab.n,) * 3)
     for j in range(tab.J):
         acc = np.zeros((tab.n,) * 3)
         for m in range(len(wm)):
-            acc += wm[m] * np.real(phase_multiplier(tab.n, np.pi * tab.g[j] * sig[m] / tab.L))
+            acc += wm[m] * np.real(phase_multiplier(tab.n, np.pi * tab.g[j] * sig[m] / (2.0 * tab.L)) ** 2)
         om += tab.w[j] * tab.B[j] * acc
     return 16.0 * np.pi ** 2 * om
 

@@ -43,9 +43,12 @@ void hemisphere_rule(int p, std::vector<double>& sig, std::vector<double>& wm) {
 
 // Loss multiplier of Eq. (2.16) per half-spectrum position (p1, p2, k3):
 //   16 pi^2 / N^3 sum_j w_j B(g_j) sum_m w_m cos(pi g_j sigma_m . k / L),
-// the cosine as Re prod_d E_d(k_d), E_d the per-axis phase factors
-// exp(i alpha_d k_d) (cos(alpha_d N/2) at the Nyquist index), alpha =
-// pi g_j sigma_m / L: fac[(jm 3 + d) N + cyclic k], weights wjm = w_j B_j w_m.
+// the cosine as Re prod_d E_d(k_d)^2 with E_d the gain's per-axis phase
+// factor exp(i alpha_d k_d), alpha = pi g_j sigma_m / (2L), which is
+// cos(alpha_d N/2) at the Nyquist index: so the squared factor is
+// exp(2 i alpha_d k_d) off the Nyquist planes and cos^2(alpha_d N/2) on them,
+// the gain's own kernel at k = 0, which makes Q^_0 vanish (Sec. 2.3):
+// fac[(jm 3 + d) N + cyclic k], weights wjm = w_j B_j w_m.
 template <int N>
 __global__ void k_omega_quadrature(const double2* __restrict__ fac, const double* __restrict__ wjm, int JM,
                                    double scale, double* __restrict__ out) {
@@ -87,11 +90,12 @@ lbo_status ensure_omega_quadrature(lbo_plan* p, QuadState* qs) {
       const size_t jm = (size_t)j * M + m;
       wjm[jm] = p->wj[j] * p->Bj[j] * qs->wm[m];
       for (int d = 0; d < 3; ++d) {
-        const double al = pi * p->gj[j] * qs->sig[3 * m + d] / p->L;
+        const double al = pi * p->gj[j] * qs->sig[3 * m + d] / (2.0 * p->L);  // the gain's alpha_d
+        const double cn = std::cos(al * (N / 2));
         for (int k = 0; k < N; ++k) {
           const int kc = k < N / 2 ? k : k - N;
-          fac[(jm * 3 + d) * N + k] = kc == -N / 2 ? make_double2(std::cos(al * (N / 2)), 0.0)
-                                                   : make_double2(std::cos(al * kc), std::sin(al * kc));
+          fac[(jm * 3 + d) * N + k] = kc == -N / 2 ? make_double2(cn * cn, 0.0)
+                                                   : make_double2(std::cos(2.0 * al * kc), std::sin(2.0 * al * kc));
         }
       }
     }

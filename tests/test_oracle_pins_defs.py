@@ -158,15 +158,38 @@ def test_sinc_quadrature_loss_conserves_mass():
     tab = Tables(n, L, 0.5, n)
     f = _anisotropic_f(n, L)
     sig, w = hemisphere_rule(2)
-    m0, a0 = _q_mass(quadratic_operator(tab, f, sig, w), n, L)
-    m1, a1 = _q_mass(quadratic_operator(tab, f, sig, w, mass_fix="sinc_quadrature"), n, L)
-    assert abs(m0) > 1e-6 * a0     # the plain M-point form loses mass
-    assert abs(m1) < 1e-14 * a1    # Eq. (2.16) keeps it to rounding
+    for p in (2, 4):
+        sig, w = hemisphere_rule(p)
+        m0, a0 = _q_mass(quadratic_operator(tab, f, sig, w), n, L)
+        m1, a1 = _q_mass(quadratic_operator(tab, f, sig, w, mass_fix="sinc_quadrature"), n, L)
+        assert abs(m0) > 1e-6 * a0     # the plain M-point form loses mass
+        assert abs(m1) < 1e-13 * a1    # Eq. (2.16) keeps it to rounding
+
+
+def test_sinc_quadrature_check_rejects_the_plain_nyquist_cosine():
+    """A planted mistake at the Nyquist planes: cos(2 alpha_d N_p) (the loss
+    argument's own cosine) in place of the gain's squared factor
+    cos^2(alpha_d N_p) breaks the cancellation of Eq. (2.15)."""
+    from oracle.linearized import FFT, InvFFT, Tables
+    from oracle.quadratic import phase_multiplier, quadratic_operator
+    from oracle.quadrature import hemisphere_rule
+    n, L = 16, 8.0
+    tab = Tables(n, L, 0.5, n)
+    f = _anisotropic_f(n, L)
+    sig, w = hemisphere_rule(2)
+    _, Qp, _ = quadratic_operator(tab, f, sig, w, return_parts=True)
+    om = np.zeros((n,) * 3)
+    for j in range(tab.J):
+        acc = sum(w[m] * np.real(phase_multiplier(n, np.pi * tab.g[j] * sig[m] / L)) for m in range(len(w)))
+        om += tab.w[j] * tab.B[j] * acc
+    m, a = _q_mass(Qp - f * np.real(InvFFT(FFT(f) * 16 * np.pi ** 2 * om)), n, L)
+    assert abs(m) > 1e-3 * a
 
 
 def test_sinc_quadrature_check_rejects_the_gain_argument():
     """A planted mistake: the loss quadrature taken at the gain's argument
-    pi g_j sigma . k / (2L) (Eq. (2.14)) instead of pi g_j sigma . k / L."""
+    pi g_j sigma . k / (2L) (Eq. (2.14)) instead of pi g_j sigma . k / L
+    (Eq. (2.16))."""
     from oracle.linearized import FFT, InvFFT, Tables
     from oracle.quadratic import phase_multiplier, quadratic_operator
     from oracle.quadrature import hemisphere_rule
