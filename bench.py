@@ -749,6 +749,64 @@ def bkw_leg(precision, steps=1, n=64, L=8.0, dt=0.05):
             "final_residual": st["residual_norm"], "rel_err_vs_bkw": err}
 
 
+def lin_vs_bin_leg(case, t_end=10.0, dt=0.1, ps=(2, 3, 4), fixes=True):
+    """Sec. 4.2: df/dt = Q(f,f) and df/dt = L_M[f] (M the standard normal)
+    by RK4 (dt = 0.1) from the paper's f^(1) (Case 1, Maxwell molecules) or
+    f^(2) (Case 2, omega = 0.72), R = 6, N_p = 16, 17 radial nodes; Q with
+    the product hemisphere rules of M = 2 p^2 points (the paper's Lebedev
+    rules of 7 to 25 points are not available).  Reports E(t) (Eq. (4.3)),
+    the L2 distances between the two solutions and to the Maxwellian at
+    t_end, the mass drift, the mass-fixed variants of Sec. 4.2, and the time
+    of 100 steps of each (Table 5's comparison)."""
+    import torch
+    from paper_2503_09580_gb300 import lbo, workloads
+    n, R, J = 32, 6.0, 17
+    L = (3 + np.sqrt(2)) * R / 4
+    om = 1.0 if case == 1 else 0.72
+    f0 = (workloads.paper_f1 if case == 1 else workloads.paper_f2)(n, L)[None]
+    h3 = (2 * L / n) ** 3
+    std = torch.tensor([[1.0, 0.0, 0.0, 0.0, 1.0]], dtype=torch.float64, device="cuda")
+    a = workloads.velocity_axis(n, L)
+    Mx = (2 * np.pi) ** -1.5 * np.exp(-(a[:, None, None] ** 2 + a[None, :, None] ** 2 + a[None, None, :] ** 2) / 2)
+    l2 = lambda x: float(np.sqrt(h3 * (x * x).sum()))
+    nrec = int(round(t_end))
+    per = int(round(1.0 / dt))
+
+    def run(plan, mode):
+        tf = torch.from_numpy(f0.copy()).cuda()
+        snaps = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(nrec):
+            plan.evolve(mode, tf, dt, per, params=std if mode == "linearized" else None)
+            snaps.append(tf.cpu().numpy()[0])
+        secs = time.perf_counter() - t0
+        return snaps, secs * 100 / (nrec * per)  # seconds per 100 steps
+
+    res = {"case": case, "omega": om, "N": n, "R": R, "L": L, "radial_nodes": J, "dt": dt, "t_end": t_end}
+    lin, tl = run(lbo.Plan(n, L, om, J, R=R), "linearized")
+    res["linearized"] = {"seconds_per_100_steps": tl, "l2_to_maxwellian": l2(lin[-1] - Mx),
+                         "mass_drift": abs(h3 * lin[-1].sum() / (h3 * f0.sum()) - 1)}
+    for p in ps:
+        bins, tb = run(lbo.Plan(n, L, om, J, R=R, hemisphere_p=p), "quadratic")
+        E = [l2(x - y) / l2(y) for x, y in zip(lin, bins)]
+        res["quadratic_M%d" % (2 * p * p)] = {
+            "seconds_per_100_steps": tb, "time_ratio_to_linearized": tb / tl,
+            "l2_to_maxwellian": l2(bins[-1] - Mx), "mass_drift": abs(h3 * bins[-1].sum() / (h3 * f0.sum()) - 1),
+            "l2_diff_to_linearized": [l2(x - y) for x, y in zip(lin, bins)], "E_t": E, "E_max": max(E)}
+    if fixes:
+        linf, _ = run(lbo.Plan(n, L, om, J, R=R, mass_fix=1), "linearized")
+        res["linearized_mass_fix"] = {"mass_drift": abs(h3 * linf[-1].sum() / (h3 * f0.sum()) - 1),
+                                      "l2_to_maxwellian": l2(linf[-1] - Mx)}
+        for name, kw in (("zero_mode", {"mass_fix": 1}), ("sinc_quadrature", {"q_sinc_quadrature": 1})):
+            p = ps[-1]
+            bf, _ = run(lbo.Plan(n, L, om, J, R=R, hemisphere_p=p, **kw), "quadratic")
+            res["quadratic_M%d_%s" % (2 * p * p, name)] = {
+                "mass_drift": abs(h3 * bf[-1].sum() / (h3 * f0.sum()) - 1), "l2_to_maxwellian": l2(bf[-1] - Mx),
+                "l2_diff_to_linearized_mass_fix": l2(bf[-1] - linf[-1])}
+    return res
+
+
 def n64_leg(with_oracle, batch=64, steps=3, L=8.0):
     """L[g] applications/s at N = 64 (J = 64, batch 64, benchmark recipe:
     per-instance Maxwellians, quartic polynomial + 1e-3 noise), FP32 and
@@ -950,6 +1008,8 @@ def run_ours(args, world, rank, local):
             line["shock_mixed_n_to_1e-10"] = shock_mixed_leg(nx=args.shock_cells)
         line["mixed_n"] = mixed_leg()
         line["n64"] = n64_leg(with_oracle=not args.no_cpu_baseline)
+        if args.lin_vs_bin:
+            line["lin_vs_bin"] = {"case1": lin_vs_bin_leg(1), "case2": lin_vs_bin_leg(2)}
         line["bkw_n64"] = {"workload": "homogeneous BKW relaxation, Maxwell molecules, N=64, J=64, M=32, "
                                        "one backward-Euler step dt=0.05 (4 Newton iterations)",
                            "fp32": bkw_leg("fp32"), "fp64": bkw_leg("fp64")}
@@ -974,6 +1034,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default radial-node grouping")
     ap.add_argument("--shock-cells", type=int, default=0,
                     help="run the mixed-N shock leg with this many cells (64 cells: about 2.5 minutes)")
+    ap.add_argument("--lin-vs-bin", action="store_true",
+                    help="run the homogeneous linearized-vs-quadratic study of Sec. 4.2 (about a minute)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

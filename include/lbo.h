@@ -152,6 +152,23 @@ lbo_status lbo_plan_cache_maxwellians(lbo_plan *plan, const double *maxwellian_p
  * split 16-bit ones). */
 lbo_status lbo_apply_quadratic(lbo_plan *plan, const double *f, double *out, int batch);
 
+/* Explicit time integration of the spatially homogeneous equation
+ * (Sec. 4.2): df/dt = Q(f,f) (mode LBO_EVOLVE_QUADRATIC) or df/dt = L_M[f]
+ * (LBO_EVOLVE_LINEARIZED, M_b the Maxwellian of params[b]; L[M] = 0, so this
+ * is the linearized equation for f - M), with the classical fourth-order
+ * Runge-Kutta scheme, nsteps steps of size dt, in place on f (device,
+ * batch*N^3 doubles).  Every operator evaluation goes through the plan (its
+ * precision, kernel set and the mass fixes: LBO_OPT_MASS_FIX sets the zero
+ * mode of every evaluation to 0, LBO_OPT_Q_SINC_QUADRATURE the Eq. (2.16)
+ * loss of Q).  The linearized form caches the Maxwellian factors for its
+ * steps (and drops them afterwards unless the caller had cached them for
+ * the same params).  Allocates 3 batch*N^3 stage buffers for the call and
+ * synchronizes the plan's stream before returning.  Errors: LBO_EINVAL,
+ * LBO_ENOMEM, LBO_ECUDA, and those of the operators. */
+typedef enum { LBO_EVOLVE_QUADRATIC = 0, LBO_EVOLVE_LINEARIZED = 1 } lbo_evolve_mode;
+lbo_status lbo_evolve_homogeneous(lbo_plan *plan, int mode, const double *maxwellian_params, double *f, int batch,
+                                  double dt, int nsteps);
+
 /* Wait for all work queued on the plan's stream; report the first
  * asynchronous CUDA error, if any. */
 lbo_status lbo_plan_sync(lbo_plan *plan);

@@ -34,7 +34,7 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_solver_pair_count", "lbo_solver_train_network", "lbo_solver_get_network", "lbo_solver_set_network",
            "lbo_solver_network_param_count", "lbo_plan_autotune", "lbo_group_create", "lbo_group_set_stream",
            "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy", "lbo_measure_alu_peaks", "lbo_plan_cache_maxwellians",
-           "lbo_dft_axis_tensor")
+           "lbo_dft_axis_tensor", "lbo_evolve_homogeneous")
 
 _lib = None
 
@@ -98,6 +98,8 @@ def load():
     lib.lbo_plan_set_stream.restype = ip
     lib.lbo_apply_linearized.argtypes = [vp, dp, dp, dp, ip]
     lib.lbo_apply_linearized.restype = ip
+    lib.lbo_evolve_homogeneous.argtypes = [vp, ip, dp, dp, ip, ctypes.c_double, ip]
+    lib.lbo_evolve_homogeneous.restype = ip
     lib.lbo_dft_axis_tensor.argtypes = [ip, ip, ip, ip, vp, vp, ip, vp]
     lib.lbo_dft_axis_tensor.restype = ip
     lib.lbo_plan_cache_maxwellians.argtypes = [vp, dp, ip]
@@ -214,7 +216,7 @@ def dft_axis_tensor(N, precision, inverse, axis, x, out):
     _check(load().lbo_dft_axis_tensor(int(N), PRECISION[precision], int(inverse), int(axis),
                                       ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       batch, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
-           "lbo_dft_axis_tensor")
+           "lbo_dft_axis_tensor", "lbo_evolve_homogeneous")
     return out
 
 
@@ -285,6 +287,17 @@ class Plan:
     def noalloc_max_batch(self):
         lib = load()
         return lib.lbo_noalloc_scratch_bytes() // lib.lbo_noalloc_bytes_per_instance(self._h)
+
+    def evolve(self, mode, f, dt, nsteps, params=None):
+        """lbo_evolve_homogeneous: RK4 steps of df/dt = Q(f,f) (mode
+        "quadratic") or L_M[f] (mode "linearized", params the Maxwellians),
+        in place on the device tensor f."""
+        batch = int(f.shape[0]) if len(f.shape) == 4 else 1
+        m = {"quadratic": 0, "linearized": 1}[mode]
+        self._stream(f)
+        _check(load().lbo_evolve_homogeneous(self._h, m, None if params is None else _ptr(params), _ptr(f), batch,
+                                             float(dt), int(nsteps)), "lbo_evolve_homogeneous")
+        return f
 
     def apply_quadratic(self, f, out):
         batch = int(f.shape[0]) if len(f.shape) == 4 else 1
