@@ -216,7 +216,7 @@ def dft_axis_tensor(N, precision, inverse, axis, x, out):
     _check(load().lbo_dft_axis_tensor(int(N), PRECISION[precision], int(inverse), int(axis),
                                       ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       batch, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
-           "lbo_dft_axis_tensor", "lbo_evolve_homogeneous")
+           "lbo_dft_axis_tensor")
     return out
 
 
