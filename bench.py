@@ -714,10 +714,13 @@ def shock_mixed_leg(nx=64, L=8.0, tol=1e-10, seed=5):
             "converged": steps[-1] < tol}
 
 
-def bkw_leg(precision, steps=1, n=64, L=8.0, dt=0.05):
-    """Backward-Euler steps of the homogeneous equation with the quadratic
-    operator (Maxwell molecules, BKW initial data at K = 0.6), Newton with the
-    linearized operator; error against the BKW closed form."""
+def bkw_leg(op_precision, res_precision=None, steps=1, n=64, L=8.0, dt=0.05, tol=1e-10, max_newton=4):
+    """Backward-Euler steps dt of the homogeneous equation with the quadratic
+    operator (Maxwell molecules, N = 64, J = 64, M = 32; BKW initial data at
+    K = 0.6), each solved by Newton with the linearized operator about the
+    state's Maxwellian (op_precision; the residual's Q(f,f) in res_precision
+    when given) until |F| < tol.  Error against the BKW closed form after
+    every step (the time discretisation dominates it: O(dt))."""
     import torch
     from paper_2503_09580_gb300 import lbo
     a = (np.arange(n) - n // 2) * (2 * L / n)
@@ -728,25 +731,64 @@ def bkw_leg(precision, steps=1, n=64, L=8.0, dt=0.05):
         return ((2 * np.pi * K) ** -1.5 * np.exp(-v2 / (2 * K))
                 * ((5 * K - 3) / (2 * K) + (1 - K) / (2 * K * K) * v2))
     t = 6 * np.log(2.5)
-    plan = lbo.Plan(n, L, 1.0, n, hemisphere_p=4, precision=precision)
+    plan = lbo.Plan(n, L, 1.0, n, hemisphere_p=4, precision=op_precision)
     solver = plan.solver(kind="homogeneous", nx=1, dt=dt, krylov_rtol=1e-10, krylov_atol=0.0,
                          krylov_restart=20, krylov_maxit=100, precond="none")
+    rplan = None
+    if res_precision is not None:
+        rplan = lbo.Plan(n, L, 1.0, n, hemisphere_p=4, precision=res_precision)
+        solver.set_residual_plan(rplan)
     fn = torch.from_numpy(bkw(t)[None]).cuda()
     f = fn.clone()
-    newton_ms, iters = [], 0
+    newton_ms, iters, errs, finals = [], [], [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     for _ in range(steps):
-        for _ in range(4):
+        k = 0
+        for k in range(1, max_newton + 1):
             st = solver.newton_step(f, fn)
             newton_ms.append(st["ms_residual"] + st["ms_linear"])
-            iters += 1
+            if st["residual_norm"] < tol:
+                break
+        finals.append(st["residual_norm"])
+        iters.append(k)
         t += dt
         fn.copy_(f)
-    ex = bkw(t)
-    err = float(np.abs(f.cpu().numpy()[0] - ex).max() / np.abs(ex).max())
+        ex = bkw(t)
+        errs.append(float(np.abs(f.cpu().numpy()[0] - ex).max() / np.abs(ex).max()))
+    secs = time.perf_counter() - t0
+    state = f.cpu().numpy()[0]
     solver.close()
     plan.close()
-    return {"newton_step_ms": float(np.median(newton_ms)), "newton_iterations": iters, "steps": steps,
-            "final_residual": st["residual_norm"], "rel_err_vs_bkw": err}
+    if rplan is not None:
+        rplan.close()
+    marks = [i for i in (1, 10, 50, 100, 200) if i <= steps]
+    return {"operator": op_precision, "residual": res_precision or op_precision, "steps": steps,
+            "seconds": secs, "newton_iteration_ms": float(np.median(newton_ms)),
+            "newton_iterations_per_step": float(np.mean(iters)), "max_residual_at_exit": float(max(finals)),
+            "rel_err_vs_bkw_at_step": {str(i): errs[i - 1] for i in marks}, "max_rel_err_vs_bkw": max(errs),
+            "_state": state}
+
+
+def bkw_study(steps=200, ref_steps=20):
+    """Config 3: 200 backward-Euler steps with an FP64-class residual (Q in
+    pairs of FP32) and an FP32 or BF16-split (tensor-core) Jacobian; the
+    all-FP64 run of the first ref_steps steps as the reference state."""
+    out = {"workload": "homogeneous BKW relaxation, Maxwell molecules, N=64, J=64, M=32, backward Euler "
+                       "dt=0.05 from K=0.6, Newton to |F| < 1e-10 (at most 4 iterations per step)"}
+    ref = bkw_leg("fp64", steps=ref_steps)
+    runs = {"fp32_operator_fp32x2_residual": bkw_leg("fp32", "fp32x2", steps=steps),
+            "bf16_split_operator_fp32x2_residual": bkw_leg("bf16_split", "fp32x2", steps=ref_steps),
+            "fp32_operator_fp32_residual": bkw_leg("fp32", steps=ref_steps)}
+    r = ref.pop("_state")
+    out["fp64"] = ref
+    for k, v in runs.items():
+        # the state after ref_steps steps (a short rerun for the long run)
+        s = v["_state"] if v["steps"] == ref_steps else bkw_leg(v["operator"], v["residual"], steps=ref_steps)["_state"]
+        v.pop("_state")
+        v["rel_diff_vs_fp64_at_step_%d" % ref_steps] = float(np.abs(s - r).max() / np.abs(r).max())
+        out[k] = v
+    return out
 
 
 def lin_vs_bin_leg(case, t_end=10.0, dt=0.1, ps=(2, 3, 4), fixes=True):
@@ -1010,9 +1052,7 @@ def run_ours(args, world, rank, local):
         line["n64"] = n64_leg(with_oracle=not args.no_cpu_baseline)
         if args.lin_vs_bin:
             line["lin_vs_bin"] = {"case1": lin_vs_bin_leg(1), "case2": lin_vs_bin_leg(2)}
-        line["bkw_n64"] = {"workload": "homogeneous BKW relaxation, Maxwell molecules, N=64, J=64, M=32, "
-                                       "one backward-Euler step dt=0.05 (4 Newton iterations)",
-                           "fp32": bkw_leg("fp32"), "fp64": bkw_leg("fp64")}
+        line["bkw_n64"] = bkw_study(steps=args.bkw_steps)
     line["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -1036,6 +1076,7 @@ def main():
                     help="run the mixed-N shock leg with this many cells (64 cells: about 2.5 minutes)")
     ap.add_argument("--lin-vs-bin", action="store_true",
                     help="run the homogeneous linearized-vs-quadratic study of Sec. 4.2 (about a minute)")
+    ap.add_argument("--bkw-steps", type=int, default=200, help="backward-Euler steps of the BKW leg")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
