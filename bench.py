@@ -849,6 +849,66 @@ def lin_vs_bin_leg(case, t_end=10.0, dt=0.1, ps=(2, 3, 4), fixes=True):
     return res
 
 
+def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5, max_newton=12, p=4):
+    """Sec. 5.3: Newton iterations of the modified Newton method with the
+    paper's source iteration (nu_j = rho_j, stop at 1e-7 absolute or 1e-3
+    relative) to |R| < 1e-5 for the Couette flow (walls theta = 1 moving at
+    -+u_W along v2; param = u_W) or the Fourier flow (theta_L = 1,
+    theta_R = param, walls at rest); Maxwell molecules, x in [-0.5, 0.5],
+    C = 1, 200 cells, N_p = 16, R = 3.5 (4 for theta_R >= 2.5), L =
+    (3 + sqrt 2) R / 4, 17 radial nodes, initial guess of the supplement
+    (the total density with the wall temperatures interpolated linearly)."""
+    import torch
+    from paper_2503_09580_gb300 import lbo
+    R = 4.0 if (flow == "fourier" and param >= 2.5) else 3.5
+    L = (3 + np.sqrt(2)) * R / 4
+    if flow == "couette":
+        wl, wr, thl, thr = (1.0, 0.0, -param, 0.0), (1.0, 0.0, param, 0.0), 1.0, 1.0
+    else:
+        wl, wr, thl, thr = (1.0, 0.0, 0.0, 0.0), (param, 0.0, 0.0, 0.0), 1.0, param
+    xl, xr, C = -0.5, 0.5, 1.0
+    x = xl + (np.arange(nx) + 0.5) * (xr - xl) / nx
+    a = (np.arange(n) - n // 2) * (2 * L / n)
+    v2 = a[:, None, None] ** 2 + a[None, :, None] ** 2 + a[None, None, :] ** 2
+    th = (xr - x) / (xr - xl) * thl + (x - xl) / (xr - xl) * thr
+    f0 = np.stack([C / (xr - xl) * (2 * np.pi * t) ** -1.5 * np.exp(-v2 / (2 * t)) for t in th])
+    plan = lbo.Plan(n, L, 1.0, 17, R=R, hemisphere_p=p, precision=precision)
+    solver = plan.solver(kind="slab", nx=nx, x_left=xl, x_right=xr, kn=kn, wall_left=wl, wall_right=wr,
+                         total_mass=C, krylov_rtol=1e-3, krylov_atol=1e-7, krylov_maxit=5000, precond="sweep",
+                         inner="source_iteration", nu_scale=1.0)
+    f = torch.from_numpy(f0).cuda()
+    work = torch.empty_like(f)
+    hist, inner, ms_res, ms_lin = [], [], 0.0, 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max_newton + 1):
+        r = solver.residual(f, work)
+        hist.append(r)
+        if r < tol or len(inner) == max_newton:
+            break
+        st = solver.newton_step(f)
+        inner.append(st["krylov_iterations"])
+        ms_res += st["ms_residual"]
+        ms_lin += st["ms_linear"]
+    secs = time.perf_counter() - t0
+    solver.close()
+    plan.close()
+    return {"flow": flow, "kn": kn, "param": param, "R": R, "newton_iterations": len(inner),
+            "converged": hist[-1] < tol, "residual_history": hist, "inner_iterations": inner,
+            "seconds": secs, "share_residual_Q": ms_res / max(ms_res + ms_lin, 1e-9)}
+
+
+def paper_newton_tables(precision="fp64"):
+    """Tables 6 and 8 of Sec. 5.3 on the GPU."""
+    out = {"precision": precision, "couette": {}, "fourier": {}}
+    for kn in (0.1, 1.0, 10.0):
+        for uw in (0.1, 0.2, 0.3, 0.4, 0.5):
+            out["couette"]["Kn=%g,u_W=%g" % (kn, uw)] = steady_counts_leg("couette", kn, uw, precision)
+        for tr in (1.5, 2.0, 2.5, 3.0):
+            out["fourier"]["Kn=%g,theta_R=%g" % (kn, tr)] = steady_counts_leg("fourier", kn, tr, precision)
+    return out
+
+
 def n64_leg(with_oracle, batch=64, steps=3, L=8.0):
     """L[g] applications/s at N = 64 (J = 64, batch 64, benchmark recipe:
     per-instance Maxwellians, quartic polynomial + 1e-3 noise), FP32 and
