@@ -478,6 +478,53 @@ void lbo_group_destroy(lbo_group *group);
 lbo_status lbo_dft_axis_tensor(int N, int precision, int inverse, int axis, const float *in, float *out, int batch,
                                void *stream);
 
+/* ------------------------------------------------------------------------
+ * Primitives on one block of cells of the 1-D slab, for a solver whose cells
+ * are split over several GPUs (a contiguous block per GPU; the host driver
+ * paper_2503_09580_gb300/distributed.py composes them into the modified
+ * Newton / flexible GMRES iteration of Sec. 5 and the supplement, exchanging
+ * boundary cells between neighbours and summing reductions over the GPUs).
+ * Cells follow one another, each N^3 doubles in the centred order; every
+ * array is a device pointer; everything runs on the plan's stream.  h =
+ * 2 box / N is the velocity spacing, dx the cell width.
+ *
+ * lbo_slab_block_transport: out_j = v1^+ (v_j - v_{j-1})/dx + v1^- (v_{j+1} -
+ *   v_j)/dx for the nx cells of the block, the outer values v_{-1} =
+ *   ghost_left and v_nx = ghost_right (one cell each; NULL means 0): a
+ *   neighbour block's boundary cell or a wall's ghost cell (Eq. (5.2)).
+ * lbo_slab_block_sweep: solves (v1^+ D^- + v1^- D^+ + nu_j/kn + shift) z = r
+ *   on the block (the sweep of the source iteration, Eq. (5.7)), with the
+ *   incoming values z_{-1} = in_left (velocities with v1 > 0) and z_nx =
+ *   in_right (v1 < 0) (NULL means 0).  direction = +1 solves only v1 >= 0,
+ *   -1 only v1 < 0, 0 both: a sweep across several blocks passes each
+ *   block's outgoing boundary values to the next block downstream.
+ *   nu: nx doubles (device).
+ * lbo_slab_block_moments: params[5 j + 0..4] = rho, u1, u2, u3, theta of
+ *   cell j (Sec. 2.1; h^3 sums on the grid); nu[j] = rho (NULL allowed).
+ * lbo_slab_cell_flux: *host_out = h^3 sum v1^- x (side 0) or h^3 sum v1^+ x
+ *   (side 1) over one cell (the wall flux of Eq. (5.2)); synchronizes.
+ * lbo_slab_maxwellian_cell: out = scale (2 pi theta)^{-3/2}
+ *   exp(-|v - u|^2/(2 theta)) on one cell (u: 3 host doubles).
+ * lbo_vec_dots: host_out[k] = <V + k ld, y> over len doubles, k < K (at
+ *   most 512), summed in a fixed order; synchronizes.
+ * lbo_vec_axpby: y = a x + b y over len doubles.
+ * lbo_vec_combination: y -= sum_k c_host[k] (V + k ld), k < K (at most 512);
+ *   synchronizes (c_host may be reused at once).
+ * Errors: LBO_EINVAL for bad arguments, LBO_ENOMEM, LBO_ECUDA. */
+lbo_status lbo_slab_block_transport(lbo_plan *plan, const double *v, const double *ghost_left,
+                                    const double *ghost_right, double *out, int nx, double dx);
+lbo_status lbo_slab_block_sweep(lbo_plan *plan, const double *r, const double *nu, const double *in_left,
+                                const double *in_right, double *z, int nx, double dx, double kn, double shift,
+                                int direction);
+lbo_status lbo_slab_block_moments(lbo_plan *plan, const double *f, int nx, double *params, double *nu);
+lbo_status lbo_slab_cell_flux(lbo_plan *plan, const double *cell, int side, double *host_out);
+lbo_status lbo_slab_maxwellian_cell(lbo_plan *plan, double theta, const double *u, double scale, double *out);
+lbo_status lbo_vec_dots(lbo_plan *plan, const double *V, size_t ld, int K, const double *y, size_t len,
+                        double *host_out);
+lbo_status lbo_vec_axpby(lbo_plan *plan, double *y, const double *x, double a, double b, size_t len);
+lbo_status lbo_vec_combination(lbo_plan *plan, double *y, const double *V, size_t ld, int K, const double *c_host,
+                               size_t len);
+
 /* Measured ALU peaks of the current device, the denominators of the
  * library's roofline fractions for ALU-bound kernels (a measurement
  * facility; the paper has no counterpart).  Runs dense chains of FP32 FFMA

@@ -612,6 +612,7 @@ void lbo_plan_destroy(lbo_plan* p) {
   if (p->mc_uh) cudaFree(p->mc_uh);
   if (p->mc_w) cudaFree(p->mc_w);
   if (p->tc_scratch) cudaFree(p->tc_scratch);
+  if (p->blk_red) cudaFree(p->blk_red);
   free_dftmm(p);
   if (p->ws) cudaFree(p->ws);
   if (p->stage_in) cudaFree(p->stage_in);

@@ -38,6 +38,9 @@ struct lbo_plan {
   void* d_tc_err = nullptr;
   void* tc_scratch = nullptr;
   size_t tc_scratch_bytes = 0;
+  // reductions of the slab-block primitives (slab_block.cu)
+  double* blk_red = nullptr;
+  size_t blk_red_cap = 0;
   // cache of the Maxwellian-dependent factors (lbo_plan_cache_maxwellians):
   // valid for apply calls with this params pointer, batch, precision and path
   const double* mc_params = nullptr;

@@ -34,7 +34,9 @@ EXPORTS = ("lbo_plan_create", "lbo_plan_set", "lbo_plan_set_stream", "lbo_apply_
            "lbo_solver_pair_count", "lbo_solver_train_network", "lbo_solver_get_network", "lbo_solver_set_network",
            "lbo_solver_network_param_count", "lbo_plan_autotune", "lbo_group_create", "lbo_group_set_stream",
            "lbo_group_use_graph", "lbo_group_apply_linearized", "lbo_group_destroy", "lbo_measure_alu_peaks", "lbo_plan_cache_maxwellians",
-           "lbo_dft_axis_tensor", "lbo_evolve_homogeneous")
+           "lbo_dft_axis_tensor", "lbo_evolve_homogeneous", "lbo_slab_block_transport", "lbo_slab_block_sweep",
+           "lbo_slab_block_moments", "lbo_slab_cell_flux", "lbo_slab_maxwellian_cell", "lbo_vec_dots",
+           "lbo_vec_axpby", "lbo_vec_combination")
 
 _lib = None
 
@@ -98,6 +100,18 @@ def load():
     lib.lbo_plan_set_stream.restype = ip
     lib.lbo_apply_linearized.argtypes = [vp, dp, dp, dp, ip]
     lib.lbo_apply_linearized.restype = ip
+    cd, sz, dpp = ctypes.c_double, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)
+    lib.lbo_slab_block_transport.argtypes = [vp, vp, vp, vp, vp, ip, cd]
+    lib.lbo_slab_block_sweep.argtypes = [vp, vp, vp, vp, vp, vp, ip, cd, cd, cd, ip]
+    lib.lbo_slab_block_moments.argtypes = [vp, vp, ip, vp, vp]
+    lib.lbo_slab_cell_flux.argtypes = [vp, vp, ip, dpp]
+    lib.lbo_slab_maxwellian_cell.argtypes = [vp, cd, dpp, cd, vp]
+    lib.lbo_vec_dots.argtypes = [vp, vp, sz, ip, vp, sz, dpp]
+    lib.lbo_vec_axpby.argtypes = [vp, vp, vp, cd, cd, sz]
+    lib.lbo_vec_combination.argtypes = [vp, vp, vp, sz, ip, dpp, sz]
+    for fn in ("lbo_slab_block_transport", "lbo_slab_block_sweep", "lbo_slab_block_moments", "lbo_slab_cell_flux",
+               "lbo_slab_maxwellian_cell", "lbo_vec_dots", "lbo_vec_axpby", "lbo_vec_combination"):
+        getattr(lib, fn).restype = ip
     lib.lbo_evolve_homogeneous.argtypes = [vp, ip, dp, dp, ip, ctypes.c_double, ip]
     lib.lbo_evolve_homogeneous.restype = ip
     lib.lbo_dft_axis_tensor.argtypes = [ip, ip, ip, ip, vp, vp, ip, vp]
@@ -190,6 +204,10 @@ def _ptr(a):
     if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
         raise TypeError("expected a C-contiguous float64 array")
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def _optr(a):
+    return None if a is None else _ptr(a)
 
 
 def _check(st, where):
@@ -307,6 +325,60 @@ class Plan:
 
     def sync(self):
         _check(load().lbo_plan_sync(self._h), "lbo_plan_sync")
+
+    # Primitives on one block of slab cells (device tensors, flat or shaped;
+    # distributed.py composes them).  None stands for a zero boundary cell.
+    def block_transport(self, v, ghost_left, ghost_right, out, nx, dx):
+        self._stream(v, out)
+        _check(load().lbo_slab_block_transport(self._h, _ptr(v), _optr(ghost_left), _optr(ghost_right), _ptr(out),
+                                               int(nx), float(dx)), "lbo_slab_block_transport")
+        return out
+
+    def block_sweep(self, r, nu, in_left, in_right, z, nx, dx, kn, shift=0.0, direction=0):
+        self._stream(r, z)
+        _check(load().lbo_slab_block_sweep(self._h, _ptr(r), _ptr(nu), _optr(in_left), _optr(in_right), _ptr(z),
+                                           int(nx), float(dx), float(kn), float(shift), int(direction)),
+               "lbo_slab_block_sweep")
+        return z
+
+    def block_moments(self, f, nx, params, nu=None):
+        self._stream(f, params)
+        _check(load().lbo_slab_block_moments(self._h, _ptr(f), int(nx), _ptr(params), _optr(nu)),
+               "lbo_slab_block_moments")
+        return params
+
+    def cell_flux(self, cell, side):
+        out = ctypes.c_double()
+        self._stream(cell)
+        _check(load().lbo_slab_cell_flux(self._h, _ptr(cell), int(side), ctypes.byref(out)), "lbo_slab_cell_flux")
+        return out.value
+
+    def maxwellian_cell(self, theta, u, scale, out):
+        uu = (ctypes.c_double * 3)(*[float(x) for x in u])
+        self._stream(out)
+        _check(load().lbo_slab_maxwellian_cell(self._h, float(theta), uu, float(scale), _ptr(out)),
+               "lbo_slab_maxwellian_cell")
+        return out
+
+    def vec_dots(self, V, ld, K, y, length):
+        """[<V + k ld, y> for k < K] over length doubles (host floats)."""
+        out = (ctypes.c_double * int(K))()
+        self._stream(V, y)
+        _check(load().lbo_vec_dots(self._h, _ptr(V), int(ld), int(K), _ptr(y), int(length), out), "lbo_vec_dots")
+        return np.frombuffer(out, dtype=np.float64).copy()
+
+    def vec_axpby(self, y, x, a, b, length):
+        self._stream(y, x)
+        _check(load().lbo_vec_axpby(self._h, _ptr(y), _ptr(x), float(a), float(b), int(length)), "lbo_vec_axpby")
+        return y
+
+    def vec_combination(self, y, V, ld, K, c, length):
+        """y -= sum_k c[k] (V + k ld), k < K."""
+        cc = (ctypes.c_double * int(K))(*[float(x) for x in c[:K]])
+        self._stream(y, V)
+        _check(load().lbo_vec_combination(self._h, _ptr(y), _ptr(V), int(ld), int(K), cc, int(length)),
+               "lbo_vec_combination")
+        return y
 
     def autotune(self, params, g, out):
         """lbo_plan_autotune on device tensors; returns the chosen shape."""
