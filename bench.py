@@ -536,10 +536,11 @@ def omega_sweep(tp, tg, tpc, tgc, params, g, pc, gc, stream, steps, with_oracle,
     return res
 
 
-def newton_leg(precision, kn, nx=128, n=32, L=8.0, residual_precision=None):
+def newton_leg(precision, kn, nx=128, n=32, L=8.0, residual_precision=None, device_krylov=False):
     """One modified Newton step of the 1-D steady problem: x in [0, 1], nx
     cells, hard spheres, diffuse walls at theta 1 and 2, initial global
-    Maxwellian rho = 1, u = 0, theta = 1.5, sweep-preconditioned FGMRES."""
+    Maxwellian rho = 1, u = 0, theta = 1.5, sweep-preconditioned FGMRES
+    (device_krylov: the Arnoldi kept on the device, cycles as CUDA graphs)."""
     import torch
     from paper_2503_09580_gb300 import lbo
     a = (np.arange(n) - n // 2) * (2 * L / n)
@@ -549,7 +550,7 @@ def newton_leg(precision, kn, nx=128, n=32, L=8.0, residual_precision=None):
     plan = lbo.Plan(n, L, 0.5, n, precision=precision, hemisphere_p=4)
     solver = plan.solver(kind="slab", nx=nx, x_left=0.0, x_right=1.0, kn=kn, wall_left=(1.0, 0, 0, 0),
                          wall_right=(2.0, 0, 0, 0), total_mass=mass, krylov_rtol=1e-3, krylov_atol=1e-7,
-                         krylov_restart=40, krylov_maxit=400, precond="sweep")
+                         krylov_restart=40, krylov_maxit=400, precond="sweep", device_krylov=device_krylov)
     rplan = None
     if residual_precision is not None:
         # the residual's Q(f,f) in its own precision, the Krylov operator in `precision`
@@ -850,7 +851,8 @@ def lin_vs_bin_leg(case, t_end=10.0, dt=0.1, ps=(2, 3, 4), fixes=True):
 
 
 def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5, max_newton=12, p=4,
-                      wall_flux="analytic", q_sinc=False):
+                      wall_flux="analytic", q_sinc=False, inner="source_iteration", krylov_rtol=1e-3,
+                      jacobian="local_maxwellian"):
     """Sec. 5.3: Newton iterations of the modified Newton method with the
     paper's source iteration (nu_j = rho_j, stop at 1e-7 absolute or 1e-3
     relative) to |R| < 1e-5 for the Couette flow (walls theta = 1 moving at
@@ -878,8 +880,8 @@ def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5,
     f0 = np.stack([C / (xr - xl) * (2 * np.pi * t) ** -1.5 * np.exp(-v2 / (2 * t)) for t in th])
     plan = lbo.Plan(n, L, 1.0, 17, R=R, hemisphere_p=p, precision=precision, q_sinc_quadrature=int(q_sinc))
     solver = plan.solver(kind="slab", nx=nx, x_left=xl, x_right=xr, kn=kn, wall_left=wl, wall_right=wr,
-                         total_mass=C, wall_flux=wall_flux, krylov_rtol=1e-3, krylov_atol=1e-7, krylov_maxit=5000, precond="sweep",
-                         inner="source_iteration", nu_scale=1.0)
+                         total_mass=C, wall_flux=wall_flux, krylov_rtol=krylov_rtol, krylov_atol=1e-7, krylov_maxit=5000,
+                         precond="sweep", inner=inner, nu_scale=1.0, jacobian=jacobian)
     f = torch.from_numpy(f0).cuda()
     work = torch.empty_like(f)
     hist, inner, ms_res, ms_lin = [], [], 0.0, 0.0
@@ -898,6 +900,7 @@ def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5,
     solver.close()
     plan.close()
     return {"flow": flow, "kn": kn, "param": param, "R": R, "wall_flux": wall_flux, "q_sinc": bool(q_sinc),
+            "inner": inner, "krylov_rtol": krylov_rtol, "jacobian": jacobian, "p": p,
             "newton_iterations": len(inner),
             "converged": hist[-1] < tol, "residual_history": hist, "inner_iterations": inner,
             "seconds": secs, "share_residual_Q": ms_res / max(ms_res + ms_lin, 1e-9)}
@@ -1111,7 +1114,9 @@ def run_ours(args, world, rank, local):
         line["newton_step"] = {"workload": "1-D steady slab, 128 cells, N=32, hard spheres, walls theta 1/2, "
                                            "Kn=1, first step from a global Maxwellian theta=1.5",
                                "fp32": newton_leg("fp32", 1.0), "fp64": newton_leg("fp64", 1.0),
-                               "fp32_operator_fp64_residual": newton_leg("fp32", 1.0, residual_precision="fp64")}
+                               "fp32_operator_fp64_residual": newton_leg("fp32", 1.0, residual_precision="fp64"),
+                               "fp32_device_krylov": newton_leg("fp32", 1.0, device_krylov=True),
+                               "fp64_device_krylov": newton_leg("fp64", 1.0, device_krylov=True)}
         line["newton_to_1e-10"] = {
             "workload": "1-D steady slab, 8 cells, N=32, hard spheres, walls theta 1/2, Kn=1, from a global "
                         "Maxwellian; modified steps, then exact-Jacobian steps, until |R| < 1e-10",

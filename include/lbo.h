@@ -301,6 +301,18 @@ typedef struct {
                              the largest loss frequency of the cell, which
                              for hard spheres exceeds rho_j (source
                              iteration then needs nu_scale ~ 2)            */
+  int device_krylov;      /* FGMRES with the modified Jacobian and the NONE
+                             or SWEEP preconditioner (uniform N, not
+                             collecting training pairs, plan profiling off).
+                             0: Arnoldi on the host (coefficients read back
+                             per iteration); 1: Gram-Schmidt coefficients,
+                             norms, Givens rotations and the stopping test
+                             kept on the device, each restart cycle one
+                             eager iteration plus a CUDA graph whose WHILE
+                             node repeats the iteration until the device-side
+                             test ends the cycle (the host reads the cycle's
+                             status and the restart residual only).  Same
+                             arithmetic; other configurations use 0.      */
 } lbo_problem;
 
 typedef struct {

@@ -93,6 +93,7 @@ struct lbo_solver {
   const double* fcur = nullptr;            // state of the current step (exact Jacobian)
   double fnorm = 0;                        // its Euclidean norm
   double *ja = nullptr, *jb = nullptr;     // f +- s v and their Q (exact Jacobian)
+  void* devk = nullptr;                    // device-resident Arnoldi state (solver.cu)
 };
 
 namespace lbo {
@@ -102,6 +103,7 @@ lbo_status network_correction(lbo_solver* S, const double* v, double* z);
 lbo_status network_record(lbo_solver* S, const double* w, const double* zk, double* s_scratch,
                           lbo_status (*sweep)(lbo_solver*, const double*, double*));
 void free_network(lbo_solver* S);
+bool network_collecting(const lbo_solver* S);
 // slab operator A' (with or without the mass border) and y = a x + b y (solver.cu)
 lbo_status solver_apply_op(lbo_solver* S, const double* v, double* out, bool border, bool collisions);
 void solver_axpby(lbo_solver* S, double* y, const double* x, double a, double b);

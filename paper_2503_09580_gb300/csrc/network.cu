@@ -3,8 +3,13 @@
 // the upwind sweep (the synthetic acceleration the paper points to for small
 // Kn, Sec. 5.2; the network itself has no counterpart in the paper).
 //
-//   features of a vector v (per cell j): x_j = [m(v_j), m(s_j)], s = sweep(v),
-//     m(y)_a = h^3 sum_v phi_a(v) y(v), phi = {1, v1, v2, v3, |v|^2};
+//   features of a vector v (per cell j): x_j = [m(r_j), m(s_j)], s = sweep(v),
+//     r = v - A_T s the part of v the sweep leaves unexplained, A_T the
+//     operator without its collision term (upwind transport, wall ghosts,
+//     mass border, shift): for the collision invariants W^T A = W^T A_T up
+//     to the discrete operator's conservation, so the five low moments of r
+//     drive the macroscopic error of s exactly as in synthetic acceleration;
+//     m(y)_a = h^3 sum_v phi_a(v) y(v), phi = 13 moments (below);
 //   network: h1 = tanh(b1 + W1 * x), y = b2 + W2 * h1 (width-5 convolutions
 //     over cells, zero padding, H hidden channels, 5 outputs);
 //   preconditioner: z = s + sum_a c_{j,a} phi_a(v) M_j(v),
@@ -33,6 +38,8 @@ struct NetState {
   float scales[31] = {};  // cs_in[26], cs_out[5]
   float* feat = nullptr;     // [nx][26] features of the vector being preconditioned
   float* corr = nullptr;     // [nx][5]
+  double* r = nullptr;       // v - A_T s of the vector being preconditioned or recorded
+  float* dev_sc = nullptr;   // scales on the device, then sigma of the current vector
   bool trained = false;
 };
 
@@ -393,23 +400,69 @@ NetState* state(lbo_solver* S) { return (NetState*)S->netstate; }
 }  // namespace
 
 // z (already the sweep of v) += learned macroscopic correction
+// sigma = RMS of the sweep moments (feature channels NMOM..NMOM+4) and the
+// normalised features x / (sigma cs_in); one block
+__global__ void k_feat_norm(float* __restrict__ feat, int nx, float* __restrict__ sc) {
+  __shared__ double sh[32];
+  double a = 0;
+  for (int i = threadIdx.x; i < nx * 5; i += blockDim.x) {
+    const double x = feat[(i / 5) * CIN + NMOM + i % 5];
+    a += x * x;
+  }
+  const double tot = bsum(a, sh);
+  __shared__ float sigma;
+  if (threadIdx.x == 0) {
+    sigma = (float)sqrt(tot / (5.0 * nx)) + 1e-30f;
+    sc[CIN + COUT] = sigma;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nx * CIN; i += blockDim.x) feat[i] = feat[i] / sigma / sc[i % CIN];
+}
+
+// c = sigma cs_out (.) y
+__global__ void k_corr_scale(float* __restrict__ corr, int nx, const float* __restrict__ sc) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx * COUT; i += gridDim.x * blockDim.x)
+    corr[i] *= sc[CIN + COUT] * sc[CIN + i % COUT];
+}
+
+// ns->r = v - A_T s (the operator without collisions)
+static lbo_status transport_residual(lbo_solver* S, NetState* ns, const double* v, const double* s) {
+  if (!ns->r) {
+    cudaError_t e = cudaMalloc(&ns->r, sizeof(double) * S->len);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error_text("network: residual buffer");
+      return LBO_ENOMEM;
+    }
+  }
+  lbo_status st = solver_apply_op(S, s, ns->r, true, false);
+  if (st != LBO_OK) return st;
+  solver_axpby(S, ns->r, v, 1.0, -1.0);
+  return LBO_OK;
+}
+
+static lbo_status upload_scales(NetState* ns) {
+  if (!ns->dev_sc) {
+    cudaError_t e = cudaMalloc(&ns->dev_sc, sizeof(float) * (CIN + COUT + 1));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error_text("network: scales");
+      return LBO_ENOMEM;
+    }
+  }
+  cudaError_t e = cudaMemcpy(ns->dev_sc, ns->scales, sizeof(float) * (CIN + COUT), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "network scales");
+}
+
 lbo_status network_correction(lbo_solver* S, const double* v, double* z) {
   NetState* ns = state(S);
   if (!ns || !ns->trained) return LBO_OK;
   cudaStream_t s = S->plan->stream;
   const int nx = S->nx, H = ns->hidden;
-  k_cell_features<<<nx, 256, 0, s>>>(v, z, nullptr, S->params, S->N, S->h, ns->feat, nullptr);
-  // sigma = RMS of the sweep moments, then the normalised forward pass
-  std::vector<float> xf((size_t)nx * CIN);
-  cudaMemcpyAsync(xf.data(), ns->feat, sizeof(float) * xf.size(), cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
-  double ss = 0;
-  for (int j = 0; j < nx; ++j)
-    for (int a = NMOM; a < NMOM + 5; ++a) ss += (double)xf[j * CIN + a] * xf[j * CIN + a];
-  const float sigma = (float)std::sqrt(ss / (5.0 * nx)) + 1e-30f;
-  for (int j = 0; j < nx; ++j)
-    for (int c = 0; c < CIN; ++c) xf[j * CIN + c] = xf[j * CIN + c] / sigma / ns->scales[c];
-  cudaMemcpyAsync(ns->feat, xf.data(), sizeof(float) * xf.size(), cudaMemcpyHostToDevice, s);
+  lbo_status st = transport_residual(S, ns, v, z);
+  if (st != LBO_OK) return st;
+  k_cell_features<<<nx, 256, 0, s>>>(ns->r, z, nullptr, S->params, S->N, S->h, ns->feat, nullptr);
+  k_feat_norm<<<1, 256, 0, s>>>(ns->feat, nx, ns->dev_sc);
   if (H == 0) {
     k_lin_fwd<<<blocks_for((size_t)nx * COUT), 256, 0, s>>>(ns->theta, nx, ns->feat, 1, nullptr, ns->corr, nullptr,
                                                           nullptr);
@@ -418,15 +471,15 @@ lbo_status network_correction(lbo_solver* S, const double* v, double* z) {
     k_fwd1<<<blocks_for((size_t)nx * H), 256, 0, s>>>(ns->theta, H, ns->feat, 1, nx, h1);
     k_fwd2<<<blocks_for((size_t)nx * COUT), 256, 0, s>>>(ns->theta, H, h1, 1, nx, nullptr, ns->corr, nullptr, nullptr);
   }
-  std::vector<float> c((size_t)nx * COUT);
-  cudaMemcpyAsync(c.data(), ns->corr, sizeof(float) * c.size(), cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
-  for (int j = 0; j < nx; ++j)
-    for (int a = 0; a < COUT; ++a) c[j * COUT + a] *= sigma * ns->scales[CIN + a];
-  cudaMemcpyAsync(ns->corr, c.data(), sizeof(float) * c.size(), cudaMemcpyHostToDevice, s);
+  k_corr_scale<<<blocks_for((size_t)nx * COUT), 256, 0, s>>>(ns->corr, nx, ns->dev_sc);
   LBO_LAUNCH(S->plan, "net_lift", s, k_lift, blocks_for(S->len), 256, 0, z, ns->corr, S->params, S->N, nx, S->h);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LBO_OK : cuda_fail(e, "network correction");
+}
+
+bool network_collecting(const lbo_solver* S) {
+  const NetState* ns = (const NetState*)S->netstate;
+  return ns && ns->collecting && ns->pairs < ns->max_pairs;
 }
 
 // record a training pair (w = A z_k, z_k); s is scratch for sweep(w)
@@ -435,9 +488,10 @@ lbo_status network_record(lbo_solver* S, const double* w, const double* zk, doub
   NetState* ns = state(S);
   if (!ns || !ns->collecting || ns->pairs >= ns->max_pairs) return LBO_OK;
   lbo_status st = sweep(S, w, s_scratch);
+  if (st == LBO_OK) st = transport_residual(S, ns, w, s_scratch);
   if (st != LBO_OK) return st;
   const int nx = S->nx;
-  k_cell_features<<<nx, 256, 0, S->plan->stream>>>(w, s_scratch, zk, S->params, S->N, S->h,
+  k_cell_features<<<nx, 256, 0, S->plan->stream>>>(ns->r, s_scratch, zk, S->params, S->N, S->h,
                                                     ns->store_x + (size_t)ns->pairs * nx * CIN,
                                                     ns->store_t + (size_t)ns->pairs * nx * COUT);
   ns->pairs++;
@@ -448,9 +502,10 @@ lbo_status network_record(lbo_solver* S, const double* w, const double* zk, doub
 void free_network(lbo_solver* S) {
   NetState* ns = state(S);
   if (!ns) return;
-  float* bufs[] = {ns->store_x, ns->store_t, ns->theta, ns->feat, ns->corr};
+  float* bufs[] = {ns->store_x, ns->store_t, ns->theta, ns->feat, ns->corr, ns->dev_sc};
   for (float* p : bufs)
     if (p) cudaFree(p);
+  if (ns->r) cudaFree(ns->r);
   delete ns;
   S->netstate = nullptr;
 }
@@ -620,6 +675,7 @@ lbo_status lbo_solver_train_network(lbo_solver* S, int hidden, int epochs, doubl
       k_adam<<<blocks_for(np), 256, 0, s>>>(ns->theta, g, m, v, (int)np, (float)lr, b1, b2, 1.f - c1, 1.f - c2);
     }
     if (result == LBO_OK) result = loss_grad_device(hidden, ns->theta, xn, tn, P, nx, h1, dz1, y, dy, se, dl, g, s);
+    if (result == LBO_OK) result = upload_scales(ns);
     if (result == LBO_OK) ns->trained = true;
     if (result == LBO_OK && final_loss) {
       e = cudaMemcpyAsync(final_loss, dl, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -664,6 +720,8 @@ lbo_status lbo_solver_set_network(lbo_solver* S, int hidden, const float* params
   if (e == cudaSuccess) e = cudaMemcpy(ns->theta, params, sizeof(float) * np, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "set network");
   std::memcpy(ns->scales, scales, sizeof(ns->scales));
+  lbo_status st = upload_scales(ns);
+  if (st != LBO_OK) return st;
   ns->trained = true;
   return LBO_OK;
 }

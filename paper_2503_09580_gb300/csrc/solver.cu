@@ -471,6 +471,382 @@ lbo_status fgmres(lbo_solver* S, lbo_newton_stats* ns) {
   return LBO_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Device-resident Arnoldi (problem.device_krylov = 1).  The Gram-Schmidt
+// coefficients, the norms, the Givens rotations and the stopping test stay
+// in device memory; a restart cycle is one eagerly launched iteration (it
+// sizes every workspace of the operator) followed by a CUDA graph whose
+// WHILE node repeats the iteration body until the device-side test clears
+// its condition.  The host reads nothing inside a cycle: the cycle's
+// status once at its end, and the restart residual norm.  The body reads
+// the iteration index k from device memory, so one captured body serves
+// every k (V_k and Z_k pass through two fixed vectors).  Same arithmetic as
+// fgmres() above; scope: modified Jacobian, NONE / SWEEP preconditioners,
+// uniform N, no training-pair collection.
+
+struct DevArnoldi {
+  double* H = nullptr;  // (m + 1) x m, then cs[m], sn[m], gam[m + 1], hv[m + 1], c[m], sc[4]
+  double *cs = nullptr, *sn = nullptr, *gam = nullptr, *hv = nullptr, *c = nullptr, *sc = nullptr;
+  int* ik = nullptr;       // k, iterations, status, k_used, continue, maxit
+  int* host_ik = nullptr;  // pinned copy read at the end of a cycle
+  double *vin = nullptr, *zbuf = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+};
+enum { IK_K = 0, IK_ITS, IK_STATUS, IK_USED, IK_CONT, IK_MAXIT, IK_N };
+enum { DS_RUNNING = 0, DS_CONVERGED = 1, DS_MAXIT = 2, DS_NAN = 3 };
+
+// dst = base + (k + ofs) ld
+__global__ void k_get_col(double* __restrict__ dst, const double* __restrict__ base, size_t ld,
+                          const int* __restrict__ ik, int ofs, size_t len) {
+  const double* src = base + (size_t)(ik[IK_K] + ofs) * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+// base + (k + ofs) ld = src, or src / *hn when hn is given (left alone if *hn <= 0)
+__global__ void k_put_col(double* __restrict__ base, size_t ld, const int* __restrict__ ik, int ofs,
+                          const double* __restrict__ src, const double* __restrict__ hn, size_t len) {
+  double a = 1.0;
+  if (hn) {
+    if (!(*hn > 0)) return;
+    a = 1.0 / *hn;
+  }
+  double* dst = base + (size_t)(ik[IK_K] + ofs) * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = hn ? src[e] * a : src[e];
+}
+
+// part[b K + i] = block b's share of <V_i, y>, K = *Kp + Kadd
+__global__ void __launch_bounds__(RED_THREADS) k_dots_dev(const double* __restrict__ V, size_t ld,
+                                                          const int* __restrict__ Kp, int Kadd,
+                                                          const double* __restrict__ y, size_t len,
+                                                          double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int K = *Kp + Kadd;
+  for (int k0 = 0; k0 < K; k0 += DOT_TILE) {
+    double acc[DOT_TILE];
+#pragma unroll
+    for (int t = 0; t < DOT_TILE; ++t) acc[t] = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x) {
+      const double ye = y[e];
+#pragma unroll
+      for (int t = 0; t < DOT_TILE; ++t)
+        if (k0 + t < K) acc[t] += V[(size_t)(k0 + t) * ld + e] * ye;
+    }
+#pragma unroll
+    for (int t = 0; t < DOT_TILE; ++t) {
+      double s = block_sum(acc[t], sh);
+      if (threadIdx.x == 0 && k0 + t < K) part[blockIdx.x * K + k0 + t] = s;
+    }
+  }
+}
+
+// hv[i] = sum of the parts (fixed order), i <= k; column k of H set (pass 0) or
+// increased (pass 1) by hv
+__global__ void k_reduce_h(const double* __restrict__ part, int nb, const int* __restrict__ ik, double* __restrict__ hv,
+                           double* __restrict__ H, int m, int pass) {
+  const int k = ik[IK_K], K = k + 1;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double s = 0;
+    for (int b = 0; b < nb; ++b) s += part[b * K + i];
+    hv[i] = s;
+    H[(size_t)i * m + k] = pass == 0 ? s : H[(size_t)i * m + k] + s;
+  }
+}
+
+// out = sqrt(sum of the parts)
+__global__ void k_norm_finish(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    *out = sqrt(s);
+  }
+}
+
+// y -= sum_i c[i] V_i, i < *Kp + Kadd
+__global__ void k_sub_comb_dev(double* __restrict__ y, const double* __restrict__ V, size_t ld,
+                               const int* __restrict__ Kp, int Kadd, const double* __restrict__ c, size_t len) {
+  const int K = *Kp + Kadd;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int k = 0; k < K; ++k) s += c[k] * V[(size_t)k * ld + e];
+    y[e] -= s;
+  }
+}
+
+// Start of a cycle: gam = beta e_0, k = 0, status running.
+__global__ void k_cycle_init(double* __restrict__ gam, double* __restrict__ sc, int* __restrict__ ik, int m,
+                             double beta, double tol, int iterations, int maxit) {
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) gam[i] = i == 0 ? beta : 0.0;
+  if (threadIdx.x == 0) {
+    sc[1] = tol;
+    ik[IK_K] = 0;
+    ik[IK_ITS] = iterations;
+    ik[IK_STATUS] = DS_RUNNING;
+    ik[IK_USED] = 0;
+    ik[IK_CONT] = 0;
+    ik[IK_MAXIT] = maxit;
+  }
+}
+
+// H(k+1, k) = hn, the earlier rotations and a new one on column k, the
+// residual estimate gam(k+1) against tol; decides whether the cycle goes on
+// (condition of the WHILE node when launched inside the graph).
+__global__ void k_givens(double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                         double* __restrict__ gam, const double* __restrict__ sc, int* __restrict__ ik, int m,
+                         cudaGraphConditionalHandle cond, int in_graph) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = ik[IK_K];
+  const double hn = sc[2], tol = sc[1];
+  int cont = 0;
+  H[(size_t)(k + 1) * m + k] = hn;
+  if (!isfinite(hn)) {
+    ik[IK_STATUS] = DS_NAN;
+    ik[IK_USED] = k;
+  } else {
+    for (int i = 0; i < k; ++i) {
+      const double a = H[(size_t)i * m + k], b = H[(size_t)(i + 1) * m + k];
+      H[(size_t)i * m + k] = cs[i] * a + sn[i] * b;
+      H[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
+    }
+    const double a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
+    const double rr = hypot(a, b);
+    cs[k] = rr > 0 ? a / rr : 1.0;
+    sn[k] = rr > 0 ? b / rr : 0.0;
+    H[(size_t)k * m + k] = rr;
+    H[(size_t)(k + 1) * m + k] = 0.0;
+    gam[k + 1] = -sn[k] * gam[k];
+    gam[k] = cs[k] * gam[k];
+    const int its = ++ik[IK_ITS];
+    if (fabs(gam[k + 1]) <= tol || hn == 0.0) {
+      ik[IK_STATUS] = DS_CONVERGED;
+      ik[IK_USED] = k + 1;
+    } else if (its >= ik[IK_MAXIT]) {
+      ik[IK_STATUS] = DS_MAXIT;
+      ik[IK_USED] = k + 1;
+    } else if (k + 1 == m) {
+      ik[IK_USED] = m;
+    } else {
+      cont = 1;
+      ik[IK_K] = k + 1;
+    }
+  }
+  ik[IK_CONT] = cont;
+  if (in_graph) cudaGraphSetConditional(cond, cont);
+}
+
+// first node of the cycle graph: the WHILE condition from the eager iteration
+__global__ void k_set_cond(cudaGraphConditionalHandle cond, const int* __restrict__ ik) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(cond, ik[IK_CONT]);
+}
+
+// c = -y with H(0:k, 0:k) y = gam(0:k), k = ik[IK_USED] (back substitution)
+__global__ void k_backsolve(const double* __restrict__ H, const double* __restrict__ gam, double* __restrict__ c,
+                            const int* __restrict__ ik, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = ik[IK_USED];
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = gam[i];
+    for (int j = i + 1; j < k; ++j) acc += H[(size_t)i * m + j] * c[j];  // c holds -y
+    c[i] = H[(size_t)i * m + i] != 0 ? -acc / H[(size_t)i * m + i] : 0.0;
+  }
+}
+
+lbo_status dev_alloc(lbo_solver* S, DevArnoldi** out) {
+  if (S->devk) {
+    *out = (DevArnoldi*)S->devk;
+    return LBO_OK;
+  }
+  DevArnoldi* D = new DevArnoldi();
+  const int m = S->m;
+  const size_t nsmall = (size_t)(m + 1) * m + m + m + (m + 1) + (m + 1) + m + 4;
+  cudaError_t e = cudaMalloc(&D->H, sizeof(double) * nsmall);
+  if (e == cudaSuccess) e = cudaMalloc(&D->ik, sizeof(int) * IK_N);
+  if (e == cudaSuccess) e = cudaMallocHost(&D->host_ik, sizeof(int) * IK_N);
+  if (e == cudaSuccess) e = cudaMalloc(&D->vin, sizeof(double) * S->len);
+  if (e == cudaSuccess) e = cudaMalloc(&D->zbuf, sizeof(double) * S->len);
+  S->devk = D;  // freed with the solver, also on failure
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error_text("device Krylov buffers");
+    return LBO_ENOMEM;
+  }
+  D->cs = D->H + (size_t)(m + 1) * m;
+  D->sn = D->cs + m;
+  D->gam = D->sn + m;
+  D->hv = D->gam + (m + 1);
+  D->c = D->hv + (m + 1);
+  D->sc = D->c + m;
+  *out = D;
+  return LBO_OK;
+}
+
+void dev_drop_graph(DevArnoldi* D) {
+  if (D->exec) cudaGraphExecDestroy(D->exec);
+  if (D->graph) cudaGraphDestroy(D->graph);
+  D->exec = nullptr;
+  D->graph = nullptr;
+}
+
+// One Arnoldi iteration on device state (k read from device memory).
+lbo_status dev_iteration(lbo_solver* S, DevArnoldi* D, int in_graph) {
+  cudaStream_t s = S->plan->stream;
+  const size_t len = S->len;
+  const int m = S->m;
+  LBO_LAUNCH(S->plan, "krylov_get", s, k_get_col, grid_for(len), 256, 0, D->vin, S->V, len, D->ik, 0, len);
+  lbo_status st = apply_precond(S, D->vin, D->zbuf);
+  if (st != LBO_OK) return st;
+  LBO_LAUNCH(S->plan, "krylov_put", s, k_put_col, grid_for(len), 256, 0, S->Z, len, D->ik, 0, D->zbuf,
+             (const double*)nullptr, len);
+  st = apply_op(S, D->zbuf, S->w);
+  if (st != LBO_OK) return st;
+  for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, two passes, FP64
+    LBO_LAUNCH(S->plan, "krylov_dots", s, k_dots_dev, RED_BLOCKS, RED_THREADS, 0, S->V, len, D->ik + IK_K, 1,
+               S->w, len, S->part);
+    LBO_LAUNCH(S->plan, "krylov_reduce_h", s, k_reduce_h, 1, 256, 0, S->part, RED_BLOCKS, D->ik, D->hv, D->H, m,
+               pass);
+    LBO_LAUNCH(S->plan, "krylov_sub", s, k_sub_comb_dev, grid_for(len), 256, 0, S->w, S->V, len, D->ik + IK_K, 1,
+               D->hv, len);
+  }
+  LBO_LAUNCH(S->plan, "krylov_dots", s, k_dots, RED_BLOCKS, RED_THREADS, 0, S->w, (size_t)0, 1, S->w, len,
+             S->part);
+  LBO_LAUNCH(S->plan, "krylov_norm", s, k_norm_finish, 1, 32, 0, S->part, RED_BLOCKS, D->sc + 2);
+  LBO_LAUNCH(S->plan, "krylov_put", s, k_put_col, grid_for(len), 256, 0, S->V, len, D->ik, 1, S->w,
+             (const double*)(D->sc + 2), len);
+  LBO_LAUNCH(S->plan, "krylov_givens", s, k_givens, 1, 32, 0, D->H, D->cs, D->sn, D->gam, D->sc, D->ik, m, D->cond,
+             in_graph);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "device Arnoldi iteration");
+}
+
+// The cycle graph [k_set_cond] -> WHILE { dev_iteration }, captured on a
+// private stream (the plan's may be the legacy default stream) and
+// instantiated; kernel parameters (shift, the cached Maxwellians, buffers)
+// are those of the current Newton step.
+lbo_status dev_capture(lbo_solver* S, DevArnoldi* D) {
+  dev_drop_graph(D);
+  cudaError_t e = cudaGraphCreate(&D->graph, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&D->cond, D->graph, 0, 0);
+  cudaGraphNode_t n_set = nullptr, n_loop = nullptr;
+  if (e == cudaSuccess) {
+    void* args[] = {(void*)&D->cond, (void*)&D->ik};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k_set_cond;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&n_set, D->graph, nullptr, 0, &kp);
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = D->cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&n_loop, D->graph, &n_set, nullptr, 1, &cp);
+  cudaStream_t cap = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    dev_drop_graph(D);
+    return cuda_fail(e, "device Krylov graph");
+  }
+  cudaStream_t own = S->plan->stream;
+  S->plan->stream = cap;
+  lbo_status st = LBO_OK;
+  e = cudaStreamBeginCaptureToGraph(cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = dev_iteration(S, D, 1);
+    cudaGraph_t body = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &body);
+    if (st == LBO_OK && e2 != cudaSuccess) e = e2;
+  }
+  S->plan->stream = own;
+  cudaStreamDestroy(cap);
+  if (e == cudaSuccess && st == LBO_OK) e = cudaGraphInstantiate(&D->exec, D->graph, 0);
+  if (e != cudaSuccess || st != LBO_OK) {
+    cudaGetLastError();
+    dev_drop_graph(D);
+    return st != LBO_OK ? st : cuda_fail(e, "device Krylov graph capture");
+  }
+  return LBO_OK;
+}
+
+// Restarted FGMRES with the device-resident Arnoldi: same iteration and
+// stopping tests as fgmres(), host reads only at the ends of cycles.
+lbo_status fgmres_device(lbo_solver* S, lbo_newton_stats* ns) {
+  DevArnoldi* D = nullptr;
+  lbo_status st = dev_alloc(S, &D);
+  if (st != LBO_OK) return st;
+  const size_t len = S->len;
+  cudaStream_t s = S->plan->stream;
+  cudaMemsetAsync(S->x, 0, sizeof(double) * len, s);
+  double rhs_norm = norm2(S, S->rhs, &st);
+  if (st != LBO_OK) return st;
+  ns->rhs_norm = rhs_norm * std::sqrt(S->wnorm);
+  const double tol = std::fmax(S->pb.krylov_rtol * rhs_norm, S->pb.krylov_atol / std::sqrt(S->wnorm));
+  ns->krylov_iterations = 0;
+  ns->restarts = 0;
+  ns->status = LBO_OK;
+  if (rhs_norm == 0.0) return LBO_OK;
+  if (!std::isfinite(rhs_norm)) {
+    ns->status = LBO_ENAN;
+    return LBO_ENAN;
+  }
+  cudaMemcpyAsync(S->V, S->rhs, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+  double beta = rhs_norm;
+  bool captured = false;
+  for (;;) {
+    LBO_LAUNCH(S->plan, "solver_scale", s, k_scale, grid_for(len), 256, 0, S->V, 1.0 / beta, len);
+    cudaMemsetAsync(D->H, 0, sizeof(double) * (size_t)(S->m + 1) * S->m, s);
+    LBO_LAUNCH(S->plan, "krylov_init", s, k_cycle_init, 1, 256, 0, D->gam, D->sc, D->ik, S->m, beta, tol,
+               ns->krylov_iterations, S->pb.krylov_maxit);
+    st = dev_iteration(S, D, 0);  // k = 0, eagerly: sizes the operator's workspaces
+    if (st != LBO_OK) return st;
+    if (!captured) {
+      st = dev_capture(S, D);
+      if (st != LBO_OK) return st;
+      captured = true;
+    }
+    cudaError_t e = cudaGraphLaunch(D->exec, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D->host_ik, D->ik, sizeof(int) * IK_N, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "device Krylov cycle");
+    ns->krylov_iterations = D->host_ik[IK_ITS];
+    const int status = D->host_ik[IK_STATUS];
+    if (status == DS_NAN) {
+      ns->status = LBO_ENAN;
+      return LBO_ENAN;
+    }
+    // x += Z y,  H(0:k,0:k) y = gam(0:k)
+    LBO_LAUNCH(S->plan, "krylov_backsolve", s, k_backsolve, 1, 32, 0, D->H, D->gam, D->c, D->ik, S->m);
+    LBO_LAUNCH(S->plan, "krylov_sub", s, k_sub_comb_dev, grid_for(len), 256, 0, S->x, S->Z, len, D->ik + IK_USED, 0,
+               D->c, len);
+    if (status == DS_CONVERGED) break;
+    if (status == DS_MAXIT) {
+      ns->status = LBO_ENOTCONV;
+      break;
+    }
+    // restart from the true residual
+    ns->restarts++;
+    st = apply_op(S, S->x, S->w);
+    if (st != LBO_OK) return st;
+    cudaMemcpyAsync(S->V, S->rhs, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    LBO_LAUNCH(S->plan, "solver_axpby", s, k_axpby, grid_for(len), 256, 0, S->V, S->w, -1.0, 1.0, len);
+    beta = norm2(S, S->V, &st);
+    if (st != LBO_OK) return st;
+    if (beta <= tol) break;
+  }
+  return LBO_OK;
+}
+
+bool device_krylov_applies(const lbo_solver* S) {
+  return S->pb.device_krylov == 1 && !S->mixed && S->pb.jacobian == 0 && !S->plan->profiling &&
+         (S->pb.precond == LBO_PRECOND_NONE || S->pb.precond == LBO_PRECOND_SWEEP) && !network_collecting(S);
+}
+
 // Source iteration (Sec. 5.2 and the supplement's discrete form): with S the
 // operator of the upwind sweep, S g_{l+1} = (S - A) g_l + rhs from g_0 = 0,
 // i.e. the Richardson iteration g += P(rhs - A g) with P the preconditioner
@@ -635,7 +1011,7 @@ lbo_status lbo_solver_create(const lbo_problem* pb, lbo_plan* plan, lbo_solver**
   }
   if (pb->precond < 0 || pb->precond > 3) return LBO_EINVAL;
   if (pb->line_search < 0 || pb->line_search > 60 || !(pb->pseudo_dt >= 0)) return LBO_EINVAL;
-  if (pb->jacobian < 0 || pb->jacobian > 1) return LBO_EINVAL;
+  if (pb->jacobian < 0 || pb->jacobian > 1 || pb->device_krylov < 0 || pb->device_krylov > 1) return LBO_EINVAL;
   if (pb->coarse_operator < 0 || pb->coarse_operator > 1) return LBO_EINVAL;
   if (pb->inner_solver < 0 || pb->inner_solver > 1 || !(pb->nu_scale >= 0) || !std::isfinite(pb->nu_scale))
     return LBO_EINVAL;
@@ -817,7 +1193,10 @@ lbo_status lbo_newton_step(lbo_solver* S, double* f, const double* f_prev, lbo_n
       st = coarse_assemble(S, bordered(S));
       if (st == LBO_OK && !coarse_valid(S)) ns->fallbacks++;  // singular: sweep alone
     }
-    if (st == LBO_OK) st = S->pb.inner_solver == 1 ? source_iteration(S, ns) : fgmres(S, ns);
+    if (st == LBO_OK)
+      st = S->pb.inner_solver == 1     ? source_iteration(S, ns)
+           : device_krylov_applies(S) ? fgmres_device(S, ns)
+                                      : fgmres(S, ns);
     if (st == LBO_OK || st == LBO_ENOTCONV) {
       // FP64 true residual of the linear system
       lbo_status st2 = apply_op(S, S->x, S->w);
@@ -871,6 +1250,16 @@ void lbo_solver_destroy(lbo_solver* S) {
                     S->jb,     S->Qf, S->params, S->nu, S->WL,  S->WR, S->part, S->res};
   for (double* p : bufs)
     if (p) cudaFree(p);
+  if (S->devk) {
+    DevArnoldi* D = (DevArnoldi*)S->devk;
+    dev_drop_graph(D);
+    if (D->H) cudaFree(D->H);
+    if (D->ik) cudaFree(D->ik);
+    if (D->host_ik) cudaFreeHost(D->host_ik);
+    if (D->vin) cudaFree(D->vin);
+    if (D->zbuf) cudaFree(D->zbuf);
+    delete D;
+  }
   free_network(S);
   free_coarse(S);
   free_mixed(S);

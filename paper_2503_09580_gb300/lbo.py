@@ -52,7 +52,7 @@ class Problem(ctypes.Structure):
                 ("inflow_right", ctypes.c_double * 5), ("line_search", ctypes.c_int),
                 ("pseudo_dt", ctypes.c_double), ("coarse_moments", ctypes.c_int),
                 ("jacobian", ctypes.c_int), ("coarse_operator", ctypes.c_int), ("inner_solver", ctypes.c_int),
-                ("nu_scale", ctypes.c_double)]
+                ("nu_scale", ctypes.c_double), ("device_krylov", ctypes.c_int)]
 
 
 class NewtonStats(ctypes.Structure):
@@ -435,7 +435,7 @@ class Solver:
                  wall_flux="analytic", dt=0.0, krylov_rtol=1e-3, krylov_atol=1e-7, krylov_restart=30,
                  krylov_maxit=300, precond="sweep", inflow_left=None, inflow_right=None, line_search=0,
                  pseudo_dt=0.0, coarse_moments=5, jacobian="local_maxwellian",
-                 coarse_operator="galerkin", inner="fgmres", nu_scale=1.0, _mixed=None):
+                 coarse_operator="galerkin", inner="fgmres", nu_scale=1.0, device_krylov=False, _mixed=None):
         lib = load()
         pb = Problem()
         pb.kind = PROBLEM[kind]
@@ -463,6 +463,7 @@ class Solver:
         pb.coarse_operator = {"galerkin": 0, "transport": 1}[coarse_operator]
         pb.inner_solver = {"fgmres": 0, "source_iteration": 1}[inner]
         pb.nu_scale = float(nu_scale)
+        pb.device_krylov = 1 if device_krylov else 0
         h = ctypes.c_void_p()
         if _mixed is None:
             _check(lib.lbo_solver_create(ctypes.byref(pb), plan._h, ctypes.byref(h)), "lbo_solver_create")
