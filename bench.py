@@ -851,7 +851,7 @@ def lin_vs_bin_leg(case, t_end=10.0, dt=0.1, ps=(2, 3, 4), fixes=True):
 
 
 def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5, max_newton=12, p=4,
-                      wall_flux="analytic", q_sinc=False, inner="source_iteration", krylov_rtol=1e-3,
+                      wall_flux="analytic", q_sinc=False, inner_solver="source_iteration", krylov_rtol=1e-3,
                       jacobian="local_maxwellian"):
     """Sec. 5.3: Newton iterations of the modified Newton method with the
     paper's source iteration (nu_j = rho_j, stop at 1e-7 absolute or 1e-3
@@ -881,7 +881,7 @@ def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5,
     plan = lbo.Plan(n, L, 1.0, 17, R=R, hemisphere_p=p, precision=precision, q_sinc_quadrature=int(q_sinc))
     solver = plan.solver(kind="slab", nx=nx, x_left=xl, x_right=xr, kn=kn, wall_left=wl, wall_right=wr,
                          total_mass=C, wall_flux=wall_flux, krylov_rtol=krylov_rtol, krylov_atol=1e-7, krylov_maxit=5000,
-                         precond="sweep", inner=inner, nu_scale=1.0, jacobian=jacobian)
+                         precond="sweep", inner=inner_solver, nu_scale=1.0, jacobian=jacobian)
     f = torch.from_numpy(f0).cuda()
     work = torch.empty_like(f)
     hist, inner, ms_res, ms_lin = [], [], 0.0, 0.0
@@ -900,7 +900,7 @@ def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5,
     solver.close()
     plan.close()
     return {"flow": flow, "kn": kn, "param": param, "R": R, "wall_flux": wall_flux, "q_sinc": bool(q_sinc),
-            "inner": inner, "krylov_rtol": krylov_rtol, "jacobian": jacobian, "p": p,
+            "inner_solver": inner_solver, "krylov_rtol": krylov_rtol, "jacobian": jacobian, "p": p,
             "newton_iterations": len(inner),
             "converged": hist[-1] < tol, "residual_history": hist, "inner_iterations": inner,
             "seconds": secs, "share_residual_Q": ms_res / max(ms_res + ms_lin, 1e-9)}
