@@ -852,7 +852,7 @@ def lin_vs_bin_leg(case, t_end=10.0, dt=0.1, ps=(2, 3, 4), fixes=True):
 
 def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5, max_newton=12, p=4,
                       wall_flux="analytic", q_sinc=False, inner_solver="source_iteration", krylov_rtol=1e-3,
-                      jacobian="local_maxwellian"):
+                      jacobian="local_maxwellian", box_factor=1.0):
     """Sec. 5.3: Newton iterations of the modified Newton method with the
     paper's source iteration (nu_j = rho_j, stop at 1e-7 absolute or 1e-3
     relative) to |R| < 1e-5 for the Couette flow (walls theta = 1 moving at
@@ -863,11 +863,13 @@ def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5,
     (the total density with the wall temperatures interpolated linearly).
     wall_flux: the wall density factor sqrt(2 pi / theta_w) of the
     supplement ("analytic") or the grid sum of the wall's flux ("discrete");
-    q_sinc: Q with the sinc quadrature of Eq. (2.16) (exact discrete mass)."""
+    q_sinc: Q with the sinc quadrature of Eq. (2.16) (exact discrete mass);
+    box_factor: the velocity box L as a multiple of the smallest one the
+    dealiasing condition of Sec. 2.3 allows, (3 + sqrt 2) R / 4."""
     import torch
     from paper_2503_09580_gb300 import lbo
     R = 4.0 if (flow == "fourier" and param >= 2.5) else 3.5
-    L = (3 + np.sqrt(2)) * R / 4
+    L = box_factor * (3 + np.sqrt(2)) * R / 4
     if flow == "couette":
         wl, wr, thl, thr = (1.0, 0.0, -param, 0.0), (1.0, 0.0, param, 0.0), 1.0, 1.0
     else:
@@ -900,7 +902,7 @@ def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5,
     solver.close()
     plan.close()
     return {"flow": flow, "kn": kn, "param": param, "R": R, "wall_flux": wall_flux, "q_sinc": bool(q_sinc),
-            "inner_solver": inner_solver, "krylov_rtol": krylov_rtol, "jacobian": jacobian, "p": p,
+            "inner_solver": inner_solver, "krylov_rtol": krylov_rtol, "jacobian": jacobian, "p": p, "box": L,
             "newton_iterations": len(inner),
             "converged": hist[-1] < tol, "residual_history": hist, "inner_iterations": inner,
             "seconds": secs, "share_residual_Q": ms_res / max(ms_res + ms_lin, 1e-9)}

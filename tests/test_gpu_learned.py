@@ -1,8 +1,11 @@
 """Learned preconditioner: hand-written GPU backward pass against the CPU
 oracle of the network, training on solver-generated pairs, and the safety
-property (the exact operator measures convergence; a poor network costs iterations only).
-The measured gain over the plain sweep is printed (on this slab problem the
-trained network does not beat the sweep; the fallback keeps the solve exact)."""
+property (the exact operator measures convergence; a poor network costs
+iterations only).  The measured gain over the plain sweep is printed; it is
+negative: an error dc in a cell's predicted coefficients reaches the
+residual through the transport of the lifted correction, amplified by about
+|v1|max / dx, so even a well-fitted network leaves a larger residual than
+the sweep alone; the fallback keeps the solve exact."""
 import numpy as np
 import pytest
 
