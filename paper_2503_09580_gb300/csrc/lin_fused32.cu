@@ -408,10 +408,14 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
       }
       if (!last) tmem::wait_st();
     }
-    tmem::fence_before_sync();
-    __syncthreads();
-    tmem::fence_after_sync();
+    // no barrier before the next node: its first pass writes, thread by
+    // thread, the same pencil this thread has just read (axis-1 pencils
+    // are private to their thread in the first and the last pass), and the
+    // partial sums and r^ are private to the thread as well
   }
+  tmem::fence_before_sync();
+  __syncthreads();
+  tmem::fence_after_sync();
   if (t < 32) tmem::dealloc(tbase, tmem::kColumns);
 }
 
