@@ -22,6 +22,7 @@
 #include "fused32.cuh"
 #include "lbo_internal.h"
 #include "tmem.cuh"
+#include "umma.cuh"
 
 namespace lbo {
 namespace {
@@ -38,6 +39,7 @@ struct FusedArgs {
   float* uhat;         // [B][J][U_STRIDE] u^_j = FFT(M^g phit_j) on the octant k in [0,16]^3
   float* lossf;        // [B][N^3] loss term -u M - w g in FP32 (loss block -> tail)
   double* out;         // [B][N^3]
+  int* err;            // set when a bounded wait gave up (read by lbo_plan_sync)
   double h, log_inv_eps;
   int cutoff, J, G, B, Q;
 };
@@ -297,6 +299,23 @@ __device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T
   }
 }
 
+// u^_j of the next radial node is staged into shared memory by a bulk
+// asynchronous copy (cp.async.bulk, 19664 bytes: both addresses 16-byte
+// aligned, size a multiple of 16) while the current node runs, two buffers
+// each with its mbarrier; every wait is bounded and sets a.err when it gives up.
+constexpr uint32_t U_BYTES = U_STRIDE * sizeof(float);
+static_assert(U_BYTES % 16 == 0, "bulk copy size");
+constexpr size_t GAIN_SMEM = sizeof(cpx<float>) * S_TOTAL + 2 * U_BYTES;
+constexpr uint32_t kUPolls = 1u << 22;
+
+// (no memory clobber: the copy's data becomes visible through the bounded
+// mbarrier wait, which carries one)
+__device__ __forceinline__ void stage_uhat(uint32_t dst, const float* src, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(U_BYTES));
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(U_BYTES), "r"(bar));
+}
+
 // The gain blocks hold the running partial L^+ in tensor memory: thread t
 // owns the same pencil (i2, k3) = (t / 17, t % 17) in the first and the last
 // pass of every j, so its 32 complex sums stay in 64 TMEM columns of its
@@ -306,6 +325,7 @@ __device__ void loss_term(const FusedArgs& a, cpx<float>* V, const PrepTables& T
 // memory.  The dynamic shared memory keeps one such block per SM (two would
 // need more than the SM's 228 KB), so the 512-column allocation never waits.
 static_assert(2 * sizeof(cpx<float>) * S_TOTAL > 228 * 1024, "gain blocks must not share an SM");
+static_assert(GAIN_SMEM + 8 * 1024 <= 227 * 1024, "gain block shared memory");
 static_assert(64 * ((F_THREADS / 32 + 3) / 4) <= tmem::kColumns, "partial sums exceed TMEM");
 
 // grid (G + 1, B): blocks x < G run the gain term for their group of radial
@@ -314,9 +334,11 @@ static_assert(64 * ((F_THREADS / 32 + 3) / 4) <= tmem::kColumns, "partial sums e
 __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   cpx<float>* V = (cpx<float>*)smem;
+  float* ubuf = (float*)(smem + sizeof(cpx<float>) * S_TOTAL);  // [2][U_STRIDE]
   __shared__ float mh[3 * F_N];
   __shared__ PrepTables T;
   __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t ubar[2];
   const int grp = blockIdx.x, b = blockIdx.y, t = threadIdx.x;
   const InstanceParams q = load_params(a.params, b);
   if (grp == a.G) {
@@ -325,6 +347,12 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
     return;
   }
   const int j0 = (a.J * grp) / a.G, j1 = (a.J * (grp + 1)) / a.G;
+  const float* usrc = a.uhat + (size_t)b * a.J * U_STRIDE;
+  const uint32_t ubuf_s = umma::smem_u32(ubuf), bar0 = umma::smem_u32(&ubar[0]);
+  if (t == 0) {
+    umma::mbar_init(bar0, 1);
+    umma::mbar_init(bar0 + 8, 1);
+  }
   if (t < 32) tmem::alloc(&tmem_slot, tmem::kColumns);
   if (t < 3 * F_N) {
     int dd = t / F_N, i = t % F_N;
@@ -342,14 +370,25 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
   const cpx<float>* rh = a.rhat + (size_t)b * F_H;
   cpx<float>* acc = a.part + ((size_t)grp * a.B + b) * F_H;
   for (int j = j0; j < j1; ++j) {
+    const int slot = (j - j0) & 1;
+    if (t == 0) {
+      if (j == j0) stage_uhat(ubuf_s, usrc + (size_t)j0 * U_STRIDE, bar0);
+      if (j + 1 < j1) {
+        // the other buffer was last read by the first pass of node j - 1,
+        // which every thread has left (several barriers ago)
+        umma::fence_proxy_async_smem();
+        stage_uhat(ubuf_s + (uint32_t)(slot ^ 1) * U_BYTES, usrc + (size_t)(j + 1) * U_STRIDE, bar0 + 8u * (slot ^ 1));
+      }
+    }
+    if (!umma::mbar_wait_bounded(bar0 + 8u * slot, ((j - j0) >> 1) & 1, kUPolls)) atomicExch(a.err, 1);
     {  // axis 1: psi^_j = u^_j r^ (r^ pre-scaled), inverse
       const int i2 = t / F_HC, k3 = t % F_HC;
       cpx<float>* base = V + srow(i2) + k3;
       const cpx<float>* rr = rh + i2 * F_HC + k3;
-      const float* uk = a.uhat + ((size_t)b * a.J + j) * U_STRIDE + fold32(i2) * U_N + k3;
+      const float* uk = ubuf + slot * U_STRIDE + fold32(i2) * U_N + k3;
       cpx<float> x[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) x[i] = cscale(rr[i * F_ROW], __ldg(uk + fold32(i) * (U_N * U_N)));
+      for (int i = 0; i < 32; ++i) x[i] = cscale(rr[i * F_ROW], uk[fold32(i) * (U_N * U_N)]);
       fft32<true>(x);
 #pragma unroll
       for (int i = 0; i < 32; ++i) base[i * S_PLANE] = x[i];
@@ -416,6 +455,15 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_f32_gain(FusedArgs a) {
   tmem::fence_before_sync();
   __syncthreads();
   tmem::fence_after_sync();
+  if (t == 0) {
+    // no copy is left in flight when every wait succeeded; after a timeout,
+    // one more bounded wait on the last phase of each buffer
+    const int n = j1 - j0;
+    for (int sl = 0; sl < 2 && sl < n; ++sl) {
+      const int uses = (n - sl + 1) / 2;
+      umma::mbar_wait_bounded(bar0 + 8u * sl, (uses - 1) & 1, kUPolls);
+    }
+  }
   if (t < 32) tmem::dealloc(tbase, tmem::kColumns);
 }
 
@@ -500,9 +548,14 @@ lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const doubl
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_f32_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_f32_gain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_f32_gain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GAIN_SMEM);
     cudaFuncSetAttribute(k_f32_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
+  }
+  if (!p->d_tc_err) {
+    e = cudaMalloc(&p->d_tc_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_tc_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait error flag");
   }
   FusedArgs a{};
   a.params = params;
@@ -515,6 +568,7 @@ lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const doubl
   a.uhat = (float*)(a.part + (size_t)G * B * F_H);
   a.lossf = a.uhat + (size_t)B * p->J * U_STRIDE;
   a.out = out;
+  a.err = (int*)p->d_tc_err;
   a.h = 2.0 * p->L / F_N;
   a.log_inv_eps = std::log(1.0 / p->eps);
   a.cutoff = p->cutoff;
@@ -530,7 +584,7 @@ lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const doubl
     LBO_LAUNCH(p, "f32_uhat", s, k_f32_uhat, dim3(a.J, B), U_THREADS, 0, a);
     *launches += 1;
   }
-  LBO_LAUNCH(p, "f32_gain", s, k_f32_gain, dim3(G + 1, B), F_THREADS, sm, a);
+  LBO_LAUNCH(p, "f32_gain", s, k_f32_gain, dim3(G + 1, B), F_THREADS, GAIN_SMEM, a);
   LBO_LAUNCH(p, "f32_tail", s, k_f32_tail, B, F_THREADS, sm, a);
   *launches += 3;
   e = cudaGetLastError();
