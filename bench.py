@@ -852,7 +852,7 @@ def lin_vs_bin_leg(case, t_end=10.0, dt=0.1, ps=(2, 3, 4), fixes=True):
 
 def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5, max_newton=12, p=4,
                       wall_flux="analytic", q_sinc=False, inner_solver="source_iteration", krylov_rtol=1e-3,
-                      jacobian="local_maxwellian", box_factor=1.0):
+                      jacobian="local_maxwellian", box_factor=1.0, nu_scale=1.0):
     """Sec. 5.3: Newton iterations of the modified Newton method with the
     paper's source iteration (nu_j = rho_j, stop at 1e-7 absolute or 1e-3
     relative) to |R| < 1e-5 for the Couette flow (walls theta = 1 moving at
@@ -883,7 +883,7 @@ def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5,
     plan = lbo.Plan(n, L, 1.0, 17, R=R, hemisphere_p=p, precision=precision, q_sinc_quadrature=int(q_sinc))
     solver = plan.solver(kind="slab", nx=nx, x_left=xl, x_right=xr, kn=kn, wall_left=wl, wall_right=wr,
                          total_mass=C, wall_flux=wall_flux, krylov_rtol=krylov_rtol, krylov_atol=1e-7, krylov_maxit=5000,
-                         precond="sweep", inner=inner_solver, nu_scale=1.0, jacobian=jacobian)
+                         precond="sweep", inner=inner_solver, nu_scale=nu_scale, jacobian=jacobian)
     f = torch.from_numpy(f0).cuda()
     work = torch.empty_like(f)
     hist, inner, ms_res, ms_lin = [], [], 0.0, 0.0
@@ -903,6 +903,7 @@ def steady_counts_leg(flow, kn, param, precision="fp64", nx=200, n=32, tol=1e-5,
     plan.close()
     return {"flow": flow, "kn": kn, "param": param, "R": R, "wall_flux": wall_flux, "q_sinc": bool(q_sinc),
             "inner_solver": inner_solver, "krylov_rtol": krylov_rtol, "jacobian": jacobian, "p": p, "box": L,
+            "nu_scale": nu_scale,
             "newton_iterations": len(inner),
             "converged": hist[-1] < tol, "residual_history": hist, "inner_iterations": inner,
             "seconds": secs, "share_residual_Q": ms_res / max(ms_res + ms_lin, 1e-9)}
