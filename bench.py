@@ -51,17 +51,15 @@ UNIT_ROUNDOFF = {"fp64": U64, "fp32": U32, "fp32x2": 2.0 ** -48, "fp64x2": 2.0 *
 BOUND_FACTOR = 4.0
 HBM_FALLBACK_GBS = 6800.0
 # Kernels bound by memory traffic, not by their arithmetic (rated in GB/s).
-HBM_KERNELS = ("combine", "fixes", "f32_head", "f32_tail", "tc_combine")
+HBM_KERNELS = ("combine", "fixes", "f32_head", "f32_tail", "tc_combine", "mh_table")
 # DRAM bytes (read + write) per launch of a dominant kernel at the benchmark
 # workload from one ncu capture, with the sha256 (first 16 hex digits) of the
 # source files it was built from; reported as null once those sources change.
 KERNEL_SOURCES = {
-    "plane_inv_mh_fwd": ("lin_kernels.cuh", "fft.cuh", "twofold.cuh", "twiddles_hi.h"),
+    "plane_inv_mh_fwd": ("lin_reg64.cuh", "fft_reg.cuh", "fft.cuh", "twiddles_hi.h"),
     "f32_gain": ("lin_fused32.cu", "fused32.cuh", "tmem.cuh"),
 }
 NCU_TRAFFIC = {
-    # profiles/linearized_generic_fp64_n32_b256.md: 71.41 MB read + 10.99 MB written
-    ("plane_inv_mh_fwd", 32, "fp64"): (82397696, "4a4d84f9edc7c313"),
 }
 
 
@@ -160,6 +158,8 @@ def kernel_bytes_per_instance(name, n, real_bytes, groups=1):
         return groups * 8 * h + 4 * n3 + 8 * n3
     if name == "tc_combine":   # L+, u (FP64), w (FP32), g in; out
         return 8 * n3 * 4 + 4 * n3
+    if name == "mh_table":     # M^h / 2 of the register plane kernel out (FP64)
+        return 8 * n3
     return 0
 
 
@@ -466,13 +466,15 @@ def dominant_roofline(prof, precision, peaks, hbm, hbm_src, groups=1):
     return rf
 
 
-def variant_leg(precision, tp, tg, tpc, tgc, stream, steps, peaks, hbm, ref, ref_clean, rms, rms_clean, k_clean):
-    """Another precision form on the same inputs: apps/s (same event timing),
-    its kernels' rooflines, and its error against the oracle with the
-    stated bound, on the noisy benchmark batch and on its noise-free twin."""
+def variant_leg(precision, tp, tg, tpc, tgc, stream, steps, peaks, hbm, ref, ref_clean, rms, rms_clean, k_clean,
+                kernel=0):
+    """Another precision form (or kernel set) on the same inputs: apps/s
+    (same event timing), its kernels' rooflines, and its error against the
+    oracle with the stated bound, on the noisy benchmark batch and on its
+    noise-free twin."""
     import torch
     from paper_2503_09580_gb300 import lbo
-    plan = lbo.Plan(N_GRID, BOX, 0.5, N_GRID, precision=precision)
+    plan = lbo.Plan(N_GRID, BOX, 0.5, N_GRID, precision=precision, kernel=kernel)
     out = torch.empty_like(tg)
     groups = plan.autotune(tp, tg, out) if precision == "fp32" else 0
     for _ in range(3):
@@ -1111,6 +1113,13 @@ def run_ours(args, world, rank, local):
                               k_clean)
             rec["speedup_vs_value"] = rec["value"] / value
             line["variants"][vp] = rec
+        if prec == "fp64":
+            # the same FP64 path with the two-stage shared-memory transforms
+            # (LBO_OPT_KERNEL = 2) in place of the register kernels
+            rec = variant_leg("fp64", tp, tg, tpc, tgc, stream, args.steps, peaks, hbm, ref, ref_c, rms, rms_c,
+                              k_clean, kernel=2)
+            rec["speedup_vs_value"] = rec["value"] / value
+            line["variants"]["fp64_shared_memory_transforms"] = rec
         line["omega_sweep_fp64"] = omega_sweep(tp, tg, tpc, tgc, params, g, pc, gc, stream, min(args.steps, 10),
                                                not args.no_cpu_baseline)
     if solo and not args.no_extra:

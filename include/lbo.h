@@ -89,7 +89,11 @@ typedef enum {
   LBO_OPT_HEMISPHERE_P = 6,/* hemisphere rule order p: M = 2 p^2 points (4)   */
   LBO_OPT_PRECISION = 7,   /* lbo_precision                                   */
   LBO_OPT_KERNEL = 8,      /* 0: fastest built kernel set for (N, precision)
-                              (default), 1: the generic plane/axis kernels    */
+                              (default), 1: the generic plane/axis kernels,
+                              2: the generic kernels with every transform a
+                              two-stage shared-memory FFT (FP64 at N = 32
+                              otherwise runs its hot kernels with one
+                              thread per pencil in registers)                 */
   LBO_OPT_JGROUPS = 9,     /* radial nodes per CTA of the fused FP32 kernel are
                               J / jgroups; 0 (default): chosen from the batch */
   LBO_OPT_Q_SINC_QUADRATURE = 10 /* Q(f,f) only.  1: the loss multiplier

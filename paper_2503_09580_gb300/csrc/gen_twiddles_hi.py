@@ -4,6 +4,12 @@ lo the correctly rounded remainder), from 60-digit decimal arithmetic.  The
 library's FFT twiddles of every precision (double, float, and the two-fold
 forms) are derived from this table on the host.
 
+It also writes the scaled form of W_32^m used by the register transforms
+(fft_reg.cuh): W = sc (1 + i q) where |cos| >= |sin|, else W = sc (q + i),
+so that |q| <= 1 and a butterfly with a twiddle takes six fused
+multiply-adds (the scaled-twiddle radix-2 butterfly of Linzer and Feig);
+sc and q are the correctly rounded doubles of the exact values.
+
     python gen_twiddles_hi.py > twiddles_hi.h
 """
 from decimal import Decimal, getcontext
@@ -61,6 +67,47 @@ def table(n):
     return rows
 
 
+def scaled(n):
+    P = pi()
+    rows = []
+    for m in range(n // 2):
+        c, s = cos_sin(-2 * P * m / n)
+        c, s = c.quantize(Decimal(10) ** -50), s.quantize(Decimal(10) ** -50)
+        if abs(c) >= abs(s):
+            rows.append((0, float(c), float(s / c)))
+        else:
+            rows.append((1, float(s), float(c / s)))
+    return rows
+
+
+def emit_scaled(name, n, rows):
+    print("// W_%d^m, m < %d: kind 0: sc (1 + i q); kind 1: sc (q + i)" % (n, n // 2))
+    print("struct ScaledTw {")
+    print("  int kind;")
+    print("  double sc, q;")
+    print("};")
+    print("LBO_HD constexpr ScaledTw %s(int m) {" % name)
+    print("  switch (m) {")
+    for m, (k, sc, q) in enumerate(rows):
+        print("    case %d: return {%d, %s, %s};" % (m, k, sc.hex(), q.hex()))
+    print("    default: return {0, 0.0, 0.0};")
+    print("  }")
+    print("}")
+
+
+def emit_cos(name, n):
+    P = pi()
+    print("// cos(2 pi m / %d), m < %d, correctly rounded" % (n, n))
+    print("LBO_HD constexpr double %s(int m) {" % name)
+    print("  switch (m) {")
+    for m in range(n):
+        c, _ = cos_sin(2 * P * m / n)
+        print("    case %d: return %s;" % (m, float(c.quantize(Decimal(10) ** -50)).hex()))
+    print("    default: return 0.0;")
+    print("  }")
+    print("}")
+
+
 def emit(name, rows):
     print("static const double %s[%d][4] = {" % (name, len(rows)))
     for r in rows:
@@ -74,3 +121,12 @@ if __name__ == "__main__":
     print("#pragma once")
     emit("kTw64Hi", table(64))
     emit("kTw48Hi", table(48))
+    print("#ifndef LBO_HD")
+    print("#ifdef __CUDACC__")
+    print("#define LBO_HD __host__ __device__")
+    print("#else")
+    print("#define LBO_HD")
+    print("#endif")
+    print("#endif")
+    emit_scaled("scaled_tw32", 32, scaled(32))
+    emit_cos("cos32", 32)

@@ -156,14 +156,17 @@ static lbo_status build_tables(lbo_plan* p) {
     TRY(cudaMemcpy(p->d_omega32, fo.data(), sizeof(float) * Q, cudaMemcpyHostToDevice));
   }
   {
-    // c_d cos(2 pi k d / N), k = 0..N/2, d = 0..N/4-1 (c_0 = 1, c_d = 2)
+    // c_d cos(2 pi k d / N), k = 0..N/2, d = 0..N/4-1 (c_0 = 1, c_d = 2);
+    // the cosines are the correctly rounded ones of the twiddle tables (N
+    // divides 64 or 48), so zeros are exact and the register kernels'
+    // compile-time cosines (cos32) are the same numbers
     const int HN = N / 2 + 1, Q4 = N / 4;
     std::vector<double> dc((size_t)HN * Q4);
     std::vector<float> df(dc.size());
     for (int k = 0; k < HN; ++k)
       for (int d = 0; d < Q4; ++d) {
-        long double a = 2.0L * 3.14159265358979323846264338327950288L * ((long double)k * d) / N;
-        dc[(size_t)k * Q4 + d] = (d == 0 ? 1.0 : 2.0) * (double)cosl(a);
+        const double c = 64 % N == 0 ? kTw64Hi[(k * d * (64 / N)) % 64][0] : kTw48Hi[(k * d * (48 / N)) % 48][0];
+        dc[(size_t)k * Q4 + d] = (d == 0 ? 1.0 : 2.0) * c;
         df[(size_t)k * Q4 + d] = (float)dc[(size_t)k * Q4 + d];
       }
     TRY(cudaMalloc(&p->d_dct64, sizeof(double) * dc.size()));
@@ -279,17 +282,6 @@ static lbo_status build_phit(lbo_plan* p, const double* d_stab, T* d_phit) {
   if (e != cudaSuccess) return cuda_fail(e, "phit build");
   (void)d_phit;
   return LBO_OK;
-}
-
-template <typename T>
-static GenericTables<T> plain_tables(const lbo_plan* p) {
-  const bool f64 = sizeof(T) == 8;
-  GenericTables<T> tb;
-  tb.phi = (const T*)(f64 ? (const void*)p->d_phi64 : (const void*)p->d_phi32);
-  tb.omega = (const T*)(f64 ? (const void*)p->d_omega64 : (const void*)p->d_omega32);
-  tb.phit = (const T*)(f64 ? (const void*)p->d_phit64 : (const void*)p->d_phit32);
-  tb.dct = (const T*)(f64 ? (const void*)p->d_dct64 : (const void*)p->d_dct32);
-  return tb;
 }
 
 template <typename T>
@@ -409,7 +401,7 @@ lbo_status lbo_plan_set(lbo_plan* p, lbo_option key, double v) {
       p->precision = (int)v;
       break;
     case LBO_OPT_KERNEL:
-      if (v != 0.0 && v != 1.0) return LBO_EINVAL;
+      if (v != 0.0 && v != 1.0 && v != 2.0) return LBO_EINVAL;
       p->kernel_choice = (int)v;
       break;
     case LBO_OPT_JGROUPS:

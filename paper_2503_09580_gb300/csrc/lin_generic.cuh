@@ -5,9 +5,11 @@
 // kernels, so each uploads its own FFT twiddle tables (upload_twiddles).
 #pragma once
 #include <cmath>
+#include <type_traits>
 
 #include "lbo_internal.h"
 #include "lin_kernels.cuh"
+#include "lin_reg64.cuh"
 
 namespace lbo {
 
@@ -19,6 +21,18 @@ struct GenericTables {
   const T* phit;   // [J][N^3] phit_j, cyclic order
   const T* dct;    // [N/2+1][N/4] DCT-I coefficients of u^_j
 };
+
+// The plan's FP64 or FP32 tables (T = double or float).
+template <typename T>
+static GenericTables<T> plain_tables(const lbo_plan* p) {
+  const bool f64 = sizeof(T) == 8;
+  GenericTables<T> tb;
+  tb.phi = (const T*)(f64 ? (const void*)p->d_phi64 : (const void*)p->d_phi32);
+  tb.omega = (const T*)(f64 ? (const void*)p->d_omega64 : (const void*)p->d_omega32);
+  tb.phit = (const T*)(f64 ? (const void*)p->d_phit64 : (const void*)p->d_phit32);
+  tb.dct = (const T*)(f64 ? (const void*)p->d_dct64 : (const void*)p->d_dct32);
+  return tb;
+}
 
 template <typename K>
 static inline void set_smem(K kernel, size_t bytes) {
@@ -92,6 +106,42 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
   const size_t sm_up = sizeof(T) * ((size_t)PL * HC * HC + (size_t)HC * (N / 4));
   set_smem(k_up, sm_up);
   auto k_comb = k_combine<T, N>;
+  // FP64 at N = 32: the gain loop's kernels with one thread per pencil
+  // (lin_reg64.cuh) unless LBO_OPT_KERNEL = 2 asks for the shared-memory ones
+  constexpr bool R64 = std::is_same<T, double>::value && N == 32;
+  const bool reg = R64 && p->kernel_choice != 2;
+  auto launch_uhat = [&](const Axis1Args& a1, bool cached) {
+    if constexpr (R64) {
+      if (reg) {
+        const dim3 gr(r64::RNC / 32, B);
+        if (cached) LBO_LAUNCH(p, "axis1_uhat_cached_inv", s, r64::k_axis1_uhat_r64<true>, gr, 32, 0, a1, RH, W1);
+        else LBO_LAUNCH(p, "axis1_uhat_inv", s, r64::k_axis1_uhat_r64<false>, gr, 32, 0, a1, RH, W1);
+        return;
+      }
+    }
+    if (cached) LBO_LAUNCH(p, "axis1_uhat_cached_inv", s, ka_uhat_c, ga, blk, 0, a1, RH, W1);
+    else LBO_LAUNCH(p, "axis1_uhat_inv", s, ka_uhat, ga, blk, 0, a1, RH, W1);
+  };
+  auto launch_mh = [&]() {
+    if constexpr (R64) {
+      if (reg) {
+        constexpr int RP = 4;
+        LBO_LAUNCH(p, "plane_inv_mh_fwd", s, r64::k_plane_mh_r64<RP>, dim3(N / RP, B), r64::PlaneR<RP>::THREADS,
+                   r64::PlaneR<RP>::BYTES, (const double*)R2, W1);
+        return;
+      }
+    }
+    LBO_LAUNCH(p, "plane_inv_mh_fwd", s, ki_mh, gp, blk, sm, pa, W1, (T*)nullptr);
+  };
+  auto launch_acc = [&](const Axis1Args& a2) {
+    if constexpr (R64) {
+      if (reg) {
+        LBO_LAUNCH(p, "axis1_fwd_acc", s, r64::k_axis1_acc_r64, dim3(r64::RNC / 32, B), 32, 0, a2, W1, LH);
+        return;
+      }
+    }
+    LBO_LAUNCH(p, "axis1_fwd_acc", s, ka_acc, ga, blk, 0, a2, W1, LH);
+  };
   int launches = 0;
   // r^ = FFT(r), r = g/M with the cut-off (Algorithm 1, gain term)
   LBO_LAUNCH(p, "plane_fwd_ratio", s, kf_ratio, gp, blk, sm, pa, W1);
@@ -99,6 +149,12 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
   LBO_LAUNCH(p, "axis1_fwd", s, ka_fwd, ga, blk, 0, ax, W1, RH);
   launches += 2;
   const size_t HC3 = (size_t)HC * HC * HC;
+  if constexpr (R64) {
+    if (reg) {  // M^h / 2 for the register plane kernel, in R2 until the loss term
+      LBO_LAUNCH(p, "mh_table", s, r64::k_mh_table_r64, B, 256, 0, params, pa.h, (double*)R2);
+      launches += 1;
+    }
+  }
   for (int j = 0; j < p->J; ++j) {
     Axis1Args a1{};
     a1.dct = dct;
@@ -106,7 +162,7 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
     if (mc) {
       // psi_j = InvFFT(u^_j r^), u^_j from the cache
       a1.uplanes = mc->uh + (size_t)j * B * HC3;
-      LBO_LAUNCH(p, "axis1_uhat_cached_inv", s, ka_uhat_c, ga, blk, 0, a1, RH, W1);
+      launch_uhat(a1, true);
       launches -= 1;
     } else {
       // u^_j = FFT(M^g phit_j), real and even: DCT-I of the octant, axes 3 and 2
@@ -114,15 +170,15 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
                  phit + (size_t)j * n3, dct, pa.h, UP);
       // psi_j = InvFFT(u^_j r^), u^_j finished along axis 1 in the same kernel
       a1.uplanes = UP;
-      LBO_LAUNCH(p, "axis1_uhat_inv", s, ka_uhat, ga, blk, 0, a1, RH, W1);
+      launch_uhat(a1, false);
     }
     // psi_j <- M^h psi_j ; psi^_j = FFT(psi_j)
-    LBO_LAUNCH(p, "plane_inv_mh_fwd", s, ki_mh, gp, blk, sm, pa, W1, (T*)nullptr);
+    launch_mh();
     // L^+ += phi_j psi^_j
     Axis1Args a2{};
     a2.table = phi + (size_t)j * Q;
     a2.first = j == 0;
-    LBO_LAUNCH(p, "axis1_fwd_acc", s, ka_acc, ga, blk, 0, a2, W1, LH);
+    launch_acc(a2);
     launches += 4;
   }
   // L+ = InvFFT(L^+)

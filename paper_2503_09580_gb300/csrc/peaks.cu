@@ -3,11 +3,16 @@
 // library's roofline fractions for the ALU-bound kernels).
 //
 // Every thread runs ACC independent fused multiply-add chains
-// x <- x * a + b (a = 1 - 2^-10, b = 2^-10: the chains converge to 1, so no
-// overflow and no subnormal operands), enough independent work to hide the
-// pipe latency; the grid is SMs x 8 blocks of 256 threads (one full wave,
-// 64 warps per SM).  A store that depends on every chain keeps the work
-// alive.  Thread 0 of every block reads clock64() around its loop; the
+// x <- x * a + b (a = 1 - 2^-10, b = 2^-10: normal numbers throughout, no
+// overflow), enough independent work to hide the pipe latency; the grid is
+// SMs x 8 blocks of 256 threads (one full wave, 64 warps per SM).  The rate
+// a chain kernel reaches depends on its code shape, not on the operands: on
+// GB300 the FP32 pipe is issue-bound (4-fold unrolling lost 6 % to loop
+// overhead in the same issue slots), and the same DFMA loop ran at 1.20
+// TFLOP/s with 4 to 8 chains but 1.01 with 12.  So FP32 runs 8 chains
+// unrolled 16 times, FP64 several chain counts and unroll depths, and the
+// largest rate is the peak.  A store that depends on every chain keeps the
+// work alive.  Thread 0 of every block reads clock64() around its loop; the
 // longest loop over the blocks of the single wave, divided by the event
 // time, gives the SM clock the peak was measured at.
 #include <cuda_runtime.h>
@@ -19,29 +24,31 @@
 namespace lbo {
 namespace {
 
-constexpr int kAcc = 8, kThreads = 256, kBlocksPerSM = 8;
+constexpr int kThreads = 256, kBlocksPerSM = 8;
 
-template <typename T>
+template <typename T, int ACC, int UNR>
 __global__ void __launch_bounds__(kThreads) k_fma_chains(T* sink, long long* cycles, int iters, T a, T b) {
-  T x[kAcc];
+  T x[ACC];
 #pragma unroll
-  for (int i = 0; i < kAcc; ++i) x[i] = (T)(threadIdx.x + 1) * (T)(i + 1) * (T)0.0009765625;
+  for (int i = 0; i < ACC; ++i) x[i] = (T)(threadIdx.x + 1) * (T)(i + 1) * (T)0.0009765625;
   const long long c0 = clock64();
-#pragma unroll 4
+#pragma unroll UNR
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int i = 0; i < kAcc; ++i) x[i] = fma(x[i], a, b);
+    for (int i = 0; i < ACC; ++i) x[i] = fma(x[i], a, b);
   }
   const long long c1 = clock64();
   T s = (T)0;
 #pragma unroll
-  for (int i = 0; i < kAcc; ++i) s += x[i];
+  for (int i = 0; i < ACC; ++i) s += x[i];
   if (s == (T)-1) sink[blockIdx.x * kThreads + threadIdx.x] = s;  // never taken: x stays near 1
   if (threadIdx.x == 0) atomicMax((unsigned long long*)cycles, (unsigned long long)(c1 - c0));
 }
 
-template <typename T>
-lbo_status measure(cudaStream_t s, int sms, int iters, double* tflops, double* mhz, T* sink, long long* d_cyc) {
+// Best rate (TFLOP/s) of k_fma_chains<T, ACC, UNR> over three launches; *mhz
+// is updated with the clock of a new best.
+template <typename T, int ACC, int UNR>
+lbo_status measure(cudaStream_t s, int sms, int iters, double* best, double* mhz, T* sink, long long* d_cyc) {
   const int blocks = sms * kBlocksPerSM;
   const T a = (T)(1.0 - 1.0 / 1024.0), b = (T)(1.0 / 1024.0);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -51,12 +58,11 @@ lbo_status measure(cudaStream_t s, int sms, int iters, double* tflops, double* m
     if (e0) cudaEventDestroy(e0);
     return cuda_fail(e, "peaks: event");
   }
-  double best = 0.0, clk = 0.0;
-  k_fma_chains<T><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters / 8, a, b);  // warm-up
+  k_fma_chains<T, ACC, UNR><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters / 8, a, b);  // warm-up
   for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
     cudaMemsetAsync(d_cyc, 0, sizeof(long long), s);
     cudaEventRecord(e0, s);
-    k_fma_chains<T><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters, a, b);
+    k_fma_chains<T, ACC, UNR><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters, a, b);
     cudaEventRecord(e1, s);
     e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) break;
@@ -64,20 +70,17 @@ lbo_status measure(cudaStream_t s, int sms, int iters, double* tflops, double* m
     cudaEventElapsedTime(&ms, e0, e1);
     long long cyc = 0;
     e = cudaMemcpy(&cyc, d_cyc, sizeof(cyc), cudaMemcpyDeviceToHost);
-    const double flops = 2.0 * kAcc * (double)iters * blocks * kThreads;
+    const double flops = 2.0 * ACC * (double)iters * blocks * kThreads;
     const double rate = flops / (ms * 1e-3) / 1e12;
-    if (rate > best) {
-      best = rate;
-      clk = (double)cyc / (ms * 1e-3) / 1e6;
+    if (rate > *best) {
+      *best = rate;
+      *mhz = (double)cyc / (ms * 1e-3) / 1e6;
     }
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (e != cudaSuccess) return cuda_fail(e, "peaks: kernel");
-  *tflops = best;
-  *mhz = clk;
-  return LBO_OK;
+  return e == cudaSuccess ? LBO_OK : cuda_fail(e, "peaks: kernel");
 }
 
 }  // namespace
@@ -100,10 +103,13 @@ extern "C" lbo_status lbo_measure_alu_peaks(void* stream, double* fp32_tflops, d
     cudaGetLastError();
     return LBO_ENOMEM;
   }
-  // about 25 ms per launch on a GB300 (128 FP32 and 2 FP64 FMA lanes per SM)
+  // about 25 ms per launch on a GB300 (128 FP32 and about 2 FP64 FMA lanes per SM)
   double f32 = 0, f64 = 0, mhz32 = 0, mhz64 = 0;
-  lbo_status st = lbo::measure<float>(s, sms, 1 << 19, &f32, &mhz32, (float*)sink, cyc);
-  if (st == LBO_OK) st = lbo::measure<double>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
+  lbo_status st = lbo::measure<float, 8, 16>(s, sms, 1 << 19, &f32, &mhz32, (float*)sink, cyc);
+  if (st == LBO_OK) st = lbo::measure<double, 4, 16>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
+  if (st == LBO_OK) st = lbo::measure<double, 6, 16>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
+  if (st == LBO_OK) st = lbo::measure<double, 6, 4>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
+  if (st == LBO_OK) st = lbo::measure<double, 8, 16>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
   cudaFree(sink);
   cudaFree(cyc);
   if (st != LBO_OK) return st;

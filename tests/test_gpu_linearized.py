@@ -92,6 +92,26 @@ def test_noisy_n32_fp64_within_conditioning_bound():
     assert relerr(got, ref) <= max(1e-12, bound)
 
 
+def test_register_and_shared_memory_transforms_fp64_n32():
+    """FP64 at N = 32 runs the gain loop's kernels with one thread per pencil
+    and the transforms in registers; LBO_OPT_KERNEL = 2 keeps the two-stage
+    shared-memory transforms.  Both meet the bar against the oracle, with and
+    without the Maxwellian cache, and agree with each other to rounding."""
+    n, L, om = 32, 8.0, 0.74
+    params, g = workloads.batched_instances(n, L, batch=4, seed=7, noise=0.0)
+    ref = apply_linearized(tables(n, L, om, n), params, g)
+    reg = lbo.Plan(n, L, om, n)
+    smem = lbo.Plan(n, L, om, n, kernel=2)
+    a, b = run(reg, params, g), run(smem, params, g)
+    assert relerr(a, ref) <= 1e-12 and relerr(b, ref) <= 1e-12
+    assert relerr(a, b) <= 1e-13
+    reg.cache_maxwellians(torch.from_numpy(params).to(DEV))
+    c = run(reg, params, g)
+    assert np.array_equal(a, c)
+    reg.close()
+    smem.close()
+
+
 def test_full_size_batch_sampled_instances():
     """The benchmark's launch configuration (N = 32, batch 256, per-instance
     Maxwellians), noise-free twin, checked on sampled instances."""

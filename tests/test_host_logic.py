@@ -1,7 +1,9 @@
 """Host-side logic inside the CUDA sources, checked on the CPU by small
 nvcc-built harnesses that run no kernel (tests/host/): the banded LU with an
-arrow border of the moment coarse correction, and the resampling matrices
-of the mixed-N solver against the oracle's FFT-based resampling."""
+arrow border of the moment coarse correction, the resampling matrices of
+the mixed-N solver against the oracle's FFT-based resampling, and the
+register-resident 32-point transform of the FP64 kernels against a direct
+DFT."""
 import os
 import shutil
 import subprocess
@@ -55,3 +57,15 @@ def test_resampling_matrices_match_the_oracle(tmp_path):
         ref = np.array(cols).T
         assert np.abs(R - ref).max() <= 1e-13, (na, nb, np.abs(R - ref).max())
     assert o == vals.size
+
+
+def test_register_fft32_against_a_direct_dft(tmp_path):
+    """The 32-point transform of the FP64 register kernels (scaled-twiddle
+    radix-2, fft_reg.cuh) against a direct DFT in long double: a few units
+    of the working precision's roundoff, forward and inverse, and the scaled
+    twiddles reproduce W_32^m to about one unit of double roundoff."""
+    out = subprocess.run([_build("fft_reg", tmp_path)], check=True, capture_output=True, text=True).stdout
+    res = {" ".join(line.split()[:-1]): float(line.split()[-1]) for line in out.strip().splitlines()}
+    assert res["double forward"] <= 8 * 2.0 ** -53 and res["double inverse"] <= 8 * 2.0 ** -53
+    assert res["float forward"] <= 8 * 2.0 ** -24 and res["float inverse"] <= 8 * 2.0 ** -24
+    assert res["twiddle"] <= 4 * 2.0 ** -53
