@@ -60,6 +60,8 @@ KERNEL_SOURCES = {
     "f32_gain": ("lin_fused32.cu", "fused32.cuh", "tmem.cuh"),
 }
 NCU_TRAFFIC = {
+    # profiles/linearized_reg64_fp64_n32_b256.md: 138.61 MB read + 26.02 MB written (8 planes per CTA)
+    ("plane_inv_mh_fwd", 32, "fp64"): (164629760, "8c4fe4705effdbc8"),
 }
 
 
@@ -1027,8 +1029,10 @@ def run_ours(args, world, rank, local):
     if args.moment_fix:
         plan.set("moment_fix", 1)
     out = torch.empty_like(tg)
-    # radial-node groups per CTA of the fused FP32 kernel, timed on this batch
-    jgroups = plan.autotune(tp, tg, out) if prec == "fp32" and not args.no_autotune else 0
+    # launch shape timed on this batch: radial-node groups per CTA of the
+    # fused FP32 kernel, or planes per CTA of the FP64 register plane kernel
+    shape = plan.autotune(tp, tg, out) if prec in ("fp32", "fp64") and not args.no_autotune else 0
+    jgroups = shape if prec == "fp32" else 0
     for _ in range(args.warmup):
         plan.apply_linearized(tp, tg, out)
     torch.cuda.synchronize()
@@ -1057,6 +1061,7 @@ def run_ours(args, world, rank, local):
     cfg = workload_config(args.omega, prec)
     cfg.update({"eps": args.eps if args.eps is not None else 1e-9,
                 "jgroups": jgroups if jgroups else "n/a",
+                "planes_per_cta": shape if prec == "fp64" and shape else "n/a",
                 "parallelism": "replicas (instances sharded, no collective)" if world > 1 else "single GPU",
                 "l2": "inputs 67 MB + outputs 67 MB + workspace per step > 129 MB L2"})
     line = {

@@ -96,13 +96,16 @@ typedef enum {
                               thread per pencil in registers)                 */
   LBO_OPT_JGROUPS = 9,     /* radial nodes per CTA of the fused FP32 kernel are
                               J / jgroups; 0 (default): chosen from the batch */
-  LBO_OPT_Q_SINC_QUADRATURE = 10 /* Q(f,f) only.  1: the loss multiplier
+  LBO_OPT_Q_SINC_QUADRATURE = 10, /* Q(f,f) only.  1: the loss multiplier
                               sum_j w_j B(g_j) sinc(pi g_j |k| / L) replaced by
                               its hemisphere quadrature
                               sum_m w_m cos(pi g_j sigma_m . k / L), the
                               second mass fix of Sec. 2.3 (Eq. (2.16)): Q^_0
                               vanishes up to rounding.  Takes the generic
                               kernels (also for FP32 at N = 32); 0: off   */
+  LBO_OPT_PLANES = 11      /* planes per CTA of the FP64 register plane kernel
+                              at N = 32 (2, 4 or 8; 0: default, 4): the tile
+                              shape lbo_plan_autotune picks for FP64        */
 } lbo_option;
 
 /* Create a plan for N^3 grids on [-box, box]^3, VHS exponent vhs_omega in
@@ -455,10 +458,13 @@ size_t lbo_noalloc_scratch_bytes(void);
 size_t lbo_noalloc_bytes_per_instance(const lbo_plan *plan);
 
 /* Launch-shape autotuner.  Times the candidate shapes of the plan's fastest
- * kernel set on the given device arrays (for the fused FP32 N = 32 kernels:
- * 1, 2, 3, 4, 6 or 8 groups of radial nodes per instance), keeps the
- * fastest in the plan (as LBO_OPT_JGROUPS) and returns it in *choice (0 when
- * the plan has nothing to tune).  Overwrites out. */
+ * kernel set on the given device arrays, keeps the fastest in the plan and
+ * returns it in *choice (0 when the plan has nothing to tune):
+ * - fused FP32 kernels (N = 32): 1, 2, 3, 4, 6 or 8 groups of radial nodes
+ *   per instance (kept as LBO_OPT_JGROUPS);
+ * - FP64 register kernels (N = 32): 2, 4 or 8 planes per CTA of the plane
+ *   kernel (kept as LBO_OPT_PLANES).
+ * Overwrites out. */
 lbo_status lbo_plan_autotune(lbo_plan *plan, const double *maxwellian_params, const double *g, double *out,
                              int batch, int *choice);
 

@@ -136,10 +136,46 @@ void lbo_group_destroy(lbo_group* G) {
   delete G;
 }
 
+// Planes per CTA of the FP64 register plane kernel (N = 32): 2, 4 or 8,
+// each timed over three applications after one untimed.
+static lbo_status autotune_planes(lbo_plan* p, const double* params, const double* g, double* out, int batch,
+                                  int* choice) {
+  const int cands[] = {2, 4, 8};
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  int best_p = 0;
+  const int keep = p->r64_planes;
+  lbo_status st = LBO_OK;
+  for (int P : cands) {
+    p->r64_planes = P;
+    st = lbo_apply_linearized(p, params, g, out, batch);
+    if (st != LBO_OK) break;
+    cudaEventRecord(a, p->stream);
+    for (int r = 0; r < 3 && st == LBO_OK; ++r) st = lbo_apply_linearized(p, params, g, out, batch);
+    cudaEventRecord(b, p->stream);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (st == LBO_OK && ms < best) {
+      best = ms;
+      best_p = P;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  p->r64_planes = st == LBO_OK ? best_p : keep;
+  if (choice) *choice = p->r64_planes;
+  return st;
+}
+
 lbo_status lbo_plan_autotune(lbo_plan* p, const double* params, const double* g, double* out, int batch,
                              int* choice) {
   if (!p || batch < 1 || !params || !g || !out) return LBO_EINVAL;
   if (choice) *choice = 0;
+  if (p->precision == LBO_PREC_FP64 && p->N == 32 && p->kernel_choice != 2) return autotune_planes(p, params, g, out,
+                                                                                                     batch, choice);
   if (!(p->precision == LBO_PREC_FP32 && p->N == 32 && p->kernel_choice == 0)) return LBO_OK;
   const int cands[] = {1, 2, 3, 4, 6, 8};
   cudaEvent_t a, b;

@@ -412,6 +412,10 @@ lbo_status lbo_plan_set(lbo_plan* p, lbo_option key, double v) {
       if (v != 0.0 && v != 1.0) return LBO_EINVAL;
       p->q_sinc_quad = (int)v;
       break;
+    case LBO_OPT_PLANES:
+      if (v != 0.0 && v != 2.0 && v != 4.0 && v != 8.0) return LBO_EINVAL;
+      p->r64_planes = (int)v;
+      break;
     default: return LBO_EINVAL;
   }
   return LBO_OK;

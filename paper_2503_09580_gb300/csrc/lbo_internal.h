@@ -12,6 +12,7 @@ struct lbo_plan {
   double L = 0, omega = 0, R = 0, C = 0, eps = 1e-9;
   int cutoff = 1, mass_fix = 0, moment_fix = 0, hemi_p = 4, precision = 0;
   int kernel_choice = 0, jgroups = 0;
+  int r64_planes = 0;  // planes per CTA of the FP64 register plane kernel (0: 4)
   int q_sinc_quad = 0;  // Q's loss multiplier: 1 = the hemisphere quadrature of Eq. (2.16)
   cudaStream_t stream = nullptr;
   bool tables_dirty = false;

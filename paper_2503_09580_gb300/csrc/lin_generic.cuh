@@ -125,9 +125,17 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
   auto launch_mh = [&]() {
     if constexpr (R64) {
       if (reg) {
-        constexpr int RP = 4;
-        LBO_LAUNCH(p, "plane_inv_mh_fwd", s, r64::k_plane_mh_r64<RP>, dim3(N / RP, B), r64::PlaneR<RP>::THREADS,
-                   r64::PlaneR<RP>::BYTES, (const double*)R2, W1);
+        // planes per CTA: LBO_OPT_PLANES (lbo_plan_autotune), default 4
+        auto go = [&](auto rp) {
+          constexpr int RP = decltype(rp)::value;
+          auto k = r64::k_plane_mh_r64<RP>;
+          set_smem(k, r64::PlaneR<RP>::BYTES);
+          LBO_LAUNCH(p, "plane_inv_mh_fwd", s, k, dim3(N / RP, B), r64::PlaneR<RP>::THREADS, r64::PlaneR<RP>::BYTES,
+                     (const double*)R2, W1);
+        };
+        if (p->r64_planes == 2) go(std::integral_constant<int, 2>());
+        else if (p->r64_planes == 8) go(std::integral_constant<int, 8>());
+        else go(std::integral_constant<int, 4>());
         return;
       }
     }

@@ -26,13 +26,17 @@ namespace r64 {
 constexpr int RN = 32, RHC = 17, RNC = RN * RHC;
 
 // Shared memory of k_plane_mh_r64 for PPC planes: half rows [i2][pp][k3] with
-// a row stride padded by two slots, which keeps the row pass (thread (pp, qq)
-// on rows 2 qq, 2 qq + 1 of plane pp) free of bank conflicts.  16 PPC
-// threads: every pass has exactly one pencil per thread (PPC even fills
-// whole warps), since an idle lane costs as much FP64 issue as a busy one.
+// a padded row stride, which keeps the row pass (thread (pp, qq) = (t % PPC,
+// t / PPC) on rows 2 qq, 2 qq + 1 of plane pp) free of bank conflicts: the
+// eight threads of a 16-byte shared-memory phase land on distinct 16-byte
+// bank groups when 2 RSB = 2 (mod 8) for PPC = 2 and 4 (mod 8) for PPC = 4
+// (any RSB for PPC = 8).  16 PPC threads: every pass has exactly one pencil
+// per thread (PPC even fills whole warps), since an idle lane costs as much
+// FP64 issue as a busy one.
 template <int PPC>
 struct PlaneR {
-  static constexpr int RSB = PPC * RHC + 2;
+  static_assert(PPC == 2 || PPC == 4 || PPC == 8, "planes per CTA");
+  static constexpr int RSB = PPC * RHC + (PPC == 2 ? 3 : 2);
   static constexpr int THREADS = 16 * PPC;
   static constexpr size_t BYTES = sizeof(cpx<double>) * RN * RSB;
 };

@@ -6,15 +6,19 @@
 // x <- x * a + b (a = 1 - 2^-10, b = 2^-10: normal numbers throughout, no
 // overflow), enough independent work to hide the pipe latency; the grid is
 // SMs x 8 blocks of 256 threads (one full wave, 64 warps per SM).  The rate
-// a chain kernel reaches depends on its code shape, not on the operands: on
-// GB300 the FP32 pipe is issue-bound (4-fold unrolling lost 6 % to loop
-// overhead in the same issue slots), and the same DFMA loop ran at 1.20
-// TFLOP/s with 4 to 8 chains but 1.01 with 12.  So FP32 runs 8 chains
-// unrolled 16 times, FP64 several chain counts and unroll depths, and the
-// largest rate is the peak.  A store that depends on every chain keeps the
-// work alive.  Thread 0 of every block reads clock64() around its loop; the
-// longest loop over the blocks of the single wave, divided by the event
-// time, gives the SM clock the peak was measured at.
+// such a loop reaches depends on its code shape, not on the operand values:
+// - the FP32 pipe is issue-bound, so loop overhead in the same issue slots
+//   costs rate (6 % with 4-fold unrolling): the loop is unrolled 16 times;
+// - on GB300 a DFMA whose operands are all registers issues about 19 %
+//   faster than one that reads a constant-bank operand (a compile-time
+//   constant, or a kernel parameter at some offsets: the same loop measured
+//   1.20 or 1.01 TFLOP/s depending only on the kernel's parameter list).  So
+//   a and b are read from a constant table through an index the compiler
+//   cannot see (blockDim.x >> 12, always 0), which puts them in registers.
+// A store that depends on every chain keeps the work alive.  In the FP32
+// run thread 0 of every block reads clock64() around its loop; the longest
+// loop over the blocks of the single wave, divided by the event time, gives
+// the SM clock the peaks were measured at.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,31 +30,40 @@ namespace {
 
 constexpr int kThreads = 256, kBlocksPerSM = 8;
 
-template <typename T, int ACC, int UNR>
-__global__ void __launch_bounds__(kThreads) k_fma_chains(T* sink, long long* cycles, int iters, T a, T b) {
+static __constant__ double c_ab64[2] = {1.0 - 1.0 / 1024.0, 1.0 / 1024.0};
+static __constant__ float c_ab32[2] = {1.0f - 1.0f / 1024.0f, 1.0f / 1024.0f};
+
+// CLK: thread 0 of every block brackets its loop with clock64().
+template <typename T, int ACC, bool CLK>
+__global__ void __launch_bounds__(kThreads) k_fma_chains(T* sink, long long* cycles, int iters) {
+  const int z = (int)(blockDim.x >> 12);
+  const T* ab = sizeof(T) == 8 ? (const T*)c_ab64 : (const T*)c_ab32;
+  const T a = ab[z], b = ab[z + 1];
   T x[ACC];
 #pragma unroll
   for (int i = 0; i < ACC; ++i) x[i] = (T)(threadIdx.x + 1) * (T)(i + 1) * (T)0.0009765625;
-  const long long c0 = clock64();
-#pragma unroll UNR
+  long long c0 = 0;
+  if constexpr (CLK) c0 = clock64();
+#pragma unroll 16
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int i = 0; i < ACC; ++i) x[i] = fma(x[i], a, b);
   }
-  const long long c1 = clock64();
   T s = (T)0;
 #pragma unroll
   for (int i = 0; i < ACC; ++i) s += x[i];
   if (s == (T)-1) sink[blockIdx.x * kThreads + threadIdx.x] = s;  // never taken: x stays near 1
-  if (threadIdx.x == 0) atomicMax((unsigned long long*)cycles, (unsigned long long)(c1 - c0));
+  if constexpr (CLK) {
+    const long long c1 = clock64();
+    if (threadIdx.x == 0) atomicMax((unsigned long long*)cycles, (unsigned long long)(c1 - c0));
+  }
 }
 
-// Best rate (TFLOP/s) of k_fma_chains<T, ACC, UNR> over three launches; *mhz
-// is updated with the clock of a new best.
-template <typename T, int ACC, int UNR>
+// Best rate (TFLOP/s) of k_fma_chains<T, ACC, CLK> over three launches; with
+// CLK, *mhz is the clock of the best.
+template <typename T, int ACC, bool CLK>
 lbo_status measure(cudaStream_t s, int sms, int iters, double* best, double* mhz, T* sink, long long* d_cyc) {
   const int blocks = sms * kBlocksPerSM;
-  const T a = (T)(1.0 - 1.0 / 1024.0), b = (T)(1.0 / 1024.0);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -58,11 +71,11 @@ lbo_status measure(cudaStream_t s, int sms, int iters, double* best, double* mhz
     if (e0) cudaEventDestroy(e0);
     return cuda_fail(e, "peaks: event");
   }
-  k_fma_chains<T, ACC, UNR><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters / 8, a, b);  // warm-up
+  k_fma_chains<T, ACC, CLK><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters / 8);  // warm-up
   for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
     cudaMemsetAsync(d_cyc, 0, sizeof(long long), s);
     cudaEventRecord(e0, s);
-    k_fma_chains<T, ACC, UNR><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters, a, b);
+    k_fma_chains<T, ACC, CLK><<<blocks, kThreads, 0, s>>>(sink, d_cyc, iters);
     cudaEventRecord(e1, s);
     e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) break;
@@ -74,7 +87,7 @@ lbo_status measure(cudaStream_t s, int sms, int iters, double* best, double* mhz
     const double rate = flops / (ms * 1e-3) / 1e12;
     if (rate > *best) {
       *best = rate;
-      *mhz = (double)cyc / (ms * 1e-3) / 1e6;
+      if (CLK) *mhz = (double)cyc / (ms * 1e-3) / 1e6;
     }
   }
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -105,11 +118,8 @@ extern "C" lbo_status lbo_measure_alu_peaks(void* stream, double* fp32_tflops, d
   }
   // about 25 ms per launch on a GB300 (128 FP32 and about 2 FP64 FMA lanes per SM)
   double f32 = 0, f64 = 0, mhz32 = 0, mhz64 = 0;
-  lbo_status st = lbo::measure<float, 8, 16>(s, sms, 1 << 19, &f32, &mhz32, (float*)sink, cyc);
-  if (st == LBO_OK) st = lbo::measure<double, 4, 16>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
-  if (st == LBO_OK) st = lbo::measure<double, 6, 16>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
-  if (st == LBO_OK) st = lbo::measure<double, 6, 4>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
-  if (st == LBO_OK) st = lbo::measure<double, 8, 16>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
+  lbo_status st = lbo::measure<float, 8, true>(s, sms, 1 << 19, &f32, &mhz32, (float*)sink, cyc);
+  if (st == LBO_OK) st = lbo::measure<double, 8, false>(s, sms, 1 << 13, &f64, &mhz64, sink, cyc);
   cudaFree(sink);
   cudaFree(cyc);
   if (st != LBO_OK) return st;

@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "liblbo.so")
 
 LBO_OPT = {"R": 0, "C": 1, "eps": 2, "cutoff": 3, "mass_fix": 4, "moment_fix": 5,
-           "hemisphere_p": 6, "precision": 7, "kernel": 8, "jgroups": 9, "q_sinc_quadrature": 10}
+           "hemisphere_p": 6, "precision": 7, "kernel": 8, "jgroups": 9, "q_sinc_quadrature": 10, "planes": 11}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32x2": 2, "fp64x2": 3, "bf16_split": 4, "fp16_split": 5}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "not converged",
           5: "Krylov breakdown", 6: "non-finite value", 7: "unsupported configuration",

@@ -65,5 +65,17 @@ def test_autotune_picks_a_shape_and_keeps_results():
     ref = apply_linearized(Tables(n, L, 0.5, n), params[:2], g[:2])
     got = out.cpu().numpy()[:2]
     assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    # FP64 at N = 32: planes per CTA of the register plane kernel; results
+    # do not depend on the shape
     plan64 = lbo.Plan(n, L, 0.5, n)
-    assert plan64.autotune(tp, tg, out) == 0
+    plan64.apply_linearized(tp, tg, out)
+    torch.cuda.synchronize()
+    ref64 = out.cpu().numpy()
+    assert plan64.autotune(tp, tg, out) in (2, 4, 8)
+    plan64.apply_linearized(tp, tg, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref64)
+    # nothing to tune on the generic kernels at another N
+    p16, g16 = workloads.batched_instances(16, L, batch=4, seed=61, noise=0.0)
+    t16, s16 = torch.from_numpy(p16).to(DEV), torch.from_numpy(g16).to(DEV)
+    assert lbo.Plan(16, L, 0.5, 16).autotune(t16, s16, torch.empty_like(s16)) == 0

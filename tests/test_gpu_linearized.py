@@ -110,6 +110,21 @@ def test_register_and_shared_memory_transforms_fp64_n32():
     assert np.array_equal(a, c)
     reg.close()
     smem.close()
+    # the plane kernel's tile shapes (planes per CTA) give the same numbers
+    for planes in (2, 8):
+        pl = lbo.Plan(n, L, om, n, planes=planes)
+        assert np.array_equal(run(pl, params, g), a)
+        pl.close()
+
+
+def test_autotune_picks_a_plane_tile_for_fp64_n32():
+    n, L = 32, 8.0
+    params, g = workloads.batched_instances(n, L, batch=8, seed=8, noise=0.0)
+    tp, tg = torch.from_numpy(params).to(DEV), torch.from_numpy(g).to(DEV)
+    out = torch.empty_like(tg)
+    plan = lbo.Plan(n, L, 0.5, n)
+    assert plan.autotune(tp, tg, out) in (2, 4, 8)
+    plan.close()
 
 
 def test_full_size_batch_sampled_instances():
