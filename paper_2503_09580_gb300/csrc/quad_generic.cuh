@@ -16,10 +16,12 @@
 #pragma once
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "lbo_internal.h"
 #include "lin_kernels.cuh"
+#include "quad_reg64.cuh"
 
 namespace lbo {
 
@@ -241,14 +243,41 @@ static lbo_status run_quadratic(lbo_plan* p, QuadState* qs, const double* f, dou
   const double* dwm = dsig + 3 * M;
   const size_t total = (size_t)B * n3;
   const int cb = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+  // FP64 at N = 32: the per-(m) kernels with one thread per pencil
+  // (quad_reg64.cuh) unless LBO_OPT_KERNEL = 2 asks for the shared-memory ones;
+  // their phase factors come from a table after the chunk buffers
+  constexpr bool R64 = std::is_same<T, double>::value && N == 32;
+  const bool reg = R64 && p->kernel_choice != 2;
+  cpx<double>* ptab = (cpx<double>*)(Pm + (size_t)MB * B * n3);
+  if constexpr (R64) {
+    if (reg) {
+      LBO_LAUNCH(p, "q_phase_table", s, r64::k_q_phase_table_r64, p->J * M, 3 * N, 0, qs->d_gsw, dsig, M, pi,
+                 2.0 * p->L, ptab);
+      smem_attr(r64::k_plane_inv_prod_r64<4>, 2 * r64::PlaneR<4>::BYTES);
+      launches += 1;
+    }
+  }
   for (int j = 0; j < p->J; ++j) {
     const double c = pi * p->gj[j] / (2.0 * p->L);
     for (int m0 = 0; m0 < M; m0 += MB) {
       const int mb = std::min(MB, M - m0);
-      LBO_LAUNCH(p, "q_axis1_phase", s, ka_ph, dim3(ga.x, B, mb), blk, 0, FH, Wm1, Wm2, dsig, m0, c,
-                 (size_t)B * H);
-      LBO_LAUNCH(p, "q_plane_inv_prod", s, kp_prod, dim3(gp.x, B, mb), blk, 2 * sm, Wm1, Wm2, Pm, dwm, m0,
-                 (size_t)B * H, total);
+      bool done = false;
+      if constexpr (R64) {
+        if (reg) {
+          LBO_LAUNCH(p, "q_axis1_phase", s, r64::k_axis1_phase_r64, dim3(r64::RNC / 32, B, mb), 32, 0, FH, Wm1, Wm2,
+                     ptab + (size_t)j * M * 3 * N, m0, (size_t)B * H);
+          LBO_LAUNCH(p, "q_plane_inv_prod", s, r64::k_plane_inv_prod_r64<4>, dim3(N / 4, B, mb),
+                     r64::PlaneR<4>::THREADS, 2 * r64::PlaneR<4>::BYTES, Wm1, Wm2, Pm, dwm, m0, (size_t)B * H,
+                     total);
+          done = true;
+        }
+      }
+      if (!done) {
+        LBO_LAUNCH(p, "q_axis1_phase", s, ka_ph, dim3(ga.x, B, mb), blk, 0, FH, Wm1, Wm2, dsig, m0, c,
+                   (size_t)B * H);
+        LBO_LAUNCH(p, "q_plane_inv_prod", s, kp_prod, dim3(gp.x, B, mb), blk, 2 * sm, Wm1, Wm2, Pm, dwm, m0,
+                   (size_t)B * H, total);
+      }
       LBO_LAUNCH(p, "q_sum_m", s, k_sum_m<T>, cb, 256, 0, Pm, Ps, mb, total, total, m0 == 0 ? 1 : 0);
       launches += 3;
     }

@@ -179,8 +179,11 @@ lbo_status apply_quadratic_device(lbo_plan* p, const double* f, double* out, int
   const int M = (int)qs->wm.size();
   const size_t rb = generic_real_bytes(p->precision);
   const size_t MB = fused ? 0 : (size_t)q_chunk(B, M, (int)N, rb);
+  // FP64 at N = 32 (register kernels): the phase-factor table after the chunk buffers
+  const size_t ptab = p->precision == LBO_PREC_FP64 && N == 32 && p->kernel_choice != 2
+                          ? (size_t)p->J * M * 3 * N * 2 * sizeof(double) : 0;
   const size_t need = fused ? quad_fused32_workspace_bytes(B, G)
-                            : (size_t)B * (4 * H * 2 * rb + 3 * n3 * rb) + MB * (size_t)B * (2 * H * 2 * rb + n3 * rb);
+                            : (size_t)B * (4 * H * 2 * rb + 3 * n3 * rb) + MB * (size_t)B * (2 * H * 2 * rb + n3 * rb) + ptab;
   if (need > qs->ws_bytes) {
     if (qs->ws) cudaFree(qs->ws);
     qs->ws = nullptr;
