@@ -980,6 +980,54 @@ def n64_leg(with_oracle, batch=64, steps=3, L=8.0):
     return res
 
 
+def quadratic_leg(precision, peaks, batch=128, steps=3, n=32, L=8.0, p=4, kernel=0):
+    """Q(f,f) in the M-point form of Eq. (2.14) at N = 32, M = 2 p^2 = 32,
+    J = N, hard spheres, on a batch of seeded g = M * quartic instances:
+    evaluations/s and the rooflines of its two per-(j, m) kernels (their
+    algorithmic work per radial and hemisphere node and instance:
+    q_axis1_phase 2 axis passes + the phase products, q_plane_inv_prod 4 axis
+    passes + the product)."""
+    import torch
+    from paper_2503_09580_gb300 import lbo, workloads
+    _, g = workloads.batched_instances(n, L, batch=batch, seed=3, noise=0.0)
+    tf = torch.from_numpy(g).cuda()
+    out = torch.empty_like(tf)
+    plan = lbo.Plan(n, L, 0.5, n, precision=precision, hemisphere_p=p, kernel=kernel)
+    for _ in range(2):
+        plan.apply_quadratic(tf, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.apply_quadratic(tf, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    plan.profile(True)
+    plan.apply_quadratic(tf, out)
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile(False)
+    plan.close()
+    M, J = 2 * p * p, n
+    peak = peaks["fp64_tflops"] if precision == "fp64" else peaks["fp32_tflops"]
+    work = {"q_axis1_phase": 2 * transform_axis_flops(n) + 9 * n ** 3,
+            "q_plane_inv_prod": 4 * transform_axis_flops(n) + 2 * n ** 3}
+    kr = {}
+    for name, (cnt, tot) in sorted(prof.items()):
+        per = tot / max(cnt, 1)
+        rec = {"launches": cnt, "ms_per_launch": per}
+        if name in work and precision != "fp32":
+            fl = work[name] * batch * (J * M / cnt)  # (j, m) pairs per launch
+            rec.update({"bound": "alu", "achieved_tflops": fl / (per * 1e-3) / 1e12})
+            rec["frac"] = rec["achieved_tflops"] / peak
+        kr[name] = rec
+    return {"workload": "Q(f,f), N=32, M=32 hemisphere points, J=32, hard spheres, batch %d" % batch,
+            "precision": precision, "kernel_set": {0: "fastest", 2: "shared-memory transforms"}.get(kernel, kernel),
+            "ms_per_evaluation": ms, "value": batch / (ms * 1e-3), "unit": "Q evaluations/s",
+            "kernel_rooflines": kr}
+
+
 def mixed_leg(steps=5):
     """512 cells with N in {24, 32, 48} (about 50/35/15 %, seeded), FP32,
     one plan per N applied as a group replayed from a CUDA graph."""
@@ -1145,6 +1193,9 @@ def run_ours(args, world, rank, local):
             "sweep": shock_leg("sweep"), "moment_transport": shock_leg("moment", coarse_operator="transport")}
         if args.shock_cells > 0:
             line["shock_mixed_n_to_1e-10"] = shock_mixed_leg(nx=args.shock_cells)
+        line["quadratic"] = {"fp64": quadratic_leg("fp64", peaks),
+                             "fp64_shared_memory_transforms": quadratic_leg("fp64", peaks, kernel=2),
+                             "fp32": quadratic_leg("fp32", peaks)}
         line["mixed_n"] = mixed_leg()
         line["n64"] = n64_leg(with_oracle=not args.no_cpu_baseline)
         if args.lin_vs_bin:
@@ -1180,9 +1231,18 @@ def main():
     ap.add_argument("--ref-per-core", type=int, default=1, help="reference arm: instances per core per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the Newton-step and mixed-N legs")
+    ap.add_argument("--q-only", action="store_true",
+                    help="only the Q(f,f) leg (N=32, M=32, batch 128; FP64 and FP32), one JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.q_only:
+        import torch
+        from paper_2503_09580_gb300 import lbo
+        peaks = lbo.measure_alu_peaks(torch.cuda.current_stream())
+        print(json.dumps({"quadratic": {"fp64": quadratic_leg("fp64", peaks), "fp32": quadratic_leg("fp32", peaks)},
+                          "measured_peaks": peaks}), flush=True)
+        return
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
