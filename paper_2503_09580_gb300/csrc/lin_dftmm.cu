@@ -74,11 +74,7 @@ template <int N, int AXIS, int PRE, int POST, bool BF>
 lbo_status pass(lbo_plan* p, const char* name, PassArgs a, int sms) {
   using G = mm::Geo<N>;
   auto k = mm::k_dft_pass<N, AXIS, PRE, POST, BF>;
-  static bool attr = false;  // per instantiation
-  if (!attr) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-    attr = true;
-  }
+  raise_smem_limit((const void*)k, G::SMEM);
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, mm::kTile, G::SMEM);
   per_sm = std::max(1, std::min(per_sm, 512 / G::TMEM_COLS));  // TMEM columns of the SM

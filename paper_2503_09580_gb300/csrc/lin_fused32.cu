@@ -545,13 +545,9 @@ lbo_status run_linearized_fused32(lbo_plan* p, const double* params, const doubl
   if (e == cudaSuccess) e = upload_dct();
   if (e != cudaSuccess) return cuda_fail(e, "fused32 twiddles");
   const size_t sm = sizeof(cpx<float>) * S_TOTAL;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_f32_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_f32_gain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GAIN_SMEM);
-    cudaFuncSetAttribute(k_f32_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
+  raise_smem_limit((const void*)k_f32_head, sm);
+  raise_smem_limit((const void*)k_f32_gain, GAIN_SMEM);
+  raise_smem_limit((const void*)k_f32_tail, sm);
   if (!p->d_tc_err) {
     e = cudaMalloc(&p->d_tc_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_tc_err, 0, sizeof(int));

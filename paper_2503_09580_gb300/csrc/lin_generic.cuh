@@ -36,7 +36,7 @@ static GenericTables<T> plain_tables(const lbo_plan* p) {
 
 template <typename K>
 static inline void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  raise_smem_limit((const void*)kernel, bytes);
 }
 
 template <int N>

@@ -1,9 +1,28 @@
 // Per-kernel CUDA-event timing of a plan (lbo_plan_profile*).
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "lbo_internal.h"
 
 namespace lbo {
+
+void raise_smem_limit(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = done[{func, dev}];
+  if (have >= bytes) return;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess) have = bytes;
+  else cudaGetLastError();
+}
 
 static cudaEvent_t take_event(lbo_plan* p) {
   if (!p->prof_pool.empty()) {

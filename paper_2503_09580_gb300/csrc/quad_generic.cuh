@@ -180,7 +180,7 @@ __global__ void k_combine_q(const double* __restrict__ f, const T* __restrict__ 
 
 template <typename K>
 inline void smem_attr(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  raise_smem_limit((const void*)kernel, bytes);
 }
 
 template <typename T, int N>

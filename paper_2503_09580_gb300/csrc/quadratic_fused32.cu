@@ -307,13 +307,9 @@ lbo_status run_quadratic_fused32(lbo_plan* p, const double* f, double* out, int 
   cudaError_t e = upload_twiddles();
   if (e != cudaSuccess) return cuda_fail(e, "fused Q twiddles");
   const size_t sm = sizeof(cpx<float>) * S_TOTAL;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_q32_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_q32_gain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_q32_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
+  raise_smem_limit((const void*)k_q32_head, sm);
+  raise_smem_limit((const void*)k_q32_gain, sm);
+  raise_smem_limit((const void*)k_q32_tail, sm);
   QArgs a{};
   a.f = f;
   a.F = (cpx<float>*)ws;
