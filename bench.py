@@ -1180,6 +1180,7 @@ def run_ours(args, world, rank, local):
                                            "Kn=1, first step from a global Maxwellian theta=1.5",
                                "fp32": newton_leg("fp32", 1.0), "fp64": newton_leg("fp64", 1.0),
                                "fp32_operator_fp64_residual": newton_leg("fp32", 1.0, residual_precision="fp64"),
+                               "fp32_operator_fp32x2_residual": newton_leg("fp32", 1.0, residual_precision="fp32x2"),
                                "fp32_device_krylov": newton_leg("fp32", 1.0, device_krylov=True),
                                "fp64_device_krylov": newton_leg("fp64", 1.0, device_krylov=True)}
         line["newton_to_1e-10"] = {

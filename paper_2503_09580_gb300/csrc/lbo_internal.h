@@ -158,10 +158,10 @@ lbo_status run_quadratic_fused32(lbo_plan* p, const double* f, double* out, int 
                                  int M, int G, int* launches);
 void free_profile(lbo_plan* p);
 
-// Raises a kernel's dynamic shared-memory limit to `bytes` (above the 48 KB
-// default) once per device: the attribute stays with the function, so later
-// launches -- including those recorded into a CUDA graph -- do not set it
-// again.
+// Raises a kernel's dynamic shared-memory limit to `bytes` once per device
+// (the 48 KB default bounds dynamic and static shared memory together): the
+// attribute stays with the function, so later launches -- including those
+// recorded into a CUDA graph -- do not set it again.
 void raise_smem_limit(const void* func, size_t bytes);
 
 // Event bracket around one launch when profiling is on.

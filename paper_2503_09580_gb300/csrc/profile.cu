@@ -9,7 +9,9 @@
 namespace lbo {
 
 void raise_smem_limit(const void* func, size_t bytes) {
-  if (bytes <= 48 * 1024) return;
+  // set for any size: the 48 KB default covers dynamic and static shared
+  // memory together, so a request just at 48 KB still needs it
+  if (bytes == 0) return;
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, size_t> done;
   int dev = 0;
