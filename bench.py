@@ -103,7 +103,7 @@ KERNEL_AXIS_PASSES = {
     "plane_fwd_ratio": 2, "plane_fwd_u": 2, "plane_fwd_g": 2, "plane_fwd_maxw": 2,
     "plane_inv_mh_fwd": 4, "plane_inv": 2,
     "axis1_fwd": 1, "axis1_inv": 1, "axis1_fwd_mul_inv": 2, "axis1_fwd_acc": 1,
-    "axis1_uhat_inv": 1,
+    "axis1_uhat_inv": 1, "axis1_uhat_octant_inv": 1, "axis1_uhat_cached_inv": 1,
 }
 
 
@@ -119,10 +119,12 @@ def dct_pass_flops(n):
 DCT_KERNELS = {
     "uhat_planes": lambda n, J: 2 * dct_pass_flops(n) + 4 * (n // 2 + 1) ** 3,      # one radial node
     "axis1_uhat_inv": lambda n, J: dct_pass_flops(n),                              # plus its FFT pass
+    "uhat_finish": lambda n, J: dct_pass_flops(n),                                 # axis 1 of the octant
     "f32_uhat": lambda n, J: J * (3 * dct_pass_flops(n) + 4 * (n // 2 + 1) ** 3),  # all radial nodes
 }
 KERNEL_POINTWISE = {  # flops per grid point per instance
     "plane_inv_mh_fwd": 2, "axis1_fwd_mul_inv": 3, "axis1_fwd_acc": 4, "axis1_uhat_inv": 3, "combine": 5,
+    "axis1_uhat_octant_inv": 3, "axis1_uhat_cached_inv": 3,
 }
 # Fused FP32 kernels (N = 32): whole real 3-D transforms per instance.
 #   head: r^ (1);  uhat: u^_j for every radial node (octant DCT-I, counted

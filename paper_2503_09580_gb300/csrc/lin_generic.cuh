@@ -110,11 +110,13 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
   // (lin_reg64.cuh) unless LBO_OPT_KERNEL = 2 asks for the shared-memory ones
   constexpr bool R64 = std::is_same<T, double>::value && N == 32;
   const bool reg = R64 && p->kernel_choice != 2;
-  auto launch_uhat = [&](const Axis1Args& a1, bool cached) {
+  // cached: u^_j read whole from an octant (the cache, or, name
+  // "axis1_uhat_octant_inv", the one uhat_finish completes for this call)
+  auto launch_uhat = [&](const Axis1Args& a1, bool cached, const char* name = "axis1_uhat_cached_inv") {
     if constexpr (R64) {
       if (reg) {
         const dim3 gr(r64::RNC / 32, B);
-        if (cached) LBO_LAUNCH(p, "axis1_uhat_cached_inv", s, r64::k_axis1_uhat_r64<true>, gr, 32, 0, a1, RH, W1);
+        if (cached) LBO_LAUNCH(p, name, s, r64::k_axis1_uhat_r64<true>, gr, 32, 0, a1, RH, W1);
         else LBO_LAUNCH(p, "axis1_uhat_inv", s, r64::k_axis1_uhat_r64<false>, gr, 32, 0, a1, RH, W1);
         return;
       }
@@ -176,9 +178,17 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
       // u^_j = FFT(M^g phit_j), real and even: DCT-I of the octant, axes 3 and 2
       LBO_LAUNCH(p, "uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params,
                  phit + (size_t)j * n3, dct, pa.h, UP);
-      // psi_j = InvFFT(u^_j r^), u^_j finished along axis 1 in the same kernel
       a1.uplanes = UP;
-      launch_uhat(a1, false);
+      if (reg) {
+        // the register kernels: axis 1 of the octant once per (|k2|, k3) pair
+        // (the kernels of the Maxwellian cache), then psi_j from the whole octant
+        LBO_LAUNCH(p, "uhat_finish", s, (k_uhat_finish<T, N>), B, blk, 0, UP, dct);
+        launch_uhat(a1, true, "axis1_uhat_octant_inv");
+        launches += 1;
+      } else {
+        // psi_j = InvFFT(u^_j r^), u^_j finished along axis 1 in the same kernel
+        launch_uhat(a1, false);
+      }
     }
     // psi_j <- M^h psi_j ; psi^_j = FFT(psi_j)
     launch_mh();
