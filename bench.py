@@ -120,6 +120,7 @@ DCT_KERNELS = {
     "uhat_planes": lambda n, J: 2 * dct_pass_flops(n) + 4 * (n // 2 + 1) ** 3,      # one radial node
     "axis1_uhat_inv": lambda n, J: dct_pass_flops(n),                              # plus its FFT pass
     "uhat_finish": lambda n, J: dct_pass_flops(n),                                 # axis 1 of the octant
+    "uhat_octant": lambda n, J: 3 * dct_pass_flops(n) + 4 * (n // 2 + 1) ** 3,     # all three axes, one node
     "f32_uhat": lambda n, J: J * (3 * dct_pass_flops(n) + 4 * (n // 2 + 1) ** 3),  # all radial nodes
 }
 KERNEL_POINTWISE = {  # flops per grid point per instance

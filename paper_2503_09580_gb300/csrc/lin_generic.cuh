@@ -175,17 +175,22 @@ static lbo_status run_linearized_generic(lbo_plan* p, const GenericTables<T>& tb
       launch_uhat(a1, true);
       launches -= 1;
     } else {
-      // u^_j = FFT(M^g phit_j), real and even: DCT-I of the octant, axes 3 and 2
-      LBO_LAUNCH(p, "uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params,
-                 phit + (size_t)j * n3, dct, pa.h, UP);
       a1.uplanes = UP;
-      if (reg) {
-        // the register kernels: axis 1 of the octant once per (|k2|, k3) pair
-        // (the kernels of the Maxwellian cache), then psi_j from the whole octant
-        LBO_LAUNCH(p, "uhat_finish", s, (k_uhat_finish<T, N>), B, blk, 0, UP, dct);
-        launch_uhat(a1, true, "axis1_uhat_octant_inv");
-        launches += 1;
-      } else {
+      bool done = false;
+      if constexpr (R64) {
+        if (reg) {
+          // u^_j on the whole octant (weight and the three DCT-I passes, one
+          // block per instance), then psi_j reading it whole
+          LBO_LAUNCH(p, "uhat_octant", s, r64::k_uhat_octant_r64, B, 320, 0, params, (const double*)phit + (size_t)j * n3,
+                     pa.h, (double*)UP);
+          launch_uhat(a1, true, "axis1_uhat_octant_inv");
+          done = true;
+        }
+      }
+      if (!done) {
+        // u^_j = FFT(M^g phit_j), real and even: DCT-I of the octant, axes 3 and 2
+        LBO_LAUNCH(p, "uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params,
+                   phit + (size_t)j * n3, dct, pa.h, UP);
         // psi_j = InvFFT(u^_j r^), u^_j finished along axis 1 in the same kernel
         launch_uhat(a1, false);
       }
@@ -253,8 +258,19 @@ static lbo_status precompute_maxwellian_generic(lbo_plan* p, const GenericTables
   pa.params = params;
   pa.h = 2.0 * p->L / N;
   pa.log_inv_eps = std::log(1.0 / p->eps);
+  constexpr bool R64 = std::is_same<T, double>::value && N == 32;
+  const bool reg = R64 && p->kernel_choice != 2;
+  int per_j = 2;
   for (int j = 0; j < p->J; ++j) {
     T* dst = uh + (size_t)j * B * HC3;
+    if constexpr (R64) {
+      if (reg) {  // the octant kernel of the uncached register path: the same numbers
+        LBO_LAUNCH(p, "cache_uhat_octant", s, r64::k_uhat_octant_r64, B, 320, 0, params,
+                   (const double*)tb.phit + (size_t)j * n3, pa.h, (double*)dst);
+        per_j = 1;
+        continue;
+      }
+    }
     LBO_LAUNCH(p, "cache_uhat_planes", s, k_up, dim3((HC + PL - 1) / PL, B), blk, sm_up, params,
                tb.phit + (size_t)j * n3, tb.dct, pa.h, dst);
     LBO_LAUNCH(p, "cache_uhat_finish", s, (k_uhat_finish<T, N>), B, blk, 0, dst, tb.dct);
@@ -264,7 +280,7 @@ static lbo_status precompute_maxwellian_generic(lbo_plan* p, const GenericTables
   LBO_LAUNCH(p, "cache_plane_fwd_maxw", s, (k_plane_fwd<T, N, PPC, SRC_MAXW>), gp, blk, sm, pa, W1);
   LBO_LAUNCH(p, "cache_axis1_fwd_mul_inv", s, (k_axis1<T, N, CW, AX_FWD_MULT_INV>), ga, blk, 0, a3, W1, W1);
   LBO_LAUNCH(p, "cache_plane_inv", s, (k_plane_inv<T, N, PPC, INV_TO_REAL>), gp, blk, sm, pa, W1, w);
-  p->last_launches = 2 * p->J + 3;
+  p->last_launches = per_j * p->J + 3;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LBO_OK : cuda_fail(e, "Maxwellian cache launch");
 }

@@ -7,6 +7,8 @@
 // the layout of the generic kernels (axes 1 and 2 in the digit-reversed
 // positions of fft.cuh, k3 natural), so the two sets mix freely.
 //
+//   k_uhat_octant_r64 u^_j of every instance on its (N/2+1)^3 octant: the
+//                    weight and its DCT-I along all three axes in one block
 //   k_mh_table_r64   M^h / 2 of every instance, once per application
 //   k_plane_mh_r64   psi_j <- M^h psi_j between InvFFT and FFT of axes 2, 3
 //                    (Algorithm 1, gain loop): the axis-2 columns, then per
@@ -56,6 +58,69 @@ static __global__ void __launch_bounds__(256) k_mh_table_r64(const double* __res
     const int i3 = e % RN, i2 = (e / RN) % RN, i1 = e / (RN * RN);
     dst[e] = ((0.5 * eh[i1]) * eh[RN + i2]) * eh[2 * RN + i3];
   }
+}
+
+// One pencil's DCT-I of length 17 in place: x_d at p[d * stride], d = 0..16,
+// U(k) = sum_d c_d x_d cos(2 pi k d / 32) (c_0 = c_16 = 1, c_d = 2), by the
+// pairing of DctPencil (d with 16 - d) and the same correctly rounded
+// cosines as the plan's DCT table, in the same order; coefficients that are
+// exactly 0 are skipped.
+__device__ __forceinline__ void dct17_inplace(double* p, int stride) {
+  double ev[8], od[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const double x0 = p[d * stride], x1 = p[(16 - d) * stride];
+    ev[d] = x0 + x1;
+    od[d] = x0 - x1;
+  }
+  const double mid = p[8 * stride];
+#pragma unroll
+  for (int k = 0; k < RHC; ++k) {
+    double acc = (k & 1) ? 0.0 : ((k & 2) ? -2.0 * mid : 2.0 * mid);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const double c = (d == 0 ? 1.0 : 2.0) * cos32((k * d) & 31);
+      if (c != 0.0) acc += c * ((k & 1) ? od[d] : ev[d]);
+    }
+    p[k * stride] = acc;
+  }
+}
+
+// u^_j = FFT(M^g phit_j) of one instance on its whole octant (Algorithm 1,
+// precomputation of the gain kernel): the weight w(d) = rho (pi theta)^-3/2
+// exp(-|d h|^2 / theta) phit_j(d), d in [0, 16]^3, formed as k_uhat_planes
+// forms it, then the DCT-I along axes 3, 2 and 1 in shared memory.  Output
+// up[b][k1][k2][k3], the octant layout of the Maxwellian cache.
+// grid = B, block = 320 (289 pencils per pass).
+static __global__ void __launch_bounds__(320) k_uhat_octant_r64(const double* __restrict__ params,
+                                                                const double* __restrict__ phit, double h,
+                                                                double* __restrict__ up) {
+  constexpr int HC2 = RHC * RHC, HC3 = HC2 * RHC;
+  __shared__ double W[HC3];
+  __shared__ double mg[RHC + 1];  // mg[17] = rho (pi theta)^-3/2
+  const int b = blockIdx.x, t = threadIdx.x;
+  const double rho = params[5 * b], theta = params[5 * b + 4];
+  if (t < RHC) {
+    const double x = t * h;
+    mg[t] = exp(-(x * x) / theta);
+  } else if (t == RHC) {
+    mg[RHC] = rho * pow(3.141592653589793 * theta, -1.5);
+  }
+  __syncthreads();
+  for (int e = t; e < HC3; e += blockDim.x) {
+    const int d3 = e % RHC, d2 = (e / RHC) % RHC, d1 = e / HC2;
+    const double w = mg[RHC] * (mg[d1] * mg[d2]) * mg[d3];
+    W[e] = w * phit[((size_t)d1 * RN + d2) * RN + d3];
+  }
+  __syncthreads();
+  if (t < HC2) dct17_inplace(W + t * RHC, 1);  // axis 3: pencil (d1, d2)
+  __syncthreads();
+  if (t < HC2) dct17_inplace(W + (t / RHC) * HC2 + t % RHC, RHC);  // axis 2: pencil (d1, k3)
+  __syncthreads();
+  if (t < HC2) dct17_inplace(W + t, HC2);  // axis 1: pencil (k2, k3)
+  __syncthreads();
+  double* dst = up + (size_t)b * HC3;
+  for (int e = t; e < HC3; e += blockDim.x) dst[e] = W[e];
 }
 
 // grid = (N / PPC, B), block = PlaneR<PPC>::THREADS; src [B][N][N][N/2+1]
