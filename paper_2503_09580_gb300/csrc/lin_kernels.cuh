@@ -91,6 +91,38 @@ __device__ __forceinline__ void fill_maxwellian_tables(double* em, double* thr, 
   __syncthreads();
 }
 
+// Tables of the ratio source r = g/M, filled once per CTA:
+//   ei[d*N + i] = exp(+(v_i - u_d)^2 / (2 theta)), axis 0 divided by the
+//   prefactor rho (2 pi theta)^{-3/2}, so 1/M = ei[i1] ei[N+i2] ei[2N+i3];
+//   *dstar = the smallest |v-u|^2 for which fl(|v-u|^2 / (2 theta)) > thr,
+//   thr = ln(1/eps) - 1.5 ln(2 pi theta).  The cut-off test of Eq. (3.9) is
+//   monotone in |v-u|^2, so |v-u|^2 >= dstar takes exactly the same
+//   decision as the oracle's division, point by point, without dividing.
+template <int N>
+__device__ __forceinline__ void fill_ratio_tables(double* ei, double* dstar, const InstanceParams& q, double h,
+                                                  double log_inv_eps) {
+  for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) {
+    const int d = t / N, i = t % N;
+    const double ud = d == 0 ? q.u1 : (d == 1 ? q.u2 : q.u3);
+    const double dv = __dsub_rn(__dmul_rn((double)(i - N / 2), h), ud);
+    double e = exp(__dmul_rn(dv, dv) / (2.0 * q.theta));
+    if (d == 0) e /= q.rho * pow(2.0 * 3.141592653589793 * q.theta, -1.5);
+    ei[t] = e;
+  }
+  if (threadIdx.x == 0) {
+    const double twoth = __dmul_rn(2.0, q.theta);
+    const double thr = __dsub_rn(log_inv_eps, __dmul_rn(1.5, log(__dmul_rn(__dmul_rn(2.0, 3.141592653589793), q.theta))));
+    double x = __dmul_rn(thr, twoth);
+    for (int it = 0; it < 64 && __ddiv_rn(x, twoth) > thr; ++it) x = nextafter(x, -1e308);
+    for (int it = 0; it < 64 && !(__ddiv_rn(x, twoth) > thr); ++it) x = nextafter(x, 1e308);
+    *dstar = x;
+  }
+  __syncthreads();
+}
+
+// The source fields of the forward plane transforms.  For SRC_MAXW, em and
+// thr are the tables of fill_maxwellian_tables; for SRC_RATIO, those of
+// fill_ratio_tables (em = the reciprocal factors, thr = dstar).
 template <typename T, int N, int SRC>
 __device__ __forceinline__ T plane_source(const PlaneArgs& a, const InstanceParams& q, int b, int i1, int i2, int i3,
                                           const double* em, double thr) {
@@ -99,17 +131,11 @@ __device__ __forceinline__ T plane_source(const PlaneArgs& a, const InstancePara
     return ((const T*)a.src)[idx];
   } else if constexpr (SRC == SRC_REAL64) {
     return (T)a.g[idx];
-  } else {
-    double M = em[i1] * em[N + i2] * em[2 * N + i3];
-    if constexpr (SRC == SRC_MAXW) {
-      return (T)M;
-    } else {  // SRC_RATIO
-      if (a.cutoff) {
-        double d2 = dist2(i1, i2, i3, N, a.h, q);
-        if (__ddiv_rn(d2, __dmul_rn(2.0, q.theta)) > thr) return (T)0;
-      }
-      return (T)(a.g[idx] / M);
-    }
+  } else if constexpr (SRC == SRC_MAXW) {
+    return (T)(em[i1] * em[N + i2] * em[2 * N + i3]);
+  } else {  // SRC_RATIO: r = g / M, 0 where the cut-off of Eq. (3.9) applies
+    if (a.cutoff && dist2(i1, i2, i3, N, a.h, q) >= thr) return (T)0;
+    return (T)(a.g[idx] * ((em[i1] * em[N + i2]) * em[2 * N + i3]));
   }
 }
 
@@ -218,7 +244,8 @@ __global__ void __launch_bounds__(256) k_plane_fwd(PlaneArgs a, cpx<T>* __restri
   __shared__ double thr;
   const int b = blockIdx.y, i1_0 = blockIdx.x * PPC;
   const InstanceParams q = load_params(a.params, b);
-  if constexpr (SRC == SRC_RATIO || SRC == SRC_MAXW) fill_maxwellian_tables<N>(em, &thr, q, a.h, a.log_inv_eps);
+  if constexpr (SRC == SRC_RATIO) fill_ratio_tables<N>(em, &thr, q, a.h, a.log_inv_eps);
+  else if constexpr (SRC == SRC_MAXW) fill_maxwellian_tables<N>(em, &thr, q, a.h, a.log_inv_eps);
   for (int t = threadIdx.x; t < PPC * (N / 2) * N; t += blockDim.x) {
     int i3 = t % N, rest = t / N, qq = rest % (N / 2), pp = rest / (N / 2);
     int i1 = i1_0 + pp;
