@@ -51,7 +51,7 @@ UNIT_ROUNDOFF = {"fp64": U64, "fp32": U32, "fp32x2": 2.0 ** -48, "fp64x2": 2.0 *
 BOUND_FACTOR = 4.0
 HBM_FALLBACK_GBS = 6800.0
 # Kernels bound by memory traffic, not by their arithmetic (rated in GB/s).
-HBM_KERNELS = ("combine", "fixes", "f32_head", "f32_tail", "tc_combine", "mh_table")
+HBM_KERNELS = ("combine", "conservation_fix", "f32_head", "f32_tail", "tc_combine", "mh_table")
 # DRAM bytes (read + write) per launch of a dominant kernel at the benchmark
 # workload from one ncu capture, with the sha256 (first 16 hex digits) of the
 # source files it was built from; reported as null once those sources change.
@@ -155,7 +155,7 @@ def kernel_bytes_per_instance(name, n, real_bytes, groups=1):
     n3, h = n ** 3, n * n * (n // 2 + 1)
     if name == "combine":      # L+, u, w (transform precision) and g in; out
         return 3 * real_bytes * n3 + 16 * n3
-    if name == "fixes":        # out read and written, twice (moments, then the correction)
+    if name == "conservation_fix":  # out read and written, twice (moments, then the correction)
         return 32 * n3
     if name == "f32_head":     # g in (FP64); r^ out (FP32 half spectrum)
         return 8 * n3 + 8 * h

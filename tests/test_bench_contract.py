@@ -49,3 +49,24 @@ def test_fewer_than_three_warmup_steps_are_refused():
     r = _run("--impl", "reference", "--steps", "1", "--warmup", "2")
     assert r.returncode != 0
     assert "warmup" in r.stderr
+
+
+def test_every_linearized_launch_has_a_roofline_model():
+    """Every kernel launch of an L[g] application (lin_generic.cuh, and the
+    fixes) is rated by bench.py's roofline model: a bandwidth-bound kernel
+    with its compulsory bytes, or an arithmetic one with non-zero
+    algorithmic flops.  A launch the model does not know would be reported
+    with a fraction of 0."""
+    import re
+    bench = _bench_module()
+    src = "".join(open(os.path.join(ROOT, "paper_2503_09580_gb300", "csrc", f)).read()
+                  for f in ("lin_generic.cuh", "fixes.cu"))
+    names = set(re.findall(r'LBO_LAUNCH\(p, "([a-z0-9_]+)"', src))
+    names |= set(re.findall(r'launch_uhat\([^)]*"([a-z0-9_]+)"\)', src))
+    names = {n for n in names if not n.startswith("cache_")}  # the Maxwellian cache: outside the timed application
+    assert {"plane_inv_mh_fwd", "axis1_uhat_octant_inv", "uhat_octant", "mh_table", "conservation_fix"} <= names
+    for n in sorted(names):
+        if n in bench.HBM_KERNELS:
+            assert bench.kernel_bytes_per_instance(n, 32, 8) > 0, n
+        else:
+            assert bench.kernel_flops_per_instance(n, 32) > 0, n
