@@ -92,8 +92,9 @@ typedef enum {
                               (default), 1: the generic plane/axis kernels,
                               2: the generic kernels with every transform a
                               two-stage shared-memory FFT (FP64 at N = 32
-                              otherwise runs its hot kernels with one
-                              thread per pencil in registers)                 */
+                              otherwise runs the hot kernels of L and of
+                              Q(f,f) with one thread per pencil in
+                              registers)                                      */
   LBO_OPT_JGROUPS = 9,     /* radial nodes per CTA of the fused FP32 kernel are
                               J / jgroups; 0 (default): chosen from the batch */
   LBO_OPT_Q_SINC_QUADRATURE = 10, /* Q(f,f) only.  1: the loss multiplier
@@ -550,12 +551,12 @@ lbo_status lbo_vec_combination(lbo_plan *plan, double *y, const double *V, size_
 /* Measured ALU peaks of the current device, the denominators of the
  * library's roofline fractions for ALU-bound kernels (a measurement
  * facility; the paper has no counterpart).  Runs dense chains of FP32 FFMA
- * and FP64 DFMA (independent chains per thread, one full wave of 64 warps
- * per SM, about 25 ms per launch), times them with CUDA events on `stream`
- * (a cudaStream_t as void*, NULL = legacy default stream) and returns the
- * best of three launches in TFLOP/s (an FMA counts 2 flops), the SM count
- * from the device properties, and the SM clock seen by the FMA loop
- * (clock64 cycles over the event time, MHz).  Any output pointer may be
+ * and FP64 DFMA (independent chains per thread, operands in registers, one
+ * full wave of 64 warps per SM, about 25 ms per launch), times them with
+ * CUDA events on `stream` (a cudaStream_t as void*, NULL = legacy default
+ * stream) and returns the best of three launches in TFLOP/s (an FMA counts
+ * 2 flops), the SM count from the device properties, and the SM clock seen
+ * by the FP32 loop (clock64 cycles over the event time, MHz).  Any output pointer may be
  * NULL.  Allocates and frees a small device buffer; synchronizes `stream`.
  * Errors: LBO_ECUDA, LBO_ENOMEM. */
 lbo_status lbo_measure_alu_peaks(void *stream, double *fp32_tflops, double *fp64_tflops, int *sm_count,
