@@ -85,3 +85,16 @@ def test_binding_structs_match_the_header_layout(cname, pystruct, tmp_path):
     got = [int(x) for x in subprocess.check_output([exe]).split()]
     assert got[0] == ctypes.sizeof(pystruct)
     assert got[1:] == [getattr(pystruct, n).offset for n in names]
+
+
+def test_binding_option_and_precision_codes_match_the_header():
+    """The binding's option keys and precision names carry the numbers the
+    header's enums give them (LBO_OPT_<NAME> = k; LBO_PREC_<NAME> = k)."""
+    hdr = open(os.path.join(ROOT, "include", "lbo.h")).read()
+    # enumerator lines only (the comments quote options too)
+    opts = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"^\s*LBO_OPT_(\w+)\s*=\s*(\d+)", hdr, re.M)}
+    precs = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"^\s*LBO_PREC_(\w+)\s*=\s*(\d+)", hdr, re.M)}
+    assert opts and precs
+    binding = {k.lower(): v for k, v in lbo.LBO_OPT.items()}
+    assert binding == opts
+    assert lbo.PRECISION == precs
